@@ -1,0 +1,320 @@
+#!/usr/bin/env python3
+"""Throughput of the deflated block-Jacobi Schur-complement GMRES solve.
+
+Workload: the 2-D Poisson-Neumann long-domain problem, 256 x 4 elements of
+order 12 on [0, 64] x [0, 1] (r = 173,056 nodes, k = 26,520 Schur unknowns),
+f = a seeded sum of 32 random low-wavenumber cos-cos modes, g = 0, plain FP64
+path (Alg. seq: block-Jacobi + deflation, CGS2 GMRES) to a relative Schur
+residual of 1e-10.  A step solves one batch of --rhs independent right-hand
+sides (each with its own Krylov space) through the C ABI; value = solved
+right-hand sides per second over all ranks (each rank its own batch: weak
+scaling, no collective on the data path).
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--rhs R] [--impl reference]
+
+--impl reference times the CPU oracle (oracle/, numpy/scipy FP64, Alg. seq
+with Householder GMRES) on the host cores on the same workload and metric.
+"""
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+GRID = dict(mx=256, mz=4, order=12, lx=64.0, lz=1.0)
+WORKLOAD = "2-D Poisson-Neumann, 256x4 elements, order 12, domain 64x1, 32 seeded cos-cos modes, g=0"
+METRIC = "solves/s at 1e-10 rel. residual (plain FP64 DBJ-GMRES)"
+TOL = 1e-10
+FP64_NOMINAL_TFLOPS = 1.25     # GB300 FP64 (non-tensor and tensor), profiling recipe table
+L2_FLUSH_BYTES = 256 << 20
+
+
+def parse():
+    p = argparse.ArgumentParser()
+    p.add_argument("--gpus", type=int, default=1)
+    p.add_argument("--steps", type=int, default=5)
+    p.add_argument("--warmup", type=int, default=3)
+    p.add_argument("--rhs", type=int, default=16)
+    p.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    p.add_argument("--cpu-sample", type=int, default=2, help="oracle right-hand sides in the cpu_baseline leg")
+    p.add_argument("--no-cpu-baseline", action="store_true")
+    return p.parse_args()
+
+
+def rank_env():
+    return int(os.environ.get("RANK", "0")), int(os.environ.get("LOCAL_RANK", "0")), int(os.environ.get("WORLD_SIZE", "1"))
+
+
+def make_f(x, z, nrhs, seed0):
+    import numpy as np
+    from paper_1512_01756_gb300 import inputs
+    F = np.empty((nrhs, x.size))
+    for i in range(nrhs):
+        spec = inputs.cos_modes_spec(seed0 + i)
+        F[i], _ = inputs.cos_modes(x, z, GRID["lx"], GRID["lz"], spec)
+    return F
+
+
+class Clocks:
+    """nvidia-smi sampler running during the timed region."""
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.path = tempfile.mktemp(suffix=".csv")
+        self.proc = None
+
+    def start(self):
+        try:
+            self.fh = open(self.path, "w")
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), "--query-gpu=" + self.Q,
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=self.fh, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.fh.close()
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            parts = [t.strip() for t in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax.append(float(parts[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        os.unlink(self.path)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def traffic_per_launch():
+    """DRAM bytes per class-GEMM launch from the committed ncu summary, if it was
+    taken on the current kernels.cu (else None)."""
+    path = os.path.join(ROOT, "profiles", "class_gemm_traffic.txt")
+    src = os.path.join(ROOT, "paper_1512_01756_gb300", "csrc", "kernels.cu")
+    if not os.path.exists(path):
+        return None
+    kv = {}
+    for line in open(path):
+        if "=" in line and not line.startswith("#"):
+            k, v = line.split("=", 1)
+            kv[k.strip()] = v.strip()
+    sha = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
+    if kv.get("kernels_cu_sha256_16") != sha:
+        return None
+    try:
+        return float(kv["dram_bytes_per_launch_scaled"])
+    except (KeyError, ValueError):
+        return None
+
+
+def oracle_solves_per_s(nrhs, seed0):
+    """Time the CPU oracle (setup excluded, as on the GPU side): returns
+    (solves/s, effective cores, seconds)."""
+    import numpy as np
+    from oracle.smpm import Grid
+    from oracle.schur import StripSchur
+    from oracle import dbj
+    g = Grid(GRID["mx"], GRID["mz"], GRID["order"], GRID["lx"], GRID["lz"])
+    X, Z = g.coords()
+    F = make_f(X, Z, nrhs, seed0)
+    sch = StripSchur(g)
+    c0, w0 = os.times(), time.perf_counter()
+    for i in range(nrhs):
+        _, info = dbj.solve(g, F[i], method="dbj", tol=TOL, schur=sch)
+        assert info["schur_residual"] < 10 * TOL
+    w1, c1 = time.perf_counter(), os.times()
+    cpu = (c1.user - c0.user) + (c1.system - c0.system)
+    cores = max(1, round(cpu / (w1 - w0)))
+    del np
+    return nrhs / (w1 - w0), cores, w1 - w0
+
+
+def run_reference(args):
+    rank, _, world = rank_env()
+    if rank != 0:
+        return 0
+    from oracle.smpm import Grid
+    from oracle.schur import StripSchur
+    from oracle import dbj
+    g = Grid(GRID["mx"], GRID["mz"], GRID["order"], GRID["lx"], GRID["lz"])
+    X, Z = g.coords()
+    from paper_1512_01756_gb300 import inputs
+    sch = StripSchur(g)
+    seed0 = inputs.seed_for(1)
+    F = make_f(X, Z, args.warmup + args.steps, seed0)
+    for i in range(args.warmup):
+        dbj.solve(g, F[i], method="dbj", tol=TOL, schur=sch)
+    c0, w0 = os.times(), time.perf_counter()
+    for i in range(args.steps):
+        dbj.solve(g, F[args.warmup + i], method="dbj", tol=TOL, schur=sch)
+    w1, c1 = time.perf_counter(), os.times()
+    el = w1 - w0
+    cores = max(1, round(((c1.user - c0.user) + (c1.system - c0.system)) / el))
+    val = args.steps / el
+    line = {"impl": "reference", "metric": METRIC, "value": val, "unit": "solves/s", "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * el / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic",
+            "config": {"workload": WORKLOAD, "rhs_per_step": 1, "solver": "oracle Alg. seq, Householder GMRES"},
+            "cpu_baseline": {"value": val, "unit": "solves/s", "cores": cores, "kind": "oracle",
+                             "sample": f"{args.steps} right-hand sides, one per step (operator setup excluded)"},
+            "e2e": {"value": val, "unit": "solves/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def run_ours(args):
+    import numpy as np
+    import torch
+    import torch.distributed as dist
+    import __graft_entry__
+    __graft_entry__.build()
+    from paper_1512_01756_gb300 import smpm, inputs
+
+    rank, local, world = rank_env()
+    dev = torch.device("cuda", local)
+    torch.cuda.set_device(dev)
+    if world > 1:
+        dist.init_process_group("nccl", device_id=dev)
+    stream = torch.cuda.current_stream()
+    R = args.rhs
+    grid = smpm.make_grid(**GRID)
+    solver = smpm.Solver(grid, 0.0, stream)
+    x, z = solver.coords()
+    F = make_f(x, z, R, inputs.seed_for(1) + 1000 * rank)
+    Fd = torch.from_numpy(F).to(dev)
+    Ud = torch.empty_like(Fd)
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
+
+    def barrier():
+        torch.cuda.synchronize()
+        if world > 1:
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    for _ in range(args.warmup):
+        st = solver.solve(Fd, Ud, tol=TOL)
+    barrier()
+    clocks = Clocks(local)
+    clocks.start()
+    l0 = smpm.kernel_launches()
+    solver.profile(True)
+    solver.profile_read(reset=True)
+    times, stats = [], []
+    for _ in range(args.steps):
+        flush.fill_(1.0)                      # evict L2 between steps (not timed)
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        st = solver.solve(Fd, Ud, tol=TOL)
+        e1.record(stream)
+        e1.synchronize()
+        times.append(e0.elapsed_time(e1))
+        stats.append(st.as_dict())
+    launches = smpm.kernel_launches() - l0
+    prof = solver.profile_read(reset=True)
+    solver.profile(False)
+    barrier()
+    clk = clocks.stop()
+    ms = sum(times) / len(times)
+    t = torch.tensor([ms], device=dev, dtype=torch.float64)
+    if world > 1:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    ms_max = float(t.item())
+    worst_res = max(s["rel_resid_true"] for s in stats)
+    iters = [s["iters"] for s in stats]
+
+    # end to end: pinned host buffers through the same C ABI (copies inside the call)
+    Fh = torch.from_numpy(F).pin_memory()
+    Uh = torch.empty_like(Fh).pin_memory()
+    solver.solve(Fh.numpy(), Uh.numpy(), tol=TOL)
+    barrier()
+    e2e_times = []
+    for _ in range(args.steps):
+        flush.fill_(1.0)
+        torch.cuda.synchronize()
+        w0 = time.perf_counter()
+        solver.solve(Fh.numpy(), Uh.numpy(), tol=TOL)
+        e2e_times.append(time.perf_counter() - w0)
+    e2 = torch.tensor([sum(e2e_times) / len(e2e_times)], device=dev, dtype=torch.float64)
+    if world > 1:
+        dist.all_reduce(e2, op=dist.ReduceOp.MAX)
+    e2e_s = float(e2.item())
+    assert np.allclose(Uh.numpy(), Ud.cpu().numpy(), rtol=0, atol=1e-9 * np.abs(Uh.numpy()).max())
+
+    fp64_probe = smpm.probe_fp64(stream)
+    peak = FP64_NOMINAL_TFLOPS
+    achieved = prof["flops"] / (prof["ms"] * 1e-3) / 1e12 if prof["ms"] > 0 else None
+    launches_gemm = max(prof["launches"], 1)
+    tr = traffic_per_launch()
+    roofline = {"bound": "alu", "kernel": "class_gemm_kernel (FP64 DFMA: Schur products, block-Jacobi, strip solves)",
+                "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                "frac": (achieved / peak) if achieved else None,
+                "traffic": tr,
+                "peak_source": "recipe FP64 1.25 TFLOP/s (GB300); measured DFMA probe %.3f TFLOP/s" % fp64_probe,
+                "flops_per_launch": prof["flops"] / launches_gemm,
+                "ms_per_launch": prof["ms"] / launches_gemm,
+                "gemm_share_of_step": prof["ms"] / (ms * args.steps)}
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        v, cores, secs = oracle_solves_per_s(args.cpu_sample, inputs.seed_for(1))
+        cpu = {"value": v, "unit": "solves/s", "cores": cores, "kind": "oracle",
+               "sample": f"{args.cpu_sample} right-hand sides of the same workload ({secs:.1f} s; operator setup excluded)"}
+
+    nb_in = F.nbytes
+    line = {"metric": METRIC, "value": R * world / (ms_max * 1e-3), "unit": "solves/s", "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_max, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "rhs_per_step": R, "tol": TOL, "restart": 64,
+                       "l2": "flushed between timed steps (256 MiB write, untimed)",
+                       "parallelism": f"independent rhs batches per GPU x{world}"},
+            "e2e": {"value": R * world / e2e_s, "unit": "solves/s", "h2d_bytes_per_step": nb_in,
+                    "d2h_bytes_per_step": nb_in},
+            "gpu_launches": launches,
+            "roofline": roofline,
+            "cpu_baseline": cpu,
+            "clocks": clk,
+            "solver": {"iters_per_step": iters, "worst_rel_resid": worst_res, "setup_ms": stats[0]["setup_ms"],
+                       "device_bytes": solver.device_bytes()}}
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    solver.close()
+    if world > 1:
+        dist.destroy_process_group()
+    return 0
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_ours(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,160 @@
+/*
+ * smpm.h -- C ABI of libsmpm.so: deflated block-Jacobi Schur-complement GMRES
+ * for the SMPM (spectral multidomain penalty, GLL collocation) discretisation
+ * of the 2-D Poisson-Neumann problem and of the per-Fourier-mode 2-D
+ * Helmholtz problems (Joshi, Thomsen & Diamessis, arXiv:1512.01756).
+ *
+ * Problem (Sec. 1, Eq. poisson; Sec. 5, Eq. fourier_poisson):
+ *     lap u - k^2 u = f  on [0,lx] x [0,lz],   n . grad u = g  on the boundary,
+ * discretised by Eq. smpm_poisson on an mx x mz element mesh with n = order+1
+ * GLL points per direction, and solved through the Schur complement
+ * S = I + B A^-1 E of the strip split L = A + E B (Sec. 2.3, Eq. operator_decomp)
+ * with right block-Jacobi preconditioning and deflation (Sec. 3, Alg. seq).
+ *
+ * Conventions shared by every entry point
+ * ---------------------------------------
+ * Node order (r = n*n*mx*mz values): index = X*fz + Z with X = ex*n + a the
+ *   global x-node (element ex, GLL point a) and Z = ez*n + b the global z-node,
+ *   fz = n*mz.  smpm_node_coords() returns the coordinates in this order.
+ * Neumann data g (nb = 2*fz + 2*n*mx values): [west: fz][east: fz]
+ *   [south: n*mx][north: n*mx]; g = n.grad u with n the outward normal; a corner
+ *   node sees the g of both sides it lies on.  A NULL g means g = 0.
+ * Pointers: f, g and u may be device pointers or host pointers (pageable or
+ *   pinned); the library detects which (cudaPointerGetAttributes) and stages
+ *   host buffers through device memory it owns, copying inside the call.
+ * Streams: all device work of a handle runs on the stream given at setup
+ *   (NULL = the legacy default stream).  Calls on one handle must not overlap.
+ * Ownership: the caller owns f, g and u.  The handle owns every operator,
+ *   Krylov basis and work array; smpm_release() frees them.
+ * Errors: every int-returning call returns SMPM_OK (0) or a negative code;
+ *   smpm_last_error() gives a message for the calling thread's last failure.
+ *   No C++ exception crosses this boundary.
+ * Gauge: for k^2 = 0 the solution is returned with zero GLL-quadrature mean
+ *   (the Neumann problem fixes u only up to a constant, Sec. 2.4).
+ */
+#ifndef SMPM_H
+#define SMPM_H
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define SMPM_OK 0
+#define SMPM_EINVAL (-1)      /* bad argument or size                         */
+#define SMPM_ENOMEM (-2)      /* device allocation or admission refused        */
+#define SMPM_ENOCONV (-3)     /* max_iter reached; u holds the best iterate     */
+#define SMPM_EBREAKDOWN (-4)  /* NaN/Inf or Arnoldi breakdown                  */
+#define SMPM_ECUDA (-5)       /* a CUDA / cuSOLVER call failed                 */
+#define SMPM_EBUSY (-6)       /* smpm_poll: request still running              */
+
+typedef struct smpm_solver* smpm_handle;
+
+/* Grid and solver options.  Defaults used when a field is 0: tau_scale 10,
+ * z_ratio 1, restart 64, max_iter 2000. */
+typedef struct {
+    int mx, mz, order;      /* elements in x and z, polynomial order (n = order+1)   */
+    double lx, lz;          /* domain [0,lx] x [0,lz]                                */
+    double z_ratio;         /* geometric z-stretch h_{e+1} = z_ratio h_e, 1 = uniform */
+    double tau_scale;       /* penalty tau = tau_scale*N(N+1)/h_perp on every edge    */
+    int deflation_groups;   /* 0: one deflation vector per interface (Sec. 3.3);
+                               1: one per interface and element row                  */
+    int restart;            /* GMRES restart length m                                */
+    int max_iter;           /* GMRES iteration cap per solve                         */
+    int precision;          /* 0: FP64 throughout                                     */
+} smpm_grid;
+
+typedef struct {
+    int iters;              /* GMRES iterations (max over the batch)            */
+    int restarts;           /* restart cycles beyond the first                  */
+    int status;             /* SMPM_OK / SMPM_ENOCONV / SMPM_EBREAKDOWN         */
+    double rel_resid_true;  /* max over the batch of ||S x_S - b_S|| / ||b_S||  */
+    double setup_ms;        /* operator build time of the handle                */
+    double solve_ms;        /* wall time of this call                           */
+} smpm_stats;
+
+/* Build the operators for one k^2 (Sec. 2.3, Sec. 3.2-3.3, Sec. 5 Eq.
+ * transverse_schur): strip operators A_c(k) = A_c - k^2 I and their inverses per
+ * strip class, the Schur blocks G_c = B A_c^-1 E, the block-Jacobi pair blocks
+ * and their inverses, the deflation coarse operator, and for k2 = 0 the left
+ * null vectors u_L, u_S (Claim 1).  stream: a cudaStream_t or NULL.
+ * Returns SMPM_EINVAL for mx < 2, mz < 1, order < 1, order > 32, k2 < 0. */
+int smpm_setup(const smpm_grid* grid, double k2, void* stream, smpm_handle* out);
+
+/* Solve L u = f + tau g (Alg. seq) for one right-hand side to a relative
+ * Schur residual ||S x_S - b_S|| / ||b_S|| <= tol (the paper's check, Sec. 4).
+ * f, u: r doubles; g: nb doubles or NULL.  st may be NULL. */
+int smpm_solve(smpm_handle h, const double* f, const double* g, double tol,
+               double* u, smpm_stats* st);
+
+/* Solve nrhs independent right-hand sides with the same operator in one
+ * batched pass: f and u hold nrhs consecutive r-vectors, g nrhs consecutive
+ * nb-vectors (or NULL).  Each right-hand side keeps its own Krylov space and
+ * meets tol itself. */
+int smpm_solve_batch(smpm_handle h, int nrhs, const double* f, const double* g,
+                     double tol, double* u, smpm_stats* st);
+
+/* One handle holding the operators of several k^2 values (the Fourier modes
+ * of the 3-D problem, Sec. 5, Alg. 3d): nop >= 1 values k2[0..nop-1], at most
+ * one of them zero.  Each operator set is built as by smpm_setup. */
+int smpm_setup_multi(const smpm_grid* grid, int nop, const double* k2, void* stream,
+                     smpm_handle* out);
+
+/* Batched solve over right-hand sides that use different operator sets of a
+ * multi handle: right-hand side i uses operator op_of_rhs[i] (non-decreasing,
+ * in [0, nop)).  All of them run in the same kernel launches (the per-mode
+ * Schur products, block-Jacobi applies and Arnoldi steps of Alg. 3d batched),
+ * each with its own Krylov space and convergence test.  Layouts as in
+ * smpm_solve_batch. */
+int smpm_solve_multi(smpm_handle h, int nrhs, const int* op_of_rhs, const double* f,
+                     const double* g, double tol, double* u, smpm_stats* st);
+
+/* Apply one operator of the method (operator set 0) to nrhs vectors, for
+ * checking the individual kernels.  kind 0: y = S x, the Schur product
+ * (Sec. 2.3, Eq. operator_decomp; assembled form of Sec. 3.1); 1: y = M^-1 x,
+ * block-Jacobi (Sec. 3.2); 2: y = P x = x - S Z K Z^T x, the deflation
+ * projection with the regularised coarse division K (Sec. 3.3); 3: y = B A^-1 b
+ * (the Schur right-hand side map, Alg. seq step 2; in: r-vectors, out:
+ * k-vectors); 4: y = A^-1 b (strip solves, r -> r).  k-vectors use the
+ * interface order (2 j + s) fz + Z: interface j = 0..mx-2, side s = 0 the
+ * east face of strip j, s = 1 the west face of strip j+1.  Pointers host or
+ * device; in and out hold nrhs consecutive vectors. */
+int smpm_apply(smpm_handle h, int kind, int nrhs, const double* in, double* out);
+
+/* Number of nodes r, Neumann values nb and Schur unknowns k of a handle. */
+int smpm_sizes(smpm_handle h, long long* r, long long* nb, long long* k);
+
+/* Node coordinates in node order (x and z: r doubles each, host memory). */
+int smpm_node_coords(smpm_handle h, double* x, double* z);
+
+/* Per right-hand side relative Schur residual ||S x_S - b_S|| / ||b_S|| of the
+ * handle's last solve (first n of them, host memory). */
+int smpm_last_residuals(smpm_handle h, int n, double* out);
+
+/* Device bytes held by the handle (operators + workspace). */
+long long smpm_device_bytes(smpm_handle h);
+
+void smpm_release(smpm_handle h);
+
+/* Measured FP64 FMA throughput of the current device in TFLOP/s (an
+ * independent-chain DFMA loop over 8 blocks per SM); the FP64 roofline
+ * denominator of the dense applies.  stream: cudaStream_t or NULL. */
+int smpm_probe_fp64(void* stream, double* tflops);
+
+/* Profiling of the dense class-GEMM launches (the Schur products, block-Jacobi
+ * applies and strip solves): when enabled, every such launch is bracketed by
+ * CUDA events on the handle's stream and its algorithmic FLOPs
+ * (2 x stored rows x K x active columns) are counted on the device.
+ * smpm_profile_read returns the totals since the last reset. */
+int smpm_profile(smpm_handle h, int enable);
+int smpm_profile_read(smpm_handle h, long long* launches, double* flops, double* ms, int reset);
+
+/* Number of CUDA kernels this library has launched in the process. */
+long long smpm_kernel_launches(void);
+
+/* Message of the calling thread's last failure ("" if none). */
+const char* smpm_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* SMPM_H */

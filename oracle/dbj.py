@@ -100,9 +100,14 @@ def householder_gmres(apply, b, tol, maxiter):
 
 
 class BlockJacobi:
-    """Pairs of interfaces -> dense diagonal blocks of S, LU-factored (Sec. 3.2)."""
+    """Pairs of interfaces -> dense diagonal blocks of S, LU-factored (Sec. 3.2).
 
-    def __init__(self, g: Grid, S):
+    With m_x <= 3 the single block is all of S; for the singular Poisson-Neumann
+    S (singular=True) that block is replaced by the identity (reading: the
+    paper's blocks are proper principal submatrices, which it notes are
+    invertible)."""
+
+    def __init__(self, g: Grid, S, singular=False):
         fz2 = 2 * g.fz
         nif = g.mx - 1
         self.ranges = []
@@ -113,9 +118,12 @@ class BlockJacobi:
             self.ranges.append((lo, hi))
             p += 1
         Sc = S.tocsr()
-        self.lus = [sla.lu_factor(Sc[lo:hi, lo:hi].toarray()) for lo, hi in self.ranges]
+        self.identity = singular and len(self.ranges) == 1
+        self.lus = [] if self.identity else [sla.lu_factor(Sc[lo:hi, lo:hi].toarray()) for lo, hi in self.ranges]
 
     def solve(self, v):
+        if self.identity:
+            return v.copy()
         out = np.empty_like(v)
         for (lo, hi), lu in zip(self.ranges, self.lus):
             out[lo:hi] = sla.lu_solve(lu, v[lo:hi])
@@ -125,7 +133,8 @@ class BlockJacobi:
 class Deflation:
     """Interface-indicator deflation with the regularised coarse division (Sec. 3.3)."""
 
-    def __init__(self, g: Grid, S, uS=None, groups="interface"):
+    def __init__(self, g: Grid, S, uS=None, groups="interface", coarse="lstsq"):
+        self.coarse_mode = coarse
         nif = g.mx - 1
         fz2 = 2 * g.fz
         rows, cols = [], []
@@ -146,6 +155,7 @@ class Deflation:
             raise ValueError(groups)
         r = np.concatenate(rows)
         c = np.concatenate(cols)
+        self.group_size = g.fz if groups == "interface" else g.n
         self.Z = sp.coo_matrix((np.ones(r.size), (r, c)), shape=(g.k, self.d)).tocsr()
         self.S = S
         self.SZ = (S @ self.Z).tocsr()
@@ -157,9 +167,22 @@ class Deflation:
             self.uC = None
 
     def coarse(self, q):
-        """C \\ (q - u_C u_C^T q); singular C read as minimum-norm least squares."""
+        """C \\ (q - u_C u_C^T q) for singular C: minimum-norm least squares
+        ("lstsq"), the solution with its last coarse unknown set to zero
+        ("pinned": the leading (d-1) x (d-1) system is solved), or the
+        zero-mean solution through C + a u_C 1^T / sqrt(d) ("rank1")."""
         if self.uC is not None:
             q = q - self.uC * np.dot(self.uC, q)
+            if self.coarse_mode == "pinned":
+                c = np.zeros_like(q)
+                if self.d > 1:
+                    c[:-1] = np.linalg.solve(self.C[:-1, :-1], q[:-1])
+                return c
+            if self.coarse_mode == "rank1":
+                # zero-mean solution of the consistent system through the
+                # nonsingular C + a u_C 1^T / sqrt(d)
+                a = (np.abs(self.C).max() + 2.0 * self.group_size) / np.sqrt(self.d)
+                return np.linalg.solve(self.C + a * np.outer(self.uC, np.ones(self.d)), q)
             return np.linalg.lstsq(self.C, q, rcond=None)[0]
         return np.linalg.solve(self.C, q)
 
@@ -177,7 +200,7 @@ class Deflation:
 
 
 def solve(g: Grid, f, gb=None, k2=0.0, method="dbj", tol=1e-13, maxiter=2000,
-          groups="interface", schur=None):
+          groups="interface", schur=None, coarse="lstsq"):
     """Iterative oracle: Alg. seq (method 'dbj') or a comparison method.
 
     Returns (u, info).  u is gauge-fixed for k2 == 0.  info holds the GMRES
@@ -198,20 +221,20 @@ def solve(g: Grid, f, gb=None, k2=0.0, method="dbj", tol=1e-13, maxiter=2000,
     if method == "schur":
         xS, it, hist = householder_gmres(lambda v: S @ v, bS, tol, maxiter)
     elif method == "bj":
-        M = BlockJacobi(g, S)
+        M = BlockJacobi(g, S, singular=(k2 == 0.0))
         y, it, hist = householder_gmres(lambda v: S @ M.solve(v), bS, tol, maxiter)
         xS = M.solve(y)
     elif method == "dbj":
-        M = BlockJacobi(g, S)
-        Df = Deflation(g, S, uS, groups)
+        M = BlockJacobi(g, S, singular=(k2 == 0.0))
+        Df = Deflation(g, S, uS, groups, coarse)
         x1, it, hist = householder_gmres(lambda v: Df.P(S @ M.solve(v)), Df.P(bS), tol, maxiter)  # step 4
         x1 = Df.Q(M.solve(x1))                       # step 5
         x2 = Df.coarse_part(bS)                      # steps 6-7
         xS = x1 + x2                                 # step 8
         info["coarse_dim"] = Df.d
     elif method == "2las":
-        M = BlockJacobi(g, S)
-        Df = Deflation(g, S, uS, groups)
+        M = BlockJacobi(g, S, singular=(k2 == 0.0))
+        Df = Deflation(g, S, uS, groups, coarse)
         prec = lambda v: M.solve(v) + Df.coarse_part(v)
         y, it, hist = householder_gmres(lambda v: S @ prec(v), bS, tol, maxiter)
         xS = prec(y)

@@ -1,0 +1,1008 @@
+// libsmpm: handle, operator setup and the batched solve driver behind the C ABI
+// of include/smpm.h.
+//
+// Setup (Secs. 2.3, 3.2, 3.3, 5): for every strip class c (west boundary,
+// interior, east boundary) and every k^2 of the handle the dense strip operator
+// A_c(k) = Ax_c (+) L_z - k^2 I is LU-factored (cuSOLVER getrf/getrs, setup
+// only) into an explicit inverse; W_c = B_c A_c^-1 (right-hand-side map),
+// G_c = W_c E_c (Schur blocks), the block-Jacobi pair blocks and their
+// inverses, the row sums rho_c of G_c that give S Z, the coarse operator K and,
+// for k^2 = 0, the null vectors u_L = u_Lx (x) u_Lz and u_S = E^T u_L (Claim 1).
+//
+// Solve (Alg. seq): b = f + tau g, b <- b - u_L u_L^T b, b_S = W b,
+// b_S <- b_S - u_S u_S^T b_S, right-preconditioned deflated GMRES on
+// P S M^-1 y = P b_S with CGS2 Arnoldi and restarts, x_S = t + Z K Z^T (b_S - S t)
+// with t = M^-1 y (= Q M^-1 y + Z C\(...) b_S), recovery u = A^-1 (b - E x_S),
+// zero-mean gauge for k^2 = 0.  Every step runs in kernels.cu; the host only
+// sequences launches and reads convergence flags.
+#include <cuda_runtime.h>
+#include <cusolverDn.h>
+
+#include <algorithm>
+#include <array>
+#include <chrono>
+#include <cmath>
+#include <cstring>
+#include <memory>
+#include <string>
+#include <vector>
+
+#include "../../include/smpm.h"
+#include "kernels.h"
+#include "smpm_internal.h"
+
+namespace smpm {
+
+static thread_local std::string g_last_error;
+
+struct Err {
+    int code;
+    std::string msg;
+};
+
+#define CK(x)                                                                              \
+    do {                                                                                   \
+        cudaError_t e_ = (x);                                                              \
+        if (e_ != cudaSuccess) throw Err{SMPM_ECUDA, std::string(#x) + ": " + cudaGetErrorString(e_)}; \
+    } while (0)
+#define CS(x)                                                                              \
+    do {                                                                                   \
+        cusolverStatus_t s_ = (x);                                                         \
+        if (s_ != CUSOLVER_STATUS_SUCCESS)                                                 \
+            throw Err{SMPM_ECUDA, std::string(#x) + ": cusolver status " + std::to_string((int)s_)}; \
+    } while (0)
+
+static constexpr int kBN = 32;      // GEMM column tile (kernels.cu BN)
+static constexpr int kChunk = 1024; // vector-kernel chunk
+
+struct Solver {
+    Geometry g;
+    smpm_grid opt{};
+    cudaStream_t stream = nullptr;
+    int nop = 1;
+    std::vector<double> k2;
+    int singular_op = -1;
+    int P = 0, nmc = 0;                      // block-Jacobi blocks and block classes
+    std::vector<int> strip_cls, pair_mc, mc_single;
+    long long kp = 0, ld = 0;
+    int restart = 64, max_iter = 2000;
+    // device operators (all ops, contiguous per kind)
+    double *Ainv = nullptr, *W = nullptr, *G = nullptr, *Minv = nullptr, *rho = nullptr, *K = nullptr;
+    double *uL = nullptr, *uS = nullptr;
+    int *rl_GW = nullptr, *rh_GW = nullptr, *rl_M = nullptr, *rh_M = nullptr, *rl_A = nullptr, *rh_A = nullptr;
+    int* d_strip_cls = nullptr;
+    double *d_tau_z = nullptr, *d_wq = nullptr, *d_hz = nullptr;
+    long long sA = 0, sW = 0, sG = 0, sM = 0, sRho = 0, sK = 0;
+    // workspace
+    int Rcap = 0;
+    struct Work {
+        double *b = nullptr, *t2 = nullptr, *bS = nullptr, *Xp = nullptr, *t = nullptr, *s = nullptr;
+        double *w = nullptr, *z = nullptr, *xS = nullptr, *V = nullptr;
+        double *Hc = nullptr, *htmp = nullptr, *cs = nullptr, *sn = nullptr, *gv = nullptr;
+        double *part1 = nullptr, *part2 = nullptr, *q = nullptr, *c = nullptr, *c0 = nullptr;
+        double *fstage = nullptr, *gstage = nullptr, *ustage = nullptr, *rpart = nullptr;
+        int *active = nullptr, *done = nullptr, *nit = nullptr, *flags = nullptr, *op = nullptr, *gauge = nullptr;
+        double *target = nullptr, *bnorm = nullptr, *rnorm = nullptr;
+        const double** uLp = nullptr;
+        const double** uSp = nullptr;
+        Tile *tM = nullptr, *tG = nullptr, *tW = nullptr, *tA = nullptr;
+        int ntM = 0, ntG = 0, ntW = 0, ntA = 0;
+        std::vector<void*> allocs;
+    } wk;
+    std::vector<int> cur_ops;               // op layout the tiles were built for
+    std::vector<void*> allocs;
+    long long bytes = 0, wk_bytes = 0;
+    std::vector<double> last_res;           // per-rhs ||S x_S - b_S|| / ||b_S|| of the last solve
+    double setup_ms = 0.0;
+    cusolverDnHandle_t sol = nullptr;
+    // optional profiling of the class-GEMM launches (events + device flop counter)
+    bool prof = false;
+    std::vector<cudaEvent_t> ev;
+    int ev_used = 0;
+    unsigned long long* d_flops = nullptr;
+    long long prof_launches = 0;
+    double prof_ms = 0.0, prof_flops = 0.0;
+
+    template <class T>
+    T* dalloc(size_t n, std::vector<void*>& list) {
+        void* p = nullptr;
+        if (n == 0) n = 1;
+        cudaError_t e = cudaMalloc(&p, n * sizeof(T));
+        if (e != cudaSuccess) {
+            cudaGetLastError();
+            throw Err{SMPM_ENOMEM, std::string("device allocation of ") + std::to_string(n * sizeof(T)) +
+                                       " bytes failed: " + cudaGetErrorString(e)};
+        }
+        list.push_back(p);
+        bytes += (long long)(n * sizeof(T));
+        return (T*)p;
+    }
+    void free_list(std::vector<void*>& list) {
+        for (void* p : list) cudaFree(p);
+        list.clear();
+    }
+    ~Solver() {
+        if (stream) cudaStreamSynchronize(stream);
+        for (cudaEvent_t e : ev) cudaEventDestroy(e);
+        free_list(wk.allocs);
+        free_list(allocs);
+        if (sol) cusolverDnDestroy(sol);
+    }
+};
+
+// ---------------------------------------------------------------------------
+// Setup
+// ---------------------------------------------------------------------------
+
+static void upload(double* dst, const std::vector<double>& src, cudaStream_t s) {
+    CK(cudaMemcpyAsync(dst, src.data(), src.size() * sizeof(double), cudaMemcpyHostToDevice, s));
+}
+
+// dst <- src^-1 for an m x m row-major matrix in device memory (src is destroyed).
+static void invert_dense(Solver& S, double* src, double* dst, int m, double* work, int lwork, int* ipiv, int* info) {
+    // cuSOLVER is column-major: the row-major buffer is read as src^T; solving
+    // src^T X = I in column-major gives X = src^-T, i.e. src^-1 in row-major.
+    k_identity(dst, m, S.stream);
+    CS(cusolverDnDgetrf(S.sol, m, m, src, m, work, ipiv, info));
+    CS(cusolverDnDgetrs(S.sol, CUBLAS_OP_N, m, m, src, m, ipiv, dst, m, info));
+    int h_info = 0;
+    CK(cudaMemcpyAsync(&h_info, info, sizeof(int), cudaMemcpyDeviceToHost, S.stream));
+    CK(cudaStreamSynchronize(S.stream));
+    if (h_info != 0) throw Err{SMPM_EBREAKDOWN, "singular strip or block-Jacobi matrix (getrf info " + std::to_string(h_info) + ")"};
+}
+
+static void setup_solver(Solver& S) {
+    auto t0 = std::chrono::steady_clock::now();
+    Geometry& g = S.g;
+    const int n = g.n, fz = g.fz, nfz = n * fz, f2 = 2 * fz, f4 = 4 * fz, mx = g.mx, ng = g.ng, d = g.d;
+    cudaStream_t st = S.stream;
+    CS(cusolverDnCreate(&S.sol));
+    CS(cusolverDnSetStream(S.sol, st));
+    S.kp = 2LL * fz * mx;
+    S.ld = ((S.kp + fz + 31) / 32) * 32;
+    S.restart = S.opt.restart > 0 ? S.opt.restart : 64;
+    S.max_iter = S.opt.max_iter > 0 ? S.opt.max_iter : 2000;
+    if (S.restart > 512) throw Err{SMPM_EINVAL, "restart above 512"};
+
+    // strip classes and block-Jacobi block classes
+    S.strip_cls.assign(mx, 1);
+    S.strip_cls[0] = 0;
+    S.strip_cls[mx - 1] = 2;
+    const int nif = mx - 1;
+    S.P = (nif + 1) / 2;
+    std::vector<std::array<int, 3>> sig;
+    S.pair_mc.assign(S.P, 0);
+    for (int p = 0; p < S.P; ++p) {
+        std::array<int, 3> sgn{S.strip_cls[2 * p], S.strip_cls[2 * p + 1], (2 * p + 1 < nif) ? S.strip_cls[2 * p + 2] : -1};
+        auto it = std::find(sig.begin(), sig.end(), sgn);
+        if (it == sig.end()) { sig.push_back(sgn); it = sig.end() - 1; }
+        S.pair_mc[p] = (int)(it - sig.begin());
+    }
+    S.nmc = (int)sig.size();
+    S.mc_single.resize(S.nmc);
+    for (int c = 0; c < S.nmc; ++c) S.mc_single[c] = sig[c][2] < 0 ? 1 : 0;
+
+    const int nop = S.nop;
+    S.sA = (long long)nfz * nfz;
+    S.sW = (long long)f2 * nfz;
+    S.sG = (long long)f2 * f2;
+    S.sM = (long long)f4 * f4;
+    S.sRho = 3LL * 2 * ng * f2;
+    S.sK = (long long)d * d;
+    S.Ainv = S.dalloc<double>((size_t)nop * 3 * S.sA, S.allocs);
+    S.W = S.dalloc<double>((size_t)nop * 3 * S.sW, S.allocs);
+    S.G = S.dalloc<double>((size_t)nop * 3 * S.sG, S.allocs);
+    S.Minv = S.dalloc<double>((size_t)nop * S.nmc * S.sM, S.allocs);
+    S.rho = S.dalloc<double>((size_t)nop * S.sRho, S.allocs);
+    S.K = S.dalloc<double>((size_t)nop * S.sK, S.allocs);
+
+    // valid output rows per matrix
+    {
+        std::vector<int> lo(nop * 3), hi(nop * 3), loM(nop * S.nmc), hiM(nop * S.nmc), loA(nop * 3), hiA(nop * 3);
+        for (int o = 0; o < nop; ++o) {
+            for (int c = 0; c < 3; ++c) {
+                lo[o * 3 + c] = c == 0 ? fz : 0;
+                hi[o * 3 + c] = c == 2 ? fz : f2;
+                loA[o * 3 + c] = 0;
+                hiA[o * 3 + c] = nfz;
+            }
+            for (int c = 0; c < S.nmc; ++c) {
+                loM[o * S.nmc + c] = 0;
+                hiM[o * S.nmc + c] = S.mc_single[c] ? f2 : f4;
+            }
+        }
+        auto up = [&](int*& dptr, const std::vector<int>& v) {
+            dptr = S.dalloc<int>(v.size(), S.allocs);
+            CK(cudaMemcpyAsync(dptr, v.data(), v.size() * sizeof(int), cudaMemcpyHostToDevice, st));
+        };
+        up(S.rl_GW, lo); up(S.rh_GW, hi); up(S.rl_M, loM); up(S.rh_M, hiM); up(S.rl_A, loA); up(S.rh_A, hiA);
+        up(S.d_strip_cls, S.strip_cls);
+        CK(cudaStreamSynchronize(st));
+    }
+    S.d_tau_z = S.dalloc<double>(g.mz, S.allocs);
+    S.d_hz = S.dalloc<double>(g.mz, S.allocs);
+    S.d_wq = S.dalloc<double>(n, S.allocs);
+    upload(S.d_tau_z, g.tau_z, st);
+    upload(S.d_hz, g.hz, st);
+    upload(S.d_wq, g.w, st);
+
+    // 1-D factors (host), uploaded once
+    std::vector<double> Ax[3], beta[3], Lz;
+    for (int c = 0; c < 3; ++c) {
+        strip_x_operator(g, c, Ax[c]);
+        face_flux_rows(g, c, beta[c]);
+    }
+    z_operator(g, Lz);
+    std::vector<void*> tmp;
+    double* dAx = S.dalloc<double>(3 * (size_t)n * n, tmp);
+    double* dbeta = S.dalloc<double>(3 * 2 * (size_t)n, tmp);
+    double* dLz = S.dalloc<double>((size_t)fz * fz, tmp);
+    for (int c = 0; c < 3; ++c) {
+        CK(cudaMemcpyAsync(dAx + (size_t)c * n * n, Ax[c].data(), sizeof(double) * n * n, cudaMemcpyHostToDevice, st));
+        CK(cudaMemcpyAsync(dbeta + (size_t)c * 2 * n, beta[c].data(), sizeof(double) * 2 * n, cudaMemcpyHostToDevice, st));
+    }
+    upload(dLz, Lz, st);
+
+    // LU workspace sized for the largest matrix
+    const int mmax = std::max(nfz, f4);
+    double* dtmp = S.dalloc<double>((size_t)mmax * mmax, tmp);
+    double* dtmp2 = S.dalloc<double>((size_t)f4 * f4, tmp);
+    int lwork = 0, lw2 = 0;
+    CS(cusolverDnDgetrf_bufferSize(S.sol, nfz, nfz, dtmp, nfz, &lwork));
+    CS(cusolverDnDgetrf_bufferSize(S.sol, f4, f4, dtmp, f4, &lw2));
+    lwork = std::max(lwork, lw2);
+    double* dwork = S.dalloc<double>((size_t)std::max(lwork, 1), tmp);
+    int* dipiv = S.dalloc<int>((size_t)mmax, tmp);
+    int* dinfo = S.dalloc<int>(1, tmp);
+
+    // null vectors (k^2 = 0): u_L = u_Lx (x) u_Lz, u_S = E^T u_L / ||E^T u_L||
+    std::vector<double> uS_h;
+    for (int o = 0; o < nop; ++o)
+        if (S.k2[o] == 0.0) S.singular_op = o;
+    if (S.singular_op >= 0) {
+        std::vector<double> ux, uz;
+        std::string msg;
+        if (!left_null_x(g, ux, msg) || !left_null_z(g, uz, msg)) throw Err{SMPM_EBREAKDOWN, msg};
+        std::vector<double> uL_h((size_t)g.r);
+        for (int X = 0; X < g.nx; ++X)
+            for (int Z = 0; Z < fz; ++Z) uL_h[(size_t)X * fz + Z] = ux[X] * uz[Z];
+        uS_h.assign((size_t)S.ld, 0.0);
+        double nrm = 0.0;
+        for (int i = 0; i < mx; ++i)
+            for (int sd = 0; sd < 2; ++sd) {
+                const int F = 2 * i + sd;
+                if (F == 0 || F == 2 * mx - 1) continue;
+                const int X = i * n + (sd == 0 ? 0 : g.N);
+                for (int Z = 0; Z < fz; ++Z) {
+                    const double v = ux[X] * uz[Z];
+                    uS_h[(size_t)F * fz + Z] = v;
+                    nrm += v * v;
+                }
+            }
+        nrm = std::sqrt(nrm);
+        for (double& v : uS_h) v /= nrm;
+        S.uL = S.dalloc<double>((size_t)g.r, S.allocs);
+        S.uS = S.dalloc<double>((size_t)S.ld, S.allocs);
+        upload(S.uL, uL_h, st);
+        upload(S.uS, uS_h, st);
+        CK(cudaStreamSynchronize(st));
+    }
+
+    for (int o = 0; o < nop; ++o) {
+        const double k2 = S.k2[o];
+        double* Ainv = S.Ainv + (size_t)o * 3 * S.sA;
+        double* W = S.W + (size_t)o * 3 * S.sW;
+        double* G = S.G + (size_t)o * 3 * S.sG;
+        for (int c = 0; c < 3; ++c) {
+            if (c == 1 && mx < 3) {  // no interior strips
+                k_fill(Ainv + c * S.sA, S.sA, 0.0, st);
+                k_fill(W + c * S.sW, S.sW, 0.0, st);
+                k_fill(G + c * S.sG, S.sG, 0.0, st);
+                continue;
+            }
+            k_build_strip_op(dtmp, dAx + (size_t)c * n * n, dLz, k2, n, fz, st);
+            invert_dense(S, dtmp, Ainv + c * S.sA, nfz, dwork, lwork, dipiv, dinfo);
+            k_build_W(W + c * S.sW, Ainv + c * S.sA, dbeta + (size_t)c * 2 * n, n, fz, st);
+            k_build_G(G + c * S.sG, W + c * S.sW, n, fz, c, st);
+            k_build_rho(S.rho + (size_t)o * S.sRho + (size_t)c * 2 * ng * f2, G + c * S.sG, fz, ng, st);
+        }
+        for (int mc = 0; mc < S.nmc; ++mc) {
+            const double* gA = G + sig[mc][0] * S.sG;
+            const double* gB = G + sig[mc][1] * S.sG;
+            const double* gC = sig[mc][2] >= 0 ? G + sig[mc][2] * S.sG : nullptr;
+            const int m = gC ? f4 : f2;
+            k_build_M(dtmp, gA, gB, gC, fz, st);
+            double* dst = S.Minv + ((size_t)o * S.nmc + mc) * S.sM;
+            if (S.P == 1 && k2 == 0.0) {
+                // m_x <= 3: the one block is all of the singular S; use M = I
+                k_identity(dtmp2, m, st);
+                k_pad_block(dst, dtmp2, m, f4, st);
+            } else if (m == f4) {
+                invert_dense(S, dtmp, dst, m, dwork, lwork, dipiv, dinfo);
+            } else {
+                invert_dense(S, dtmp, dtmp2, m, dwork, lwork, dipiv, dinfo);
+                k_pad_block(dst, dtmp2, m, f4, st);
+            }
+        }
+        // coarse matrix C = Z^T S Z from the row sums (host), then K
+        std::vector<double> rho_h((size_t)S.sRho);
+        CK(cudaMemcpyAsync(rho_h.data(), S.rho + (size_t)o * S.sRho, sizeof(double) * S.sRho, cudaMemcpyDeviceToHost, st));
+        CK(cudaStreamSynchronize(st));
+        const int gs = fz / ng;
+        // gsum[cls][side][g][half][g'] = sum over group g' of half `half` of rho[cls][side][g]
+        auto rh = [&](int cls, int side, int gg) { return rho_h.data() + ((size_t)(cls * 2 + side) * ng + gg) * f2; };
+        auto gsum = [&](int cls, int side, int gg, int half, int gp) {
+            const double* v = rh(cls, side, gg) + half * fz + gp * gs;
+            double s = 0.0;
+            for (int z = 0; z < gs; ++z) s += v[z];
+            return s;
+        };
+        std::vector<double> C((size_t)d * d, 0.0);
+        for (int t = 0; t < nif; ++t)
+            for (int gg = 0; gg < ng; ++gg) {
+                const int col = t * ng + gg;
+                const int cl_r = S.strip_cls[t + 1], cl_l = S.strip_cls[t];
+                C[(size_t)col * d + col] += 2.0 * gs;
+                for (int gp = 0; gp < ng; ++gp) {
+                    C[(size_t)(t * ng + gp) * d + col] += gsum(cl_r, 0, gg, 0, gp) + gsum(cl_l, 1, gg, 1, gp);
+                    if (t >= 1) C[(size_t)((t - 1) * ng + gp) * d + col] += gsum(cl_l, 1, gg, 0, gp);
+                    if (t + 1 <= nif - 1) C[(size_t)((t + 1) * ng + gp) * d + col] += gsum(cl_r, 0, gg, 1, gp);
+                }
+            }
+        std::vector<double> Kh, uC;
+        const double* uCp = nullptr;
+        if (k2 == 0.0) {  // u_C = Z^T u_S normalised (Sec. 3.3)
+            uC.assign(d, 0.0);
+            double nrm = 0.0;
+            for (int t = 0; t < nif; ++t)
+                for (int gg = 0; gg < ng; ++gg) {
+                    double s = 0.0;
+                    for (int z = 0; z < gs; ++z)
+                        s += uS_h[(size_t)(2 * t + 1) * fz + gg * gs + z] + uS_h[(size_t)(2 * t + 2) * fz + gg * gs + z];
+                    uC[t * ng + gg] = s;
+                    nrm += s * s;
+                }
+            nrm = std::sqrt(nrm);
+            for (double& v : uC) v /= nrm;
+            uCp = uC.data();
+        }
+        std::string msg;
+        if (!coarse_operator(C, d, fz / ng, uCp, Kh, msg)) throw Err{SMPM_EBREAKDOWN, msg};
+        upload(S.K + (size_t)o * S.sK, Kh, st);
+        CK(cudaStreamSynchronize(st));
+    }
+    CK(cudaStreamSynchronize(st));
+    S.free_list(tmp);
+    S.setup_ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+}
+
+// ---------------------------------------------------------------------------
+// Workspace and tiles
+// ---------------------------------------------------------------------------
+
+static void ensure_workspace(Solver& S, int R) {
+    if (R <= S.Rcap) return;
+    CK(cudaStreamSynchronize(S.stream));
+    S.bytes -= S.wk_bytes;
+    S.free_list(S.wk.allocs);
+    const long long bytes_before = S.bytes;
+    auto& w = S.wk;
+    auto& L = w.allocs;
+    const Geometry& g = S.g;
+    const int m = S.restart;
+    const long long ld = S.ld;
+    const int nch = (int)((S.kp + kChunk - 1) / kChunk);
+    const int rch = (int)((g.r + kChunk - 1) / kChunk);
+    w.b = S.dalloc<double>((size_t)R * g.r, L);
+    w.t2 = S.dalloc<double>((size_t)R * g.r, L);
+    w.fstage = S.dalloc<double>((size_t)R * g.r, L);
+    w.ustage = S.dalloc<double>((size_t)R * g.r, L);
+    w.gstage = S.dalloc<double>((size_t)R * (2 * g.fz + 2 * g.nx), L);
+    double** vecs[] = {&w.bS, &w.Xp, &w.t, &w.s, &w.w, &w.z, &w.xS};
+    for (double** v : vecs) {
+        *v = S.dalloc<double>((size_t)R * ld, L);
+        k_fill(*v, (long long)R * ld, 0.0, S.stream);
+    }
+    w.V = S.dalloc<double>((size_t)R * (m + 1) * ld, L);
+    k_fill(w.V, (long long)R * (m + 1) * ld, 0.0, S.stream);
+    w.Hc = S.dalloc<double>((size_t)R * m * (m + 1), L);
+    w.htmp = S.dalloc<double>((size_t)R * (m + 1), L);
+    w.cs = S.dalloc<double>((size_t)R * m, L);
+    w.sn = S.dalloc<double>((size_t)R * m, L);
+    w.gv = S.dalloc<double>((size_t)R * (m + 1), L);
+    w.part1 = S.dalloc<double>((size_t)R * nch * (m + 2), L);
+    w.part2 = S.dalloc<double>((size_t)R * nch * (m + 2), L);
+    w.rpart = S.dalloc<double>((size_t)R * std::max(nch, rch), L);
+    w.q = S.dalloc<double>((size_t)R * g.d, L);
+    w.c = S.dalloc<double>((size_t)R * g.d, L);
+    w.c0 = S.dalloc<double>((size_t)R * g.d, L);
+    w.active = S.dalloc<int>(R, L);
+    w.done = S.dalloc<int>(R, L);
+    w.nit = S.dalloc<int>(R, L);
+    w.flags = S.dalloc<int>(R, L);
+    w.op = S.dalloc<int>(R, L);
+    w.gauge = S.dalloc<int>(R, L);
+    w.target = S.dalloc<double>(R, L);
+    w.bnorm = S.dalloc<double>(R, L);
+    w.rnorm = S.dalloc<double>(R, L);
+    w.uLp = (const double**)S.dalloc<double*>(R, L);
+    w.uSp = (const double**)S.dalloc<double*>(R, L);
+    // tile lists sized for the worst case (every rhs its own op): units * R
+    const size_t tcap_strip = (size_t)(g.mx + 2) * R + 8;
+    const size_t tcap_pair = (size_t)(S.P + 2) * R + 8;
+    w.tG = S.dalloc<Tile>(tcap_strip, L);
+    w.tW = S.dalloc<Tile>(tcap_strip, L);
+    w.tA = S.dalloc<Tile>(tcap_strip, L);
+    w.tM = S.dalloc<Tile>(tcap_pair, L);
+    CK(cudaStreamSynchronize(S.stream));
+    S.wk_bytes = S.bytes - bytes_before;
+    S.Rcap = R;
+    S.cur_ops.clear();
+}
+
+static std::vector<Tile> make_tiles(const std::vector<int>& unit_cls, int ncls, const std::vector<int>& ops) {
+    std::vector<Tile> out;
+    const int R = (int)ops.size(), nu = (int)unit_cls.size();
+    int rb = 0;
+    while (rb < R) {
+        int re = rb;
+        while (re < R && ops[re] == ops[rb]) ++re;
+        int ub = 0;
+        while (ub < nu) {
+            int ue = ub;
+            while (ue < nu && unit_cls[ue] == unit_cls[ub]) ++ue;
+            for (int rr = rb; rr < re;) {
+                const int nr = std::min(kBN, re - rr);
+                const int upt = std::max(1, kBN / nr);
+                for (int u = ub; u < ue; u += upt)
+                    out.push_back(Tile{ops[rb] * ncls + unit_cls[ub], u, std::min(upt, ue - u), rr, nr});
+                rr += nr;
+            }
+            ub = ue;
+        }
+        rb = re;
+    }
+    return out;
+}
+
+static void prepare_ops(Solver& S, const std::vector<int>& ops) {
+    if (ops == S.cur_ops) return;
+    auto& w = S.wk;
+    const int R = (int)ops.size();
+    auto tS = make_tiles(S.strip_cls, 3, ops);
+    auto tM = make_tiles(S.pair_mc, S.nmc, ops);
+    CK(cudaMemcpyAsync(w.tG, tS.data(), tS.size() * sizeof(Tile), cudaMemcpyHostToDevice, S.stream));
+    CK(cudaMemcpyAsync(w.tW, tS.data(), tS.size() * sizeof(Tile), cudaMemcpyHostToDevice, S.stream));
+    CK(cudaMemcpyAsync(w.tA, tS.data(), tS.size() * sizeof(Tile), cudaMemcpyHostToDevice, S.stream));
+    CK(cudaMemcpyAsync(w.tM, tM.data(), tM.size() * sizeof(Tile), cudaMemcpyHostToDevice, S.stream));
+    w.ntG = w.ntW = w.ntA = (int)tS.size();
+    w.ntM = (int)tM.size();
+    std::vector<const double*> uLp(R, nullptr), uSp(R, nullptr);
+    std::vector<int> gauge(R, 0);
+    for (int r = 0; r < R; ++r)
+        if (ops[r] == S.singular_op) {
+            uLp[r] = S.uL;
+            uSp[r] = S.uS;
+            gauge[r] = 1;
+        }
+    CK(cudaMemcpyAsync(w.op, ops.data(), R * sizeof(int), cudaMemcpyHostToDevice, S.stream));
+    CK(cudaMemcpyAsync(w.gauge, gauge.data(), R * sizeof(int), cudaMemcpyHostToDevice, S.stream));
+    CK(cudaMemcpyAsync(w.uLp, uLp.data(), R * sizeof(double*), cudaMemcpyHostToDevice, S.stream));
+    CK(cudaMemcpyAsync(w.uSp, uSp.data(), R * sizeof(double*), cudaMemcpyHostToDevice, S.stream));
+    CK(cudaStreamSynchronize(S.stream));
+    S.cur_ops = ops;
+}
+
+// ---------------------------------------------------------------------------
+// Solve
+// ---------------------------------------------------------------------------
+
+static bool is_device_ptr(const void* p) {
+    if (!p) return false;
+    cudaPointerAttributes at;
+    cudaError_t e = cudaPointerGetAttributes(&at, p);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    return at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged;
+}
+
+static GemmArgs gemm_base(const Solver& S) {
+    GemmArgs a;
+    std::memset(&a, 0, sizeof(a));
+    (void)S;
+    return a;
+}
+
+static constexpr int kEventPairs = 8192;
+
+static void run_gemm(Solver& S, GemmArgs a, const Tile* tiles, int ntiles, int epi) {
+    const bool rec = S.prof && S.ev_used < kEventPairs;
+    if (S.prof) a.flops = S.d_flops;
+    if (rec) CK(cudaEventRecord(S.ev[2 * S.ev_used], S.stream));
+    launch_class_gemm(a, tiles, ntiles, epi, S.stream);
+    if (rec) {
+        CK(cudaEventRecord(S.ev[2 * S.ev_used + 1], S.stream));
+        ++S.ev_used;
+    }
+}
+
+// Accumulate the recorded GEMM launches (after the stream has drained).
+static void harvest_profile(Solver& S) {
+    if (!S.prof) return;
+    for (int i = 0; i < S.ev_used; ++i) {
+        float ms = 0.f;
+        CK(cudaEventElapsedTime(&ms, S.ev[2 * i], S.ev[2 * i + 1]));
+        S.prof_ms += ms;
+    }
+    S.prof_launches += S.ev_used;
+    S.ev_used = 0;
+    unsigned long long fl = 0;
+    CK(cudaMemcpy(&fl, S.d_flops, sizeof(fl), cudaMemcpyDeviceToHost));
+    S.prof_flops += (double)fl;
+    CK(cudaMemset(S.d_flops, 0, sizeof(fl)));
+}
+
+static int solve_impl(Solver& S, const std::vector<int>& ops, const double* f, const double* gb, double tol,
+                      double* u, smpm_stats* st) {
+    auto t0 = std::chrono::steady_clock::now();
+    const int R = (int)ops.size();
+    if (R <= 0) throw Err{SMPM_EINVAL, "nrhs must be positive"};
+    if (!(tol > 0.0)) throw Err{SMPM_EINVAL, "tol must be positive"};
+    if (!f || !u) throw Err{SMPM_EINVAL, "f and u must not be null"};
+    ensure_workspace(S, R);
+    prepare_ops(S, ops);
+    const Geometry& g = S.g;
+    auto& w = S.wk;
+    cudaStream_t st_ = S.stream;
+    const int fz = g.fz, n = g.n, nfz = n * fz, f2 = 2 * fz, f4 = 4 * fz, m = S.restart;
+    const long long ld = S.ld, nb = 2LL * fz + 2LL * g.nx;
+    const int nch = (int)((S.kp + kChunk - 1) / kChunk);
+    const int rch = (int)((g.r + kChunk - 1) / kChunk);
+
+    // inputs
+    const double* f_d = f;
+    if (!is_device_ptr(f)) {
+        CK(cudaMemcpyAsync(w.fstage, f, sizeof(double) * g.r * R, cudaMemcpyHostToDevice, st_));
+        f_d = w.fstage;
+    }
+    const double* g_d = gb;
+    if (gb && !is_device_ptr(gb)) {
+        CK(cudaMemcpyAsync(w.gstage, gb, sizeof(double) * nb * R, cudaMemcpyHostToDevice, st_));
+        g_d = w.gstage;
+    }
+    const bool u_dev = is_device_ptr(u);
+    double* u_d = u_dev ? u : w.ustage;
+
+    GridArgs ga;
+    ga.n = n; ga.N = g.N; ga.mx = g.mx; ga.mz = g.mz; ga.fz = fz; ga.nx = g.nx; ga.r = g.r;
+    ga.tau_x = g.tau_x; ga.tau_z = S.d_tau_z; ga.wq = S.d_wq; ga.hz = S.d_hz; ga.hx = g.hx; ga.area = g.lx * g.lz;
+
+    // Alg. seq steps 1-3
+    k_rhs_assemble(ga, R, f_d, g.r, g_d, nb, w.b, g.r, w.uLp, w.rpart, rch, kChunk, st_);
+    k_project(R, g.r, w.b, g.r, w.uLp, w.rpart, rch, kChunk, st_);
+    GemmArgs aW = gemm_base(S);
+    aW.mats = S.W; aW.mat_stride = S.sW; aW.M = f2; aW.K = nfz;
+    aW.row_lo = S.rl_GW; aW.row_hi = S.rh_GW;
+    aW.in = w.b; aW.in_rs = g.r; aW.in_us = nfz; aW.in_off = 0;
+    aW.out = w.bS; aW.out_rs = ld; aW.out_us = f2; aW.out_off0 = -fz; aW.out_off1 = f2; aW.msplit = fz;
+    run_gemm(S, aW, w.tW, w.ntW, 0);
+    k_dot_partial(R, S.kp, w.bS, ld, w.uSp, w.rpart, nch, kChunk, st_);
+    k_project(R, S.kp, w.bS, ld, w.uSp, w.rpart, nch, kChunk, st_);
+
+    KArgs ka;
+    std::memset(&ka, 0, sizeof(ka));
+    ka.R = R; ka.m = m; ka.nch = nch; ka.ch = kChunk; ka.ld = ld; ka.kp = S.kp;
+    ka.fz = fz; ka.mx = g.mx; ka.ng = g.ng; ka.d = g.d; ka.n = n;
+    ka.V = w.V; ka.w = w.w; ka.Hc = w.Hc; ka.htmp = w.htmp; ka.cs = w.cs; ka.sn = w.sn; ka.gv = w.gv;
+    ka.part1 = w.part1; ka.part2 = w.part2; ka.q = w.q; ka.c = w.c;
+    ka.rho = S.rho; ka.rho_stride = S.sRho; ka.K = S.K; ka.K_stride = S.sK;
+    ka.op = w.op; ka.strip_cls = S.d_strip_cls;
+    ka.active = w.active; ka.done = w.done; ka.nit = w.nit; ka.target = w.target;
+    ka.bnorm = w.bnorm; ka.rnorm = w.rnorm; ka.flags = w.flags;
+
+    // block-Jacobi apply: out = Minv_p in over pairs p (faces [(4p+1) fz, (4p+5) fz))
+    auto bj = [&](const double* in, long long in_rs, long long in_off, double* out, long long out_rs,
+                  long long out_off, const int* active) {
+        GemmArgs a = gemm_base(S);
+        a.mats = S.Minv; a.mat_stride = S.sM; a.M = f4; a.K = f4;
+        a.row_lo = S.rl_M; a.row_hi = S.rh_M;
+        a.in = in; a.in_rs = in_rs; a.in_us = f4; a.in_off = in_off + fz;
+        a.out = out; a.out_rs = out_rs; a.out_us = f4; a.out_off0 = out_off + fz; a.out_off1 = 0; a.msplit = f4;
+        a.active = active;
+        run_gemm(S, a, w.tM, w.ntM, 0);
+    };
+    // Schur product: out = in + sum_i scatter_i G_i gather_i in
+    auto schur = [&](const double* in, long long in_rs, long long in_off, double* out, const int* active) {
+        GemmArgs a = gemm_base(S);
+        a.mats = S.G; a.mat_stride = S.sG; a.M = f2; a.K = f2;
+        a.row_lo = S.rl_GW; a.row_hi = S.rh_GW;
+        a.in = in; a.in_rs = in_rs; a.in_us = f2; a.in_off = in_off;
+        a.out = out; a.out_rs = ld; a.out_us = f2; a.out_off0 = -fz; a.out_off1 = f2; a.msplit = fz;
+        a.add = in;  // identity term, same layout when in_rs == ld and in_off == 0
+        a.active = active;
+        run_gemm(S, a, w.tG, w.ntG, 1);
+    };
+
+    CK(cudaMemsetAsync(w.done, 0, R * sizeof(int), st_));
+    CK(cudaMemsetAsync(w.active, 0, R * sizeof(int), st_));
+    CK(cudaMemsetAsync(w.flags, 0, R * sizeof(int), st_));
+    CK(cudaMemsetAsync(w.nit, 0, R * sizeof(int), st_));
+    k_fill(w.xS, (long long)R * ld, 0.0, st_);
+
+    // Restart cycles as iterative refinement on x_S: every cycle starts from the
+    // true residual d = b_S - S x_S, runs deflated right-preconditioned GMRES on
+    // P S M^-1 y = P d, and adds dx = t + Z K Z^T (d - S t), t = M^-1 V y
+    // (= Q M^-1 y + Z C\ d of Eq. deflated_schur for this cycle's system).
+    std::vector<int> h_done(R), h_active(R), h_nit(R), h_flags(R);
+    int total_it = 0, cycles = 0, status = SMPM_OK;
+    bool first = true;
+    const int check_every = 4;
+    while (true) {
+        if (!first) schur(w.xS, ld, 0, w.s, nullptr);
+        k_residual(ka, w.bS, first ? nullptr : w.s, st_);
+        k_cycle_start(ka, w.c0, first ? 1 : 0, tol, st_);
+        CK(cudaMemcpyAsync(h_done.data(), w.done, R * sizeof(int), cudaMemcpyDeviceToHost, st_));
+        CK(cudaStreamSynchronize(st_));
+        bool all = true;
+        for (int r = 0; r < R; ++r) all &= h_done[r] != 0;
+        if (all) break;
+        if (total_it >= S.max_iter) { status = SMPM_ENOCONV; break; }
+        const int last_allowed = std::min(m, S.max_iter - total_it);
+        int j = 0;
+        for (; j < last_allowed; ++j) {
+            bj(w.V, (long long)(m + 1) * ld, (long long)j * ld, w.z, ld, 0, w.active);
+            schur(w.z, ld, 0, w.w, w.active);
+            k_deflate_sum(ka, w.w, nullptr, st_);
+            k_coarse(ka, st_);
+            k_cgs(ka, j, 0, st_);
+            k_cgs(ka, j, 1, st_);
+            k_cgs(ka, j, 2, st_);
+            k_normalize(ka, j, last_allowed, st_);
+            if ((j + 1) % check_every == 0 || j + 1 == last_allowed) {
+                CK(cudaMemcpyAsync(h_active.data(), w.active, R * sizeof(int), cudaMemcpyDeviceToHost, st_));
+                CK(cudaStreamSynchronize(st_));
+                bool any = false;
+                for (int r = 0; r < R; ++r) any |= h_active[r] != 0;
+                if (!any) { ++j; break; }
+            }
+        }
+        CK(cudaMemcpyAsync(h_nit.data(), w.nit, R * sizeof(int), cudaMemcpyDeviceToHost, st_));
+        k_cycle_update(ka, w.Xp, st_);                 // Y = V y
+        bj(w.Xp, ld, 0, w.t, ld, 0, nullptr);          // t = M^-1 Y
+        schur(w.t, ld, 0, w.s, nullptr);               // S t
+        k_deflate_coarse_pending(ka, w.s, st_);        // c = K Z^T S t
+        k_xs_update(ka, w.xS, w.t, w.c0, st_);         // x_S += t + Z (c0 - c)
+        CK(cudaStreamSynchronize(st_));
+        int mx_it = 0;
+        for (int r = 0; r < R; ++r) mx_it = std::max(mx_it, h_nit[r]);
+        total_it += std::max(mx_it, 1);
+        ++cycles;
+        first = false;
+    }
+    // recovery: u = A^-1 (b - E x_S)  (Alg. seq step 9)
+    k_recovery_rhs(ga, R, w.b, g.r, w.xS, ld, w.t2, st_);
+    {
+        GemmArgs a = gemm_base(S);
+        a.mats = S.Ainv; a.mat_stride = S.sA; a.M = nfz; a.K = nfz;
+        a.row_lo = S.rl_A; a.row_hi = S.rh_A;
+        a.in = w.t2; a.in_rs = g.r; a.in_us = nfz; a.in_off = 0;
+        a.out = u_d; a.out_rs = g.r; a.out_us = nfz; a.out_off0 = 0; a.out_off1 = 0; a.msplit = nfz;
+        run_gemm(S, a, w.tA, w.ntA, 0);
+    }
+    k_gauge(ga, R, u_d, g.r, w.gauge, w.rpart, rch, kChunk, st_);
+    if (!u_dev) CK(cudaMemcpyAsync(u, u_d, sizeof(double) * g.r * R, cudaMemcpyDeviceToHost, st_));
+    std::vector<double> h_r(R), h_b(R);
+    CK(cudaMemcpyAsync(h_r.data(), w.rnorm, R * sizeof(double), cudaMemcpyDeviceToHost, st_));
+    CK(cudaMemcpyAsync(h_b.data(), w.bnorm, R * sizeof(double), cudaMemcpyDeviceToHost, st_));
+    CK(cudaMemcpyAsync(h_flags.data(), w.flags, R * sizeof(int), cudaMemcpyDeviceToHost, st_));
+    CK(cudaStreamSynchronize(st_));
+    CK(cudaGetLastError());
+    harvest_profile(S);
+    double worst = 0.0;
+    for (int r = 0; r < R; ++r) {
+        const double rel = h_b[r] > 0 ? h_r[r] / h_b[r] : 0.0;
+        worst = std::max(worst, rel);
+        if (h_flags[r] & 1) status = SMPM_EBREAKDOWN;
+        if (!std::isfinite(rel)) status = SMPM_EBREAKDOWN;
+    }
+    S.last_res.assign(R, 0.0);
+    for (int r = 0; r < R; ++r) S.last_res[r] = h_b[r] > 0 ? h_r[r] / h_b[r] : 0.0;
+    if (st) {
+        st->iters = total_it;
+        st->restarts = std::max(0, cycles - 1);
+        st->status = status;
+        st->rel_resid_true = worst;
+        st->setup_ms = S.setup_ms;
+        st->solve_ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+    }
+    return status;
+}
+
+// One operator of the method applied to nrhs vectors (parity checks of the
+// individual kernels): kind 0: S x (Sec. 2.3); 1: M^-1 x (Sec. 3.2);
+// 2: P x = x - S Z K Z^T x (Sec. 3.3); 3: b_S = B A^-1 b (r -> k);
+// 4: A^-1 b per strip (r -> r).  Face vectors use the unpadded interface order
+// (2 j + s) fz + Z of length k.
+static int apply_impl(Solver& S, int kind, int R, const double* in, double* out) {
+    if (R <= 0 || !in || !out) throw Err{SMPM_EINVAL, "bad apply arguments"};
+    if (kind < 0 || kind > 4) throw Err{SMPM_EINVAL, "unknown operator kind"};
+    std::vector<int> ops(R, 0);
+    ensure_workspace(S, R);
+    prepare_ops(S, ops);
+    const Geometry& g = S.g;
+    auto& w = S.wk;
+    cudaStream_t st_ = S.stream;
+    const int fz = g.fz, nfz = g.n * fz, f2 = 2 * fz, f4 = 4 * fz;
+    const long long ld = S.ld, k = g.k, r = g.r;
+    const bool face_in = kind <= 2, face_out = kind <= 3;
+    const cudaMemcpyKind kin = is_device_ptr(in) ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
+    const cudaMemcpyKind kout = is_device_ptr(out) ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
+    if (face_in)
+        CK(cudaMemcpy2DAsync(w.z + fz, ld * 8, in, k * 8, k * 8, R, kin, st_));
+    else
+        CK(cudaMemcpyAsync(w.t2, in, sizeof(double) * r * R, kin, st_));
+    std::vector<int> ones(R, 1);
+    CK(cudaMemcpyAsync(w.active, ones.data(), R * sizeof(int), cudaMemcpyHostToDevice, st_));
+    double* res = w.w;
+    GemmArgs a;
+    std::memset(&a, 0, sizeof(a));
+    if (kind == 0) {
+        a.mats = S.G; a.mat_stride = S.sG; a.M = f2; a.K = f2; a.row_lo = S.rl_GW; a.row_hi = S.rh_GW;
+        a.in = w.z; a.in_rs = ld; a.in_us = f2; a.in_off = 0;
+        a.out = w.w; a.out_rs = ld; a.out_us = f2; a.out_off0 = -fz; a.out_off1 = f2; a.msplit = fz; a.add = w.z;
+        run_gemm(S, a, w.tG, w.ntG, 1);
+    } else if (kind == 1) {
+        a.mats = S.Minv; a.mat_stride = S.sM; a.M = f4; a.K = f4; a.row_lo = S.rl_M; a.row_hi = S.rh_M;
+        a.in = w.z; a.in_rs = ld; a.in_us = f4; a.in_off = fz;
+        a.out = w.w; a.out_rs = ld; a.out_us = f4; a.out_off0 = fz; a.msplit = f4;
+        run_gemm(S, a, w.tM, w.ntM, 0);
+    } else if (kind == 2) {
+        KArgs ka;
+        std::memset(&ka, 0, sizeof(ka));
+        const int m = S.restart;
+        ka.R = R; ka.m = m; ka.nch = (int)((S.kp + kChunk - 1) / kChunk); ka.ch = kChunk; ka.ld = ld; ka.kp = S.kp;
+        ka.fz = fz; ka.mx = g.mx; ka.ng = g.ng; ka.d = g.d; ka.n = g.n;
+        ka.V = w.V; ka.w = w.w; ka.Hc = w.Hc; ka.htmp = w.htmp; ka.cs = w.cs; ka.sn = w.sn; ka.gv = w.gv;
+        ka.part1 = w.part1; ka.part2 = w.part2; ka.q = w.q; ka.c = w.c;
+        ka.rho = S.rho; ka.rho_stride = S.sRho; ka.K = S.K; ka.K_stride = S.sK;
+        ka.op = w.op; ka.strip_cls = S.d_strip_cls;
+        ka.active = w.active; ka.done = w.done; ka.nit = w.nit; ka.target = w.target;
+        ka.bnorm = w.bnorm; ka.rnorm = w.rnorm; ka.flags = w.flags;
+        CK(cudaMemcpyAsync(w.w, w.z, sizeof(double) * ld * R, cudaMemcpyDeviceToDevice, st_));
+        k_deflate_sum(ka, w.w, nullptr, st_);
+        k_coarse(ka, st_);
+        k_cgs(ka, -1, 0, st_);  // w -= S Z c, no dot products
+    } else if (kind == 3) {
+        a.mats = S.W; a.mat_stride = S.sW; a.M = f2; a.K = nfz; a.row_lo = S.rl_GW; a.row_hi = S.rh_GW;
+        a.in = w.t2; a.in_rs = r; a.in_us = nfz; a.in_off = 0;
+        a.out = w.w; a.out_rs = ld; a.out_us = f2; a.out_off0 = -fz; a.out_off1 = f2; a.msplit = fz;
+        run_gemm(S, a, w.tW, w.ntW, 0);
+    } else {
+        a.mats = S.Ainv; a.mat_stride = S.sA; a.M = nfz; a.K = nfz; a.row_lo = S.rl_A; a.row_hi = S.rh_A;
+        a.in = w.t2; a.in_rs = r; a.in_us = nfz; a.in_off = 0;
+        a.out = w.b; a.out_rs = r; a.out_us = nfz; a.msplit = nfz;
+        run_gemm(S, a, w.tA, w.ntA, 0);
+        res = w.b;
+    }
+    if (face_out)
+        CK(cudaMemcpy2DAsync(out, k * 8, res + fz, ld * 8, k * 8, R, kout, st_));
+    else
+        CK(cudaMemcpyAsync(out, res, sizeof(double) * r * R, kout, st_));
+    CK(cudaStreamSynchronize(st_));
+    CK(cudaGetLastError());
+    harvest_profile(S);
+    return SMPM_OK;
+}
+
+static Solver* make_solver(const smpm_grid* grid, int nop, const double* k2, void* stream) {
+    if (!grid) throw Err{SMPM_EINVAL, "grid is null"};
+    if (nop < 1) throw Err{SMPM_EINVAL, "need at least one k^2"};
+    auto S = std::make_unique<Solver>();
+    S->opt = *grid;
+    std::string msg;
+    if (!make_geometry(grid->mx, grid->mz, grid->order, grid->lx, grid->lz, grid->z_ratio, grid->tau_scale,
+                       grid->deflation_groups, S->g, msg))
+        throw Err{SMPM_EINVAL, msg};
+    if (grid->precision != 0) throw Err{SMPM_EINVAL, "precision mode not supported by this entry point"};
+    S->nop = nop;
+    S->k2.assign(k2, k2 + nop);
+    int nzero = 0;
+    for (double v : S->k2) {
+        if (!(v >= 0.0) || !std::isfinite(v)) throw Err{SMPM_EINVAL, "k2 must be finite and >= 0"};
+        if (v == 0.0) ++nzero;
+    }
+    if (nzero > 1) throw Err{SMPM_EINVAL, "at most one k2 = 0 operator per handle"};
+    S->stream = (cudaStream_t)stream;
+    setup_solver(*S);
+    return S.release();
+}
+
+template <class F>
+static int guarded(F&& fn) {
+    try {
+        g_last_error.clear();
+        return fn();
+    } catch (const Err& e) {
+        g_last_error = e.msg;
+        return e.code;
+    } catch (const std::exception& e) {
+        g_last_error = e.what();
+        return SMPM_ECUDA;
+    } catch (...) {
+        g_last_error = "unknown error";
+        return SMPM_ECUDA;
+    }
+}
+
+}  // namespace smpm
+
+using namespace smpm;
+
+extern "C" {
+
+int smpm_setup(const smpm_grid* grid, double k2, void* stream, smpm_handle* out) {
+    return guarded([&] {
+        if (!out) throw Err{SMPM_EINVAL, "out is null"};
+        *out = (smpm_handle)make_solver(grid, 1, &k2, stream);
+        return SMPM_OK;
+    });
+}
+
+int smpm_setup_multi(const smpm_grid* grid, int nop, const double* k2, void* stream, smpm_handle* out) {
+    return guarded([&] {
+        if (!out || !k2) throw Err{SMPM_EINVAL, "null argument"};
+        *out = (smpm_handle)make_solver(grid, nop, k2, stream);
+        return SMPM_OK;
+    });
+}
+
+int smpm_solve(smpm_handle h, const double* f, const double* g, double tol, double* u, smpm_stats* st) {
+    return guarded([&] {
+        if (!h) throw Err{SMPM_EINVAL, "null handle"};
+        std::vector<int> ops(1, 0);
+        return solve_impl(*(Solver*)h, ops, f, g, tol, u, st);
+    });
+}
+
+int smpm_solve_batch(smpm_handle h, int nrhs, const double* f, const double* g, double tol, double* u,
+                     smpm_stats* st) {
+    return guarded([&] {
+        if (!h) throw Err{SMPM_EINVAL, "null handle"};
+        if (nrhs <= 0) throw Err{SMPM_EINVAL, "nrhs must be positive"};
+        std::vector<int> ops(nrhs, 0);
+        return solve_impl(*(Solver*)h, ops, f, g, tol, u, st);
+    });
+}
+
+int smpm_solve_multi(smpm_handle h, int nrhs, const int* op_of_rhs, const double* f, const double* g, double tol,
+                     double* u, smpm_stats* st) {
+    return guarded([&] {
+        if (!h || !op_of_rhs) throw Err{SMPM_EINVAL, "null argument"};
+        Solver& S = *(Solver*)h;
+        if (nrhs <= 0) throw Err{SMPM_EINVAL, "nrhs must be positive"};
+        std::vector<int> ops(op_of_rhs, op_of_rhs + nrhs);
+        for (int o : ops)
+            if (o < 0 || o >= S.nop) throw Err{SMPM_EINVAL, "operator index out of range"};
+        for (int r = 1; r < nrhs; ++r)
+            if (ops[r] < ops[r - 1]) throw Err{SMPM_EINVAL, "op_of_rhs must be non-decreasing"};
+        return solve_impl(S, ops, f, g, tol, u, st);
+    });
+}
+
+int smpm_apply(smpm_handle h, int kind, int nrhs, const double* in, double* out) {
+    return guarded([&] {
+        if (!h) throw Err{SMPM_EINVAL, "null handle"};
+        return apply_impl(*(Solver*)h, kind, nrhs, in, out);
+    });
+}
+
+int smpm_sizes(smpm_handle h, long long* r, long long* nb, long long* k) {
+    return guarded([&] {
+        if (!h) throw Err{SMPM_EINVAL, "null handle"};
+        const Solver& S = *(Solver*)h;
+        if (r) *r = S.g.r;
+        if (nb) *nb = 2LL * S.g.fz + 2LL * S.g.nx;
+        if (k) *k = S.g.k;
+        return SMPM_OK;
+    });
+}
+
+int smpm_node_coords(smpm_handle h, double* x, double* z) {
+    return guarded([&] {
+        if (!h || !x || !z) throw Err{SMPM_EINVAL, "null argument"};
+        const Geometry& g = ((Solver*)h)->g;
+        for (int X = 0; X < g.nx; ++X) {
+            const int ex = X / g.n, a = X % g.n;
+            const double xv = ex * g.hx + (g.xi[a] + 1.0) * g.hx * 0.5;
+            for (int Z = 0; Z < g.fz; ++Z) {
+                const int ez = Z / g.n, b = Z % g.n;
+                x[(size_t)X * g.fz + Z] = xv;
+                z[(size_t)X * g.fz + Z] = g.zb[ez] + (g.xi[b] + 1.0) * g.hz[ez] * 0.5;
+            }
+        }
+        return SMPM_OK;
+    });
+}
+
+int smpm_last_residuals(smpm_handle h, int n, double* out) {
+    return guarded([&] {
+        if (!h || !out) throw Err{SMPM_EINVAL, "null argument"};
+        const Solver& S = *(Solver*)h;
+        if (n > (int)S.last_res.size()) throw Err{SMPM_EINVAL, "more values requested than the last solve had"};
+        for (int i = 0; i < n; ++i) out[i] = S.last_res[i];
+        return SMPM_OK;
+    });
+}
+
+long long smpm_device_bytes(smpm_handle h) { return h ? ((Solver*)h)->bytes : 0; }
+
+void smpm_release(smpm_handle h) {
+    try {
+        delete (Solver*)h;
+    } catch (...) {
+    }
+}
+
+const char* smpm_last_error(void) { return g_last_error.c_str(); }
+
+int smpm_profile(smpm_handle h, int enable) {
+    return guarded([&] {
+        if (!h) throw Err{SMPM_EINVAL, "null handle"};
+        Solver& S = *(Solver*)h;
+        if (enable && S.ev.empty()) {
+            S.ev.resize(2 * kEventPairs);
+            for (auto& e : S.ev) CK(cudaEventCreate(&e));
+            S.d_flops = S.dalloc<unsigned long long>(1, S.allocs);
+            CK(cudaMemset(S.d_flops, 0, sizeof(unsigned long long)));
+        }
+        S.prof = enable != 0;
+        return SMPM_OK;
+    });
+}
+
+int smpm_profile_read(smpm_handle h, long long* launches, double* flops, double* ms, int reset) {
+    return guarded([&] {
+        if (!h) throw Err{SMPM_EINVAL, "null handle"};
+        Solver& S = *(Solver*)h;
+        if (launches) *launches = S.prof_launches;
+        if (flops) *flops = S.prof_flops;
+        if (ms) *ms = S.prof_ms;
+        if (reset) { S.prof_launches = 0; S.prof_flops = 0.0; S.prof_ms = 0.0; }
+        return SMPM_OK;
+    });
+}
+
+long long smpm_kernel_launches(void) { return launch_count(); }
+
+int smpm_probe_fp64(void* stream, double* tflops) {
+    return guarded([&] {
+        if (!tflops) throw Err{SMPM_EINVAL, "null argument"};
+        cudaStream_t s = (cudaStream_t)stream;
+        int dev = 0, sms = 0;
+        CK(cudaGetDevice(&dev));
+        CK(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+        double* out = nullptr;
+        CK(cudaMalloc(&out, sizeof(double) * 4096));
+        const int blocks = sms * 8, iters = 4096;
+        k_fp64_probe(out, blocks, 64, s);
+        cudaEvent_t e0, e1;
+        CK(cudaEventCreate(&e0));
+        CK(cudaEventCreate(&e1));
+        CK(cudaEventRecord(e0, s));
+        k_fp64_probe(out, blocks, iters, s);
+        CK(cudaEventRecord(e1, s));
+        CK(cudaEventSynchronize(e1));
+        float ms = 0.f;
+        CK(cudaEventElapsedTime(&ms, e0, e1));
+        cudaEventDestroy(e0);
+        cudaEventDestroy(e1);
+        cudaFree(out);
+        const double flops = 2.0 * 8.0 * 256.0 * (double)blocks * (double)iters;
+        *tflops = flops / (ms * 1e-3) / 1e12;
+        return SMPM_OK;
+    });
+}
+
+}  // extern "C"

@@ -1,0 +1,867 @@
+// Device kernels of libsmpm (FP64, sm_103a).
+//
+// Hot path of Alg. seq (Sec. 3): the Schur product S x = x + sum_i scatter_i(G_i gather_i x)
+// (Sec. 2.3 / 3.1, assembled form), the block-Jacobi apply M^-1 (Sec. 3.2), the
+// deflation Z^T, coarse solve and S Z c correction (Sec. 3.3), classical
+// Gram-Schmidt applied twice with Givens rotations (Arnoldi of GMRES), the
+// null-space projections (Eqs. regularize_poisson / regularize_schur) and the
+// strip solves A^-1 of the right-hand side and of the recovery step.
+//
+// FP64 arithmetic is bound by the DFMA pipe on this part, so the dense applies
+// are register-tiled SIMT GEMMs over tiles that share one class matrix; the
+// vector kernels are chunked streams over the face vectors.
+#include <atomic>
+#include <cmath>
+
+#include "kernels.h"
+
+namespace smpm {
+
+static std::atomic<long long> g_launches{0};
+long long launch_count() { return g_launches.load(); }
+void count_launches(int n) { g_launches.fetch_add(n); }
+
+#define CUDA_LAUNCH_CHECK() (void)0
+
+static constexpr int BM = 64, BN = 32, BK = 16, GT = 128;
+static constexpr int VB = 256;  // threads of the vector kernels
+
+__device__ __forceinline__ double warp_sum(double v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+
+// Sum over a block of VB threads; every thread gets the result.
+__device__ __forceinline__ double block_sum(double v, double* sh) {
+    v = warp_sum(v);
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    __syncthreads();
+    if (lane == 0) sh[wid] = v;
+    __syncthreads();
+    double t = lane < (VB / 32) ? sh[lane] : 0.0;
+    t = warp_sum(t);
+    return t;
+}
+
+// ---------------------------------------------------------------------------
+// Class GEMM: out[:, col] = Mat_{tile} * in[:, col] (+ add) over tiles of columns
+// sharing one class matrix.  Each thread owns a 4 x 4 block of a 64 x 32 tile.
+// ---------------------------------------------------------------------------
+template <int EPI>
+__global__ void __launch_bounds__(GT) class_gemm_kernel(GemmArgs a, const Tile* __restrict__ tiles) {
+    const Tile t = tiles[blockIdx.x];
+    const int row0 = blockIdx.y * BM;
+    const int lo = a.row_lo[t.mat], hi = a.row_hi[t.mat];
+    if (row0 >= hi || row0 + BM <= lo) return;
+    if (a.active) {
+        int any = 0;
+        for (int c = 0; c < t.nr; ++c) any |= a.active[t.r0 + c];
+        if (!any) return;
+    }
+    const int ncol = t.nu * t.nr;
+    if (a.flops && threadIdx.x == 0) {
+        int cols = 0;
+        for (int c = 0; c < ncol; ++c) cols += (a.active == nullptr || a.active[t.r0 + c % t.nr]) ? 1 : 0;
+        const int r_lo = max(lo, row0), r_hi = min(min(hi, row0 + BM), a.M);
+        atomicAdd(a.flops, 2ULL * (unsigned long long)max(0, r_hi - r_lo) * (unsigned long long)a.K *
+                               (unsigned long long)cols);
+    }
+    __shared__ double As[BK][BM + 1];
+    __shared__ double Bs[BK][BN + 1];
+    const double* __restrict__ A = a.mats + (long long)t.mat * a.mat_stride;
+    const int tid = threadIdx.x;
+    const int tr = tid >> 3, tc = tid & 7;
+    double acc[4][4];
+#pragma unroll
+    for (int i = 0; i < 4; ++i)
+#pragma unroll
+        for (int j = 0; j < 4; ++j) acc[i][j] = 0.0;
+
+    // per-thread column pointers for the B-tile loads (4 loads per thread)
+    const double* colp[(BN * BK) / GT];
+#pragma unroll
+    for (int l = 0; l < (BN * BK) / GT; ++l) {
+        const int e = tid + l * GT, c = e >> 4;
+        colp[l] = nullptr;
+        if (c < ncol) {
+            const int u = t.u0 + c / t.nr, r = t.r0 + c % t.nr;
+            colp[l] = a.in + (long long)r * a.in_rs + (long long)u * a.in_us + a.in_off;
+        }
+    }
+    for (int k0 = 0; k0 < a.K; k0 += BK) {
+#pragma unroll
+        for (int l = 0; l < (BM * BK) / GT; ++l) {
+            const int e = tid + l * GT, i = e >> 4, kk = e & 15;
+            const int row = row0 + i, k = k0 + kk;
+            As[kk][i] = (row < a.M && k < a.K) ? A[(long long)row * a.K + k] : 0.0;
+        }
+#pragma unroll
+        for (int l = 0; l < (BN * BK) / GT; ++l) {
+            const int e = tid + l * GT, c = e >> 4, kk = e & 15;
+            const int k = k0 + kk;
+            Bs[kk][c] = (colp[l] != nullptr && k < a.K) ? colp[l][k] : 0.0;
+        }
+        __syncthreads();
+#pragma unroll
+        for (int kk = 0; kk < BK; ++kk) {
+            double av[4], bv[4];
+#pragma unroll
+            for (int i = 0; i < 4; ++i) av[i] = As[kk][tr * 4 + i];
+#pragma unroll
+            for (int j = 0; j < 4; ++j) bv[j] = Bs[kk][tc * 4 + j];
+#pragma unroll
+            for (int i = 0; i < 4; ++i)
+#pragma unroll
+                for (int j = 0; j < 4; ++j) acc[i][j] = fma(av[i], bv[j], acc[i][j]);
+        }
+        __syncthreads();
+    }
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+        const int c = tc * 4 + j;
+        if (c >= ncol) continue;
+        const int u = t.u0 + c / t.nr, r = t.r0 + c % t.nr;
+        if (a.active && !a.active[r]) continue;
+        const long long base = (long long)r * a.out_rs + (long long)u * a.out_us;
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+            const int row = row0 + tr * 4 + i;
+            if (row < lo || row >= hi || row >= a.M) continue;
+            const long long addr = base + (row < a.msplit ? a.out_off0 + row : a.out_off1 + (row - a.msplit));
+            double v = acc[i][j];
+            if (EPI == 1) v += a.add[addr];
+            a.out[addr] = v;
+        }
+    }
+}
+
+void launch_class_gemm(const GemmArgs& a, const Tile* d_tiles, int ntiles, int epi, void* stream) {
+    if (ntiles <= 0) return;
+    dim3 grid(ntiles, (a.M + BM - 1) / BM);
+    cudaStream_t s = (cudaStream_t)stream;
+    if (epi == 1)
+        class_gemm_kernel<1><<<grid, GT, 0, s>>>(a, d_tiles);
+    else
+        class_gemm_kernel<0><<<grid, GT, 0, s>>>(a, d_tiles);
+    count_launches(1);
+}
+
+// ---------------------------------------------------------------------------
+// Deflation (Sec. 3.3)
+// ---------------------------------------------------------------------------
+
+// gate: 0 -> rhs running Arnoldi (active), 1 -> rhs not yet converged
+__device__ __forceinline__ bool gate_ok(const KArgs& a, int r, int gate) {
+    return gate == 0 ? a.active[r] != 0 : a.done[r] == 0;
+}
+
+__global__ void deflate_sum_kernel(KArgs a, const double* __restrict__ v, const double* __restrict__ vsub,
+                                   int gate) {
+    const int r = blockIdx.y;
+    if (!gate_ok(a, r, gate)) return;
+    const int wg = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
+    if (wg >= a.d) return;
+    const int t = wg / a.ng, gi = wg % a.ng, gs = a.fz / a.ng;
+    const long long off = (long long)r * a.ld + (long long)(2 * t + 1) * a.fz + (long long)gi * gs;
+    double s = 0.0;
+    for (int z = lane; z < gs; z += 32) {
+        double x = v[off + z] + v[off + a.fz + z];
+        if (vsub) x -= vsub[off + z] + vsub[off + a.fz + z];
+        s += x;
+    }
+    s = warp_sum(s);
+    if (lane == 0) a.q[(long long)r * a.d + wg] = s;
+}
+
+static void deflate_sum_gate(const KArgs& a, const double* v, const double* vsub, int gate, cudaStream_t s) {
+    dim3 grid((a.d * 32 + VB - 1) / VB, a.R);
+    deflate_sum_kernel<<<grid, VB, 0, s>>>(a, v, vsub, gate);
+    count_launches(1);
+}
+
+void k_deflate_sum(const KArgs& a, const double* v, const double* vsub, cudaStream_t s) {
+    deflate_sum_gate(a, v, vsub, 0, s);
+}
+
+__global__ void coarse_kernel(KArgs a, int gate) {
+    const int r = blockIdx.y;
+    if (!gate_ok(a, r, gate)) return;
+    const int i = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
+    if (i >= a.d) return;
+    const double* K = a.K + (long long)a.op[r] * a.K_stride + (long long)i * a.d;
+    const double* q = a.q + (long long)r * a.d;
+    double s = 0.0;
+    for (int j = lane; j < a.d; j += 32) s = fma(K[j], q[j], s);
+    s = warp_sum(s);
+    if (lane == 0) a.c[(long long)r * a.d + i] = s;
+}
+
+void k_coarse(const KArgs& a, cudaStream_t s) {
+    dim3 grid((a.d * 32 + VB - 1) / VB, a.R);
+    coarse_kernel<<<grid, VB, 0, s>>>(a, 0);
+    count_launches(1);
+}
+static void k_coarse_gate(const KArgs& a, int gate, cudaStream_t s) {
+    dim3 grid((a.d * 32 + VB - 1) / VB, a.R);
+    coarse_kernel<<<grid, VB, 0, s>>>(a, gate);
+    count_launches(1);
+}
+
+// (S Z c) at face-vector position e (Sec. 3.3): Z c is c_{t,g} on both faces of
+// interface t; S adds the G row-sums rho of the two strips that touch it.
+__device__ __forceinline__ double szc_at(const KArgs& a, int r, long long e) {
+    const int fz = a.fz;
+    const int F = (int)(e / fz), Z = (int)(e - (long long)F * fz);
+    if (F == 0 || F >= 2 * a.mx - 1) return 0.0;
+    const int i = F >> 1, s = F & 1, ng = a.ng, gs = fz / ng;
+    const double* c = a.c + (long long)r * a.d;
+    const double* rho = a.rho + (long long)a.op[r] * a.rho_stride;
+    const long long fz2 = 2LL * fz;
+    double val;
+    if (s == 1) {  // east face of strip i, interface t = i; strip i+1's west output half
+        const int t = i, cl = a.strip_cls[i + 1];
+        val = c[t * ng + Z / gs];
+        const double* rL = rho + (long long)(cl * 2 + 0) * ng * fz2;
+        const double* rR = rho + (long long)(cl * 2 + 1) * ng * fz2;
+        const bool has_next = (t + 1) <= a.mx - 2;
+        for (int gg = 0; gg < ng; ++gg) {
+            val = fma(c[t * ng + gg], rL[gg * fz2 + Z], val);
+            if (has_next) val = fma(c[(t + 1) * ng + gg], rR[gg * fz2 + Z], val);
+        }
+    } else {       // west face of strip i, interface t = i-1; strip i-1's east output half
+        const int t = i - 1, cl = a.strip_cls[i - 1];
+        val = c[t * ng + Z / gs];
+        const double* rL = rho + (long long)(cl * 2 + 0) * ng * fz2 + fz;
+        const double* rR = rho + (long long)(cl * 2 + 1) * ng * fz2 + fz;
+        const bool has_prev = t >= 1;
+        for (int gg = 0; gg < ng; ++gg) {
+            if (has_prev) val = fma(c[(t - 1) * ng + gg], rL[gg * fz2 + Z], val);
+            val = fma(c[t * ng + gg], rR[gg * fz2 + Z], val);
+        }
+    }
+    return val;
+}
+
+// Z c at position e (prolongation of the coarse vector).
+__device__ __forceinline__ double zc_at(const KArgs& a, int r, long long e) {
+    const int fz = a.fz;
+    const int F = (int)(e / fz), Z = (int)(e - (long long)F * fz);
+    if (F == 0 || F >= 2 * a.mx - 1) return 0.0;
+    const int t = (F - 1) >> 1, gs = fz / a.ng;
+    return a.c[(long long)r * a.d + t * a.ng + Z / gs];
+}
+
+// ---------------------------------------------------------------------------
+// CGS2 Arnoldi step (Sec. 3.1 orthogonalisation; CGS applied twice)
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(VB) cgs_kernel(KArgs a, int j, int mode) {
+    const int r = blockIdx.y;
+    if (!a.active[r]) return;
+    extern __shared__ double sm[];
+    double* wsh = sm;                 // [ch]
+    double* hsh = sm + a.ch;          // [m+2]
+    double* red = hsh + (a.m + 2);    // [32]
+    const long long e0 = (long long)blockIdx.x * a.ch;
+    const long long e1 = min(e0 + (long long)a.ch, a.kp);
+    const int len = (int)(e1 - e0);
+    double* w = a.w + (long long)r * a.ld;
+    const double* Vr = a.V + (long long)r * (a.m + 1) * a.ld;
+    const int nv = j + 1;
+    const long long pstride = (long long)a.nch * (a.m + 2);
+    if (mode == 0) {
+        for (int e = threadIdx.x; e < len; e += VB) {
+            double x = w[e0 + e] - szc_at(a, r, e0 + e);
+            wsh[e] = x;
+            w[e0 + e] = x;
+        }
+    } else {
+        const double* pin = (mode == 1 ? a.part1 : a.part2) + (long long)r * pstride;
+        for (int i = threadIdx.x; i < nv; i += VB) {
+            double s = 0.0;
+            for (int ch = 0; ch < a.nch; ++ch) s += pin[(long long)ch * (a.m + 2) + i];
+            hsh[i] = s;
+        }
+        __syncthreads();
+        for (int e = threadIdx.x; e < len; e += VB) {
+            double x = w[e0 + e];
+            for (int i = 0; i < nv; ++i) x = fma(-Vr[(long long)i * a.ld + e0 + e], hsh[i], x);
+            wsh[e] = x;
+            w[e0 + e] = x;
+        }
+        if (blockIdx.x == 0) {
+            if (mode == 1)
+                for (int i = threadIdx.x; i < nv; i += VB) a.htmp[(long long)r * (a.m + 1) + i] = hsh[i];
+            else
+                for (int i = threadIdx.x; i < nv; i += VB)
+                    a.Hc[((long long)r * a.m + j) * (a.m + 1) + i] = a.htmp[(long long)r * (a.m + 1) + i] + hsh[i];
+        }
+    }
+    __syncthreads();
+    if (mode <= 1) {
+        double* pout = (mode == 0 ? a.part1 : a.part2) + (long long)r * pstride + (long long)blockIdx.x * (a.m + 2);
+        const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+        for (int i = wid; i < nv; i += VB / 32) {
+            const double* vi = Vr + (long long)i * a.ld + e0;
+            double s = 0.0;
+            for (int e = lane; e < len; e += 32) s = fma(vi[e], wsh[e], s);
+            s = warp_sum(s);
+            if (lane == 0) pout[i] = s;
+        }
+    } else {
+        double s = 0.0;
+        for (int e = threadIdx.x; e < len; e += VB) s = fma(wsh[e], wsh[e], s);
+        s = block_sum(s, red);
+        if (threadIdx.x == 0) a.part1[(long long)r * pstride + (long long)blockIdx.x * (a.m + 2)] = s;
+    }
+}
+
+void k_cgs(const KArgs& a, int j, int mode, cudaStream_t s) {
+    dim3 grid(a.nch, a.R);
+    size_t sh = (size_t)(a.ch + a.m + 2 + 32) * sizeof(double);
+    cgs_kernel<<<grid, VB, sh, s>>>(a, j, mode);
+    count_launches(1);
+}
+
+__device__ double reduce_part(const KArgs& a, int r, int slot, double* red) {
+    const long long pstride = (long long)a.nch * (a.m + 2);
+    const double* p = a.part1 + (long long)r * pstride;
+    double s = 0.0;
+    for (int ch = threadIdx.x; ch < a.nch; ch += VB) s += p[(long long)ch * (a.m + 2) + slot];
+    return block_sum(s, red);
+}
+
+__global__ void __launch_bounds__(VB) normalize_kernel(KArgs a, int j, int last_allowed) {
+    const int r = blockIdx.y;
+    if (!a.active[r]) return;
+    __shared__ double red[32];
+    const double beta = sqrt(reduce_part(a, r, 0, red));
+    const bool bad = !(beta > 1e-300) || !isfinite(beta);
+    const long long e0 = (long long)blockIdx.x * a.ch;
+    const long long e1 = min(e0 + (long long)a.ch, a.kp);
+    const double* w = a.w + (long long)r * a.ld;
+    double* vn = a.V + ((long long)r * (a.m + 1) + (j + 1)) * a.ld;
+    const double inv = bad ? 0.0 : 1.0 / beta;
+    for (long long e = e0 + threadIdx.x; e < e1; e += VB) vn[e] = w[e] * inv;
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+        double* h = a.Hc + ((long long)r * a.m + j) * (a.m + 1);
+        double* cs = a.cs + (long long)r * a.m;
+        double* sn = a.sn + (long long)r * a.m;
+        double* g = a.gv + (long long)r * (a.m + 1);
+        h[j + 1] = isfinite(beta) ? beta : 0.0;
+        for (int i = 0; i < j; ++i) {
+            const double t = cs[i] * h[i] + sn[i] * h[i + 1];
+            h[i + 1] = -sn[i] * h[i] + cs[i] * h[i + 1];
+            h[i] = t;
+        }
+        const double rho = hypot(h[j], h[j + 1]);
+        double c = 1.0, s = 0.0;
+        if (rho > 0.0) { c = h[j] / rho; s = h[j + 1] / rho; }
+        h[j] = rho;
+        h[j + 1] = 0.0;
+        cs[j] = c;
+        sn[j] = s;
+        g[j + 1] = -s * g[j];
+        g[j] = c * g[j];
+        a.nit[r] = j + 1;
+        const bool nonfinite = !isfinite(g[j + 1]) || !isfinite(rho);
+        if (nonfinite || !(rho > 0.0)) a.flags[r] |= 1;
+        if (nonfinite || !(rho > 0.0) || fabs(g[j + 1]) <= a.target[r] || j + 1 >= last_allowed || bad)
+            a.active[r] = 0;
+    }
+}
+
+void k_normalize(const KArgs& a, int j, int last_allowed, cudaStream_t s) {
+    dim3 grid(a.nch, a.R);
+    normalize_kernel<<<grid, VB, 0, s>>>(a, j, last_allowed);
+    count_launches(1);
+}
+
+// Residual at the start of a restart cycle: r = (bS - s) - S Z c, c = K Z^T (bS - s).
+__global__ void __launch_bounds__(VB) residual_kernel(KArgs a, const double* __restrict__ bS,
+                                                     const double* __restrict__ sv) {
+    const int r = blockIdx.y;
+    if (a.done[r]) return;
+    __shared__ double red[32];
+    const long long e0 = (long long)blockIdx.x * a.ch;
+    const long long e1 = min(e0 + (long long)a.ch, a.kp);
+    const double* b = bS + (long long)r * a.ld;
+    const double* sr = sv ? sv + (long long)r * a.ld : nullptr;
+    double* v0 = a.V + (long long)r * (a.m + 1) * a.ld;
+    double s2 = 0.0, b2 = 0.0, d2 = 0.0;
+    for (long long e = e0 + threadIdx.x; e < e1; e += VB) {
+        const double bb = b[e];
+        const double dd = bb - (sr ? sr[e] : 0.0);      // true residual b_S - S x_S
+        const double x = dd - szc_at(a, r, e);          // deflated residual P d
+        v0[e] = x;
+        s2 = fma(x, x, s2);
+        b2 = fma(bb, bb, b2);
+        d2 = fma(dd, dd, d2);
+    }
+    s2 = block_sum(s2, red);
+    b2 = block_sum(b2, red);
+    d2 = block_sum(d2, red);
+    if (threadIdx.x == 0) {
+        const long long pstride = (long long)a.nch * (a.m + 2);
+        double* p = a.part1 + (long long)r * pstride + (long long)blockIdx.x * (a.m + 2);
+        p[0] = s2;
+        p[1] = b2;
+        p[2] = d2;
+    }
+}
+
+void k_residual(const KArgs& a, const double* bS, const double* sv, cudaStream_t s) {
+    deflate_sum_gate(a, bS, sv, 1, s);  // q = Z^T (bS - s) for every unconverged rhs
+    k_coarse_gate(a, 1, s);
+    dim3 grid(a.nch, a.R);
+    residual_kernel<<<grid, VB, 0, s>>>(a, bS, sv);
+    count_launches(1);
+}
+
+__global__ void __launch_bounds__(VB) cycle_start_kernel(KArgs a, double* __restrict__ c0, int stamp, double tol) {
+    const int r = blockIdx.y;
+    if (a.done[r]) return;
+    __shared__ double red[32];
+    const double beta = sqrt(reduce_part(a, r, 0, red));   // ||P d||: GMRES starting residual
+    const double bn = sqrt(reduce_part(a, r, 1, red));     // ||b_S||
+    const double dn = sqrt(reduce_part(a, r, 2, red));     // ||b_S - S x_S||: true residual
+    const double target = (stamp == 1) ? tol * bn : a.target[r];
+    const bool conv = (dn <= target) || !(bn > 0.0);
+    const bool bad = !isfinite(beta) || !isfinite(dn);
+    const bool lucky = !(beta > 0.0);                      // P d = 0: nothing left for GMRES
+    const long long e0 = (long long)blockIdx.x * a.ch;
+    const long long e1 = min(e0 + (long long)a.ch, a.kp);
+    if (!(conv || bad || lucky)) {
+        double* v0 = a.V + (long long)r * (a.m + 1) * a.ld;
+        const double inv = 1.0 / beta;
+        for (long long e = e0 + threadIdx.x; e < e1; e += VB) v0[e] *= inv;
+    }
+    if (blockIdx.x == 0) {
+        for (int i = threadIdx.x; i < a.d; i += VB) c0[(long long)r * a.d + i] = a.c[(long long)r * a.d + i];
+        if (threadIdx.x == 0) {
+            if (stamp == 1) { a.target[r] = target; a.bnorm[r] = bn; }
+            a.rnorm[r] = dn;
+            a.nit[r] = 0;
+            if (bad) a.flags[r] |= 1;
+            if (conv || bad) {
+                a.active[r] = 0;
+            } else {
+                double* g = a.gv + (long long)r * (a.m + 1);
+                g[0] = beta;
+                for (int i = 1; i <= a.m; ++i) g[i] = 0.0;
+                a.active[r] = lucky ? 0 : 1;
+            }
+        }
+    }
+}
+
+__global__ void commit_kernel(KArgs a, int stamp) {
+    const int r = blockIdx.x * blockDim.x + threadIdx.x;
+    if (r >= a.R || a.done[r]) return;
+    if (!a.active[r] && a.nit[r] == 0) a.done[r] = stamp;  // converged (or failed) at this cycle start
+}
+
+void k_cycle_start(const KArgs& a, double* c0, int first, double tol, cudaStream_t s) {
+    dim3 grid(a.nch, a.R);
+    // stamp == 1 marks the first cycle (targets are set from ||b_S||)
+    cycle_start_kernel<<<grid, VB, 0, s>>>(a, c0, first ? 1 : 2, tol);
+    count_launches(1);
+    commit_kernel<<<(a.R + 127) / 128, 128, 0, s>>>(a, 1);
+    count_launches(1);
+}
+
+// End of a cycle: x_S += t + Z (c0 - c), with t = M^-1 V y, c0 = K Z^T d from the
+// cycle start and c = K Z^T S t (Q M^-1 y + Z C\ d restricted to this cycle).
+__global__ void __launch_bounds__(VB) xs_update_kernel(KArgs a, double* __restrict__ xS, const double* __restrict__ t,
+                                                      const double* __restrict__ c0) {
+    const int r = blockIdx.y;
+    if (a.done[r] || a.nit[r] <= 0) return;
+    const long long e0 = (long long)blockIdx.x * a.ch;
+    const long long e1 = min(e0 + (long long)a.ch, a.kp);
+    const int fz = a.fz, gs = fz / a.ng;
+    double* x = xS + (long long)r * a.ld;
+    const double* tr = t + (long long)r * a.ld;
+    for (long long e = e0 + threadIdx.x; e < e1; e += VB) {
+        const int F = (int)(e / fz), Z = (int)(e - (long long)F * fz);
+        double v = tr[e];
+        if (F > 0 && F < 2 * a.mx - 1) {
+            const long long ci = (long long)r * a.d + ((F - 1) >> 1) * a.ng + Z / gs;
+            v += c0[ci] - a.c[ci];
+        }
+        x[e] += v;
+    }
+}
+
+void k_xs_update(const KArgs& a, double* xS, const double* t, const double* c0, cudaStream_t s) {
+    dim3 grid(a.nch, a.R);
+    xs_update_kernel<<<grid, VB, 0, s>>>(a, xS, t, c0);
+    count_launches(1);
+}
+
+void k_deflate_coarse_pending(const KArgs& a, const double* v, cudaStream_t s) {
+    deflate_sum_gate(a, v, nullptr, 1, s);
+    k_coarse_gate(a, 1, s);
+}
+
+__global__ void __launch_bounds__(VB) cycle_update_kernel(KArgs a, double* __restrict__ Xp) {
+    const int r = blockIdx.y;
+    if (a.done[r]) return;
+    const int ni = a.nit[r];
+    if (ni <= 0) return;
+    extern __shared__ double y[];
+    if (threadIdx.x == 0) {
+        const double* g = a.gv + (long long)r * (a.m + 1);
+        for (int i = ni - 1; i >= 0; --i) {
+            double s = g[i];
+            for (int l = i + 1; l < ni; ++l) s -= a.Hc[((long long)r * a.m + l) * (a.m + 1) + i] * y[l];
+            const double d = a.Hc[((long long)r * a.m + i) * (a.m + 1) + i];
+            y[i] = d != 0.0 ? s / d : 0.0;
+        }
+    }
+    __syncthreads();
+    const long long e0 = (long long)blockIdx.x * a.ch;
+    const long long e1 = min(e0 + (long long)a.ch, a.kp);
+    const double* Vr = a.V + (long long)r * (a.m + 1) * a.ld;
+    double* x = Xp + (long long)r * a.ld;
+    for (long long e = e0 + threadIdx.x; e < e1; e += VB) {
+        double s = 0.0;
+        for (int i = 0; i < ni; ++i) s = fma(y[i], Vr[(long long)i * a.ld + e], s);
+        x[e] = s;
+    }
+}
+
+void k_cycle_update(const KArgs& a, double* Xp, cudaStream_t s) {
+    dim3 grid(a.nch, a.R);
+    cycle_update_kernel<<<grid, VB, (size_t)(a.m + 1) * sizeof(double), s>>>(a, Xp);
+    count_launches(1);
+}
+
+// ---------------------------------------------------------------------------
+// Full-grid kernels: RHS assembly, projections, recovery input, gauge
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(VB) rhs_assemble_kernel(GridArgs g, const double* __restrict__ f, long long f_ld,
+                                                         const double* __restrict__ gb, long long g_ld,
+                                                         double* __restrict__ b, long long b_ld,
+                                                         const double* const* __restrict__ uL,
+                                                         double* __restrict__ part, int nch, int ch) {
+    const int r = blockIdx.y;
+    __shared__ double red[32];
+    const long long e0 = (long long)blockIdx.x * ch;
+    const long long e1 = min(e0 + (long long)ch, g.r);
+    const double* u = uL ? uL[r] : nullptr;
+    const double* gr = gb ? gb + (long long)r * g_ld : nullptr;
+    double s = 0.0;
+    for (long long e = e0 + threadIdx.x; e < e1; e += VB) {
+        double v = f[(long long)r * f_ld + e];
+        if (gr) {
+            const int X = (int)(e / g.fz), Z = (int)(e - (long long)X * g.fz);
+            if (X == 0) v += g.tau_x * gr[Z];
+            if (X == g.nx - 1) v += g.tau_x * gr[g.fz + Z];
+            if (Z == 0) v += g.tau_z[0] * gr[2 * g.fz + X];
+            if (Z == g.fz - 1) v += g.tau_z[g.mz - 1] * gr[2 * g.fz + g.nx + X];
+        }
+        b[(long long)r * b_ld + e] = v;
+        if (u) s = fma(u[e], v, s);
+    }
+    if (u) {
+        s = block_sum(s, red);
+        if (threadIdx.x == 0) part[(long long)r * nch + blockIdx.x] = s;
+    }
+}
+
+void k_rhs_assemble(const GridArgs& g, int R, const double* f, long long f_ld, const double* gb,
+                    long long g_ld, double* b, long long b_ld, const double* const* uL,
+                    double* part, int nch, int ch, cudaStream_t s) {
+    dim3 grid(nch, R);
+    rhs_assemble_kernel<<<grid, VB, 0, s>>>(g, f, f_ld, gb, g_ld, b, b_ld, uL, part, nch, ch);
+    count_launches(1);
+}
+
+__global__ void __launch_bounds__(VB) dot_partial_kernel(long long len, const double* __restrict__ v, long long v_ld,
+                                                        const double* const* __restrict__ u,
+                                                        double* __restrict__ part, int nch, int ch) {
+    const int r = blockIdx.y;
+    const double* ur = u[r];
+    if (!ur) return;
+    __shared__ double red[32];
+    const long long e0 = (long long)blockIdx.x * ch;
+    const long long e1 = min(e0 + (long long)ch, len);
+    double s = 0.0;
+    for (long long e = e0 + threadIdx.x; e < e1; e += VB) s = fma(ur[e], v[(long long)r * v_ld + e], s);
+    s = block_sum(s, red);
+    if (threadIdx.x == 0) part[(long long)r * nch + blockIdx.x] = s;
+}
+
+void k_dot_partial(int R, long long len, const double* v, long long v_ld, const double* const* u,
+                   double* part, int nch, int ch, cudaStream_t s) {
+    dim3 grid(nch, R);
+    dot_partial_kernel<<<grid, VB, 0, s>>>(len, v, v_ld, u, part, nch, ch);
+    count_launches(1);
+}
+
+__global__ void __launch_bounds__(VB) project_kernel(long long len, double* __restrict__ v, long long v_ld,
+                                                    const double* const* __restrict__ u,
+                                                    const double* __restrict__ part, int nch, int ch) {
+    const int r = blockIdx.y;
+    const double* ur = u[r];
+    if (!ur) return;
+    __shared__ double red[32];
+    double s = 0.0;
+    for (int c = threadIdx.x; c < nch; c += VB) s += part[(long long)r * nch + c];
+    s = block_sum(s, red);
+    const long long e0 = (long long)blockIdx.x * ch;
+    const long long e1 = min(e0 + (long long)ch, len);
+    for (long long e = e0 + threadIdx.x; e < e1; e += VB) v[(long long)r * v_ld + e] -= s * ur[e];
+}
+
+void k_project(int R, long long len, double* v, long long v_ld, const double* const* u,
+               const double* part, int nch, int ch, cudaStream_t s) {
+    dim3 grid(nch, R);
+    project_kernel<<<grid, VB, 0, s>>>(len, v, v_ld, u, part, nch, ch);
+    count_launches(1);
+}
+
+__global__ void __launch_bounds__(VB) recovery_rhs_kernel(GridArgs g, const double* __restrict__ b, long long b_ld,
+                                                         const double* __restrict__ xS, long long x_ld,
+                                                         double* __restrict__ t2) {
+    const int r = blockIdx.y;
+    const long long e = (long long)blockIdx.x * VB + threadIdx.x;
+    if (e >= g.r) return;
+    const int X = (int)(e / g.fz), Z = (int)(e - (long long)X * g.fz);
+    const int i = X / g.n, a = X - i * g.n;
+    double v = b[(long long)r * b_ld + e];
+    if (a == 0) v -= xS[(long long)r * x_ld + (long long)(2 * i) * g.fz + Z];
+    if (a == g.N) v -= xS[(long long)r * x_ld + (long long)(2 * i + 1) * g.fz + Z];
+    t2[(long long)r * g.r + e] = v;
+}
+
+void k_recovery_rhs(const GridArgs& g, int R, const double* b, long long b_ld, const double* xS,
+                    long long x_ld, double* t2, cudaStream_t s) {
+    dim3 grid((unsigned)((g.r + VB - 1) / VB), R);
+    recovery_rhs_kernel<<<grid, VB, 0, s>>>(g, b, b_ld, xS, x_ld, t2);
+    count_launches(1);
+}
+
+__global__ void __launch_bounds__(VB) gauge_partial_kernel(GridArgs g, const double* __restrict__ u, long long u_ld,
+                                                          const int* __restrict__ apply,
+                                                          double* __restrict__ part, int nch, int ch) {
+    const int r = blockIdx.y;
+    if (!apply[r]) return;
+    __shared__ double red[32];
+    const long long e0 = (long long)blockIdx.x * ch;
+    const long long e1 = min(e0 + (long long)ch, g.r);
+    double s = 0.0;
+    for (long long e = e0 + threadIdx.x; e < e1; e += VB) {
+        const int X = (int)(e / g.fz), Z = (int)(e - (long long)X * g.fz);
+        const int a = X % g.n, ez = Z / g.n, bb = Z - ez * g.n;
+        const double wq = g.wq[a] * g.wq[bb] * g.hx * g.hz[ez] * 0.25;
+        s = fma(wq, u[(long long)r * u_ld + e], s);
+    }
+    s = block_sum(s, red);
+    if (threadIdx.x == 0) part[(long long)r * nch + blockIdx.x] = s;
+}
+
+__global__ void __launch_bounds__(VB) gauge_apply_kernel(GridArgs g, double* __restrict__ u, long long u_ld,
+                                                        const int* __restrict__ apply,
+                                                        const double* __restrict__ part, int nch, int ch) {
+    const int r = blockIdx.y;
+    if (!apply[r]) return;
+    __shared__ double red[32];
+    double s = 0.0;
+    for (int c = threadIdx.x; c < nch; c += VB) s += part[(long long)r * nch + c];
+    s = block_sum(s, red) / g.area;
+    const long long e0 = (long long)blockIdx.x * ch;
+    const long long e1 = min(e0 + (long long)ch, g.r);
+    for (long long e = e0 + threadIdx.x; e < e1; e += VB) u[(long long)r * u_ld + e] -= s;
+}
+
+void k_gauge(const GridArgs& g, int R, double* u, long long u_ld, const int* apply, double* part,
+             int nch, int ch, cudaStream_t s) {
+    dim3 grid(nch, R);
+    gauge_partial_kernel<<<grid, VB, 0, s>>>(g, u, u_ld, apply, part, nch, ch);
+    count_launches(1);
+    gauge_apply_kernel<<<grid, VB, 0, s>>>(g, u, u_ld, apply, part, nch, ch);
+    count_launches(1);
+}
+
+// ---------------------------------------------------------------------------
+// Setup builders
+// ---------------------------------------------------------------------------
+__global__ void build_strip_op_kernel(double* __restrict__ A, const double* __restrict__ Ax,
+                                      const double* __restrict__ Lz, double k2, int n, int fz) {
+    const long long m = (long long)n * fz;
+    const long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx >= m * m) return;
+    const long long row = idx / m, col = idx - row * m;
+    const int a = (int)(row / fz), Z = (int)(row - (long long)a * fz);
+    const int ap = (int)(col / fz), Zp = (int)(col - (long long)ap * fz);
+    double v = 0.0;
+    if (Z == Zp) v += Ax[a * n + ap];
+    if (a == ap) v += Lz[(long long)Z * fz + Zp];
+    if (row == col) v -= k2;
+    A[idx] = v;
+}
+
+void k_build_strip_op(double* A, const double* Ax, const double* Lz, double k2, int n, int fz,
+                      cudaStream_t s) {
+    const long long m = (long long)n * fz;
+    const long long tot = m * m;
+    build_strip_op_kernel<<<(unsigned)((tot + 255) / 256), 256, 0, s>>>(A, Ax, Lz, k2, n, fz);
+    count_launches(1);
+}
+
+__global__ void identity_kernel(double* X, int m) {
+    const long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    const long long tot = (long long)m * m;
+    if (idx >= tot) return;
+    const long long i = idx / m, j = idx - i * m;
+    X[idx] = (i == j) ? 1.0 : 0.0;
+}
+
+void k_identity(double* X, int m, cudaStream_t s) {
+    const long long tot = (long long)m * m;
+    identity_kernel<<<(unsigned)((tot + 255) / 256), 256, 0, s>>>(X, m);
+    count_launches(1);
+}
+
+// W = B_c A_c^-1 (2 fz x n fz): row (s, Z) = sum_a beta[s][a] Ainv[(a, Z), :]
+__global__ void build_W_kernel(double* __restrict__ W, const double* __restrict__ Ainv,
+                               const double* __restrict__ beta, int n, int fz) {
+    const long long m = (long long)n * fz;
+    const long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx >= 2LL * fz * m) return;
+    const long long row = idx / m, col = idx - row * m;
+    const int s = (int)(row / fz), Z = (int)(row - (long long)s * fz);
+    double v = 0.0;
+    for (int a = 0; a < n; ++a) v = fma(beta[s * n + a], Ainv[((long long)a * fz + Z) * m + col], v);
+    W[idx] = v;
+}
+
+void k_build_W(double* W, const double* Ainv, const double* beta, int n, int fz, cudaStream_t s) {
+    const long long tot = 2LL * fz * n * fz;
+    build_W_kernel<<<(unsigned)((tot + 255) / 256), 256, 0, s>>>(W, Ainv, beta, n, fz);
+    count_launches(1);
+}
+
+// G = W E_c (2 fz x 2 fz): columns of W at the strip's west (a = 0) and east
+// (a = N) face nodes; the physical face of a boundary class is zeroed.
+__global__ void build_G_kernel(double* __restrict__ G, const double* __restrict__ W, int n, int fz, int cls) {
+    const long long m = (long long)n * fz;
+    const int idx = blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx >= 4 * fz * fz) return;
+    const int row = idx / (2 * fz), col = idx - row * 2 * fz;
+    const int sp = col / fz, Zp = col - sp * fz;
+    const int a = sp == 0 ? 0 : n - 1;
+    double v = W[(long long)row * m + (long long)a * fz + Zp];
+    if ((cls == 0 && sp == 0) || (cls == 2 && sp == 1)) v = 0.0;
+    G[idx] = v;
+}
+
+void k_build_G(double* G, const double* W, int n, int fz, int cls, cudaStream_t s) {
+    const int tot = 4 * fz * fz;
+    build_G_kernel<<<(tot + 255) / 256, 256, 0, s>>>(G, W, n, fz, cls);
+    count_launches(1);
+}
+
+// Block-Jacobi block (Sec. 3.2).  Full pair, local faces 0..3 = (east face of
+// strip 2p, west and east faces of strip 2p+1, west face of strip 2p+2):
+//   M = I + [0 Gb_tl Gb_tr 0; Ga_br 0 0 0; 0 0 0 Gc_tl; 0 Gb_bl Gb_br 0]
+// with G?_xy the (out half x, in face y) block of that strip's G.  Single
+// interface (gC == null), local faces (east of 2p, west of 2p+1):
+//   M = I + [0 Gb_tl; Ga_br 0].
+__global__ void build_M_kernel(double* __restrict__ M, const double* __restrict__ gA, const double* __restrict__ gB,
+                               const double* __restrict__ gC, int fz) {
+    const int nb = gC ? 4 : 2;
+    const int m = nb * fz;
+    const int idx = blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx >= m * m) return;
+    const int row = idx / m, col = idx - row * m;
+    const int bi = row / fz, zi = row - bi * fz, bj = col / fz, zj = col - bj * fz;
+    const int f2 = 2 * fz;
+    auto gblk = [&](const double* G, int outh, int inf) { return G[(outh * fz + zi) * f2 + inf * fz + zj]; };
+    double v = (row == col) ? 1.0 : 0.0;
+    if (nb == 4) {
+        if (bi == 0 && bj == 1) v += gblk(gB, 0, 0);
+        if (bi == 0 && bj == 2) v += gblk(gB, 0, 1);
+        if (bi == 3 && bj == 1) v += gblk(gB, 1, 0);
+        if (bi == 3 && bj == 2) v += gblk(gB, 1, 1);
+        if (bi == 1 && bj == 0) v += gblk(gA, 1, 1);
+        if (bi == 2 && bj == 3) v += gblk(gC, 0, 0);
+    } else {
+        if (bi == 1 && bj == 0) v += gblk(gA, 1, 1);
+        if (bi == 0 && bj == 1) v += gblk(gB, 0, 0);
+    }
+    M[idx] = v;
+}
+
+void k_build_M(double* M, const double* gA, const double* gB, const double* gC, int fz, cudaStream_t s) {
+    const int m = (gC ? 4 : 2) * fz;
+    build_M_kernel<<<(m * m + 255) / 256, 256, 0, s>>>(M, gA, gB, gC, fz);
+    count_launches(1);
+}
+
+__global__ void pad_block_kernel(double* __restrict__ dst, const double* __restrict__ src, int ms, int md) {
+    const int idx = blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx >= md * md) return;
+    const int i = idx / md, j = idx - i * md;
+    dst[idx] = (i < ms && j < ms) ? src[i * ms + j] : 0.0;
+}
+
+void k_pad_block(double* dst, const double* src, int m_src, int m_dst, cudaStream_t s) {
+    pad_block_kernel<<<(m_dst * m_dst + 255) / 256, 256, 0, s>>>(dst, src, m_src, m_dst);
+    count_launches(1);
+}
+
+// rho[side][g][row] = sum over group g of the side's input face of G[row][.]
+__global__ void build_rho_kernel(double* __restrict__ rho, const double* __restrict__ G, int fz, int ng) {
+    const int f2 = 2 * fz;
+    const int idx = blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx >= 2 * ng * f2) return;
+    const int row = idx % f2, sg = idx / f2, g = sg % ng, side = sg / ng;
+    const int gs = fz / ng;
+    double v = 0.0;
+    for (int z = 0; z < gs; ++z) v += G[row * f2 + side * fz + g * gs + z];
+    rho[idx] = v;
+}
+
+void k_build_rho(double* rho, const double* G, int fz, int ng, cudaStream_t s) {
+    const int tot = 2 * ng * 2 * fz;
+    build_rho_kernel<<<(tot + 255) / 256, 256, 0, s>>>(rho, G, fz, ng);
+    count_launches(1);
+}
+
+__global__ void fill_kernel(double* x, long long n, double v) {
+    const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) x[i] = v;
+}
+
+void k_fill(double* x, long long n, double v, cudaStream_t s) {
+    if (n <= 0) return;
+    fill_kernel<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(x, n, v);
+    count_launches(1);
+}
+
+// ---------------------------------------------------------------------------
+// FP64 DFMA throughput probe (eight independent FMA chains per thread)
+// ---------------------------------------------------------------------------
+__global__ void fp64_probe_kernel(double* out, int iters) {
+    double x[8];
+    const double y = 0.999999, z = 1e-7;
+#pragma unroll
+    for (int i = 0; i < 8; ++i) x[i] = threadIdx.x * 1e-3 + i;
+    for (int it = 0; it < iters; ++it) {
+#pragma unroll
+        for (int i = 0; i < 8; ++i) x[i] = fma(x[i], y, z);
+    }
+    double s = 0.0;
+#pragma unroll
+    for (int i = 0; i < 8; ++i) s += x[i];
+    if (s == 12345.678) out[blockIdx.x] = s;  // practically never taken; keeps the chains live
+}
+
+void k_fp64_probe(double* out, int blocks, int iters, cudaStream_t s) {
+    fp64_probe_kernel<<<blocks, 256, 0, s>>>(out, iters);
+    count_launches(1);
+}
+
+}  // namespace smpm

@@ -1,0 +1,109 @@
+// Launch wrappers of the libsmpm device kernels (kernels.cu).
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include "smpm_internal.h"
+
+namespace smpm {
+
+// Face-vector layout: for strip i, face s (0 = west, 1 = east) the fz values
+// sit at offset (2 i + s) fz of a padded vector of length kp = 2 fz mx; the
+// two physical faces (strip 0 west, strip mx-1 east) are padding and hold 0.
+// Interface t (between strips t and t+1) is the contiguous range
+// [(2 t + 1) fz, (2 t + 3) fz).  ld >= kp + fz is the stride between the
+// vectors of consecutive right-hand sides.
+
+// Per-solve arguments of the Krylov / deflation kernels.
+struct KArgs {
+    int R, m, nch, ch;             // rhs, restart length, chunks, chunk length
+    long long ld, kp;
+    int fz, mx, ng, d, n;
+    double* V;                     // [R][m+1][ld]  Arnoldi basis
+    double* w;                     // [R][ld]       work vector
+    double* Hc;                    // [R][m][m+1]   rotated Hessenberg columns
+    double* htmp;                  // [R][m+1]      first CGS pass coefficients
+    double* cs;                    // [R][m]        Givens cosines
+    double* sn;                    // [R][m]        Givens sines
+    double* gv;                    // [R][m+1]      rotated residual vector
+    double* part1;                 // [R][nch][m+2] partial dot products
+    double* part2;
+    double* q;                     // [R][d]        coarse restriction Z^T v
+    double* c;                     // [R][d]        coarse solution K q
+    const double* rho;             // op o: rho + o*rho_stride, [cls][side][ng][2 fz]
+    long long rho_stride;
+    const double* K;               // op o: K + o*K_stride, [d][d]
+    long long K_stride;
+    const int* op;                 // [R] operator set of each rhs
+    const int* strip_cls;          // [mx]
+    int* active;                   // [R] running Arnoldi in this cycle
+    int* done;                     // [R] converged (or stopped)
+    int* nit;                      // [R] Arnoldi steps taken in this cycle
+    double* target;                // [R] absolute residual target tol*||b_S||
+    double* bnorm;                 // [R] ||b_S||
+    double* rnorm;                 // [R] residual norm at the last cycle start
+    int* flags;                    // [R] bit 0: breakdown / non-finite
+};
+
+void k_deflate_sum(const KArgs& a, const double* v, const double* vsub, cudaStream_t s);
+void k_coarse(const KArgs& a, cudaStream_t s);
+// mode 0: w -= S Z c, dots with V[0..j];  mode 1: reduce pass 1, w -= V h1, dots;
+// mode 2: reduce pass 2, w -= V h2, store Hessenberg column, partial norms.
+void k_cgs(const KArgs& a, int j, int mode, cudaStream_t s);
+// beta = ||w||, V[j+1] = w / beta, Givens update, convergence flags.
+void k_normalize(const KArgs& a, int j, int last_allowed, cudaStream_t s);
+// Start of a restart cycle (iterative refinement on x_S): d = b_S - s with
+// s = S x_S (null on the first cycle), q = Z^T d, c = K q, V[0] = P d = d - S Z c,
+// partial norms ||P d||, ||b_S||, ||d||; then k_cycle_start tests ||d|| against
+// tol ||b_S||, normalises V[0] and saves c into c0.
+void k_residual(const KArgs& a, const double* bS, const double* sv, cudaStream_t s);
+void k_cycle_start(const KArgs& a, double* c0, int first, double tol, cudaStream_t s);
+// Y = V y with y from the rotated Hessenberg system of the cycle.
+void k_cycle_update(const KArgs& a, double* Y, cudaStream_t s);
+// c = K Z^T v for every unconverged rhs.
+void k_deflate_coarse_pending(const KArgs& a, const double* v, cudaStream_t s);
+// x_S += t + Z (c0 - c) for rhs that ran this cycle.
+void k_xs_update(const KArgs& a, double* xS, const double* t, const double* c0, cudaStream_t s);
+
+// RHS assembly b = f + tau g at the physical boundary, per rhs; partial
+// dots with u_L for the projection (uL[r] may be null).
+struct GridArgs {
+    int n, N, mx, mz, fz, nx;
+    long long r;
+    double tau_x;
+    const double* tau_z;           // [mz] (device)
+    const double* wq;              // [n] GLL weights (device)
+    const double* hz;              // [mz] (device)
+    double hx, area;
+};
+void k_rhs_assemble(const GridArgs& g, int R, const double* f, long long f_ld, const double* gb,
+                    long long g_ld, double* b, long long b_ld, const double* const* uL,
+                    double* part, int nch, int ch, cudaStream_t s);
+void k_project(int R, long long len, double* v, long long v_ld, const double* const* u,
+               const double* part, int nch, int ch, cudaStream_t s);
+void k_dot_partial(int R, long long len, const double* v, long long v_ld, const double* const* u,
+                   double* part, int nch, int ch, cudaStream_t s);
+void k_recovery_rhs(const GridArgs& g, int R, const double* b, long long b_ld, const double* xS,
+                    long long x_ld, double* t2, cudaStream_t s);
+void k_gauge(const GridArgs& g, int R, double* u, long long u_ld, const int* apply, double* part,
+             int nch, int ch, cudaStream_t s);
+
+// Setup builders.
+void k_build_strip_op(double* A, const double* Ax, const double* Lz, double k2, int n, int fz,
+                      cudaStream_t s);
+void k_identity(double* X, int m, cudaStream_t s);
+void k_build_W(double* W, const double* Ainv, const double* beta, int n, int fz, cudaStream_t s);
+void k_build_G(double* G, const double* W, int n, int fz, int cls, cudaStream_t s);
+// Pair block of block-Jacobi (Sec. 3.2) from the G of strips 2p, 2p+1, 2p+2
+// (gC null for the single-interface last block).
+void k_build_M(double* M, const double* gA, const double* gB, const double* gC, int fz,
+               cudaStream_t s);
+void k_pad_block(double* dst, const double* src, int m_src, int m_dst, cudaStream_t s);
+void k_build_rho(double* rho, const double* G, int fz, int ng, cudaStream_t s);
+void k_fill(double* x, long long n, double v, cudaStream_t s);
+
+// FP64 DFMA throughput probe: each thread runs `iters` dependent-chain-free
+// FMA groups; returns nothing, writes a checksum to out.
+void k_fp64_probe(double* out, int blocks, int iters, cudaStream_t s);
+
+}  // namespace smpm

@@ -1,0 +1,118 @@
+// Internal declarations of libsmpm: host-side operator builders (host_ops.cpp),
+// device kernels (kernels.cu) and the API / solve driver (api.cu).
+#pragma once
+
+#include <cstdint>
+#include <string>
+#include <vector>
+
+namespace smpm {
+
+// ---------------------------------------------------------------------------
+// Host side (plain C++, FP64)
+// ---------------------------------------------------------------------------
+
+// GLL points and quadrature weights on [-1, 1] (n points, order n-1).
+void gll(int n, std::vector<double>& x, std::vector<double>& w);
+// Nodal differentiation matrix, row-major n x n (D[i*n + j] = l_j'(x_i)).
+void gll_diff(const std::vector<double>& x, std::vector<double>& D);
+
+struct Geometry {
+    int mx = 0, mz = 0, order = 0, n = 0, N = 0;
+    int fz = 0, nx = 0;                   // z-nodes per strip column, x-nodes total
+    long long r = 0, k = 0;               // grid nodes, Schur unknowns
+    double lx = 0, lz = 0, hx = 0, tau_x = 0, z_ratio = 1, tau_scale = 10;
+    std::vector<double> hz, zb, tau_z;    // per z-element
+    std::vector<double> xi, w, D, D2;     // GLL data (row-major n x n)
+    int ng = 1;                           // deflation groups per interface
+    int d = 0;                            // coarse dimension (mx-1)*ng
+};
+
+// Fills every derived quantity; returns false on a bad argument (msg set).
+bool make_geometry(int mx, int mz, int order, double lx, double lz, double z_ratio,
+                   double tau_scale, int groups, Geometry& g, std::string& msg);
+
+// 1-D x-operator of one strip class (n x n row-major): Laplacian plus the own
+// part of the x-face terms (cls 0: Neumann west / Robin east, 1: Robin both,
+// 2: Robin west / Neumann east).
+void strip_x_operator(const Geometry& g, int cls, std::vector<double>& Ax);
+// 1-D z-operator over the mz elements of a strip column (fz x fz row-major).
+void z_operator(const Geometry& g, std::vector<double>& Lz);
+// Full 1-D x-operator over all mx elements (nx x nx row-major) -- used only
+// for the left null vector.
+void full_x_operator(const Geometry& g, std::vector<double>& Lx);
+// B-row coefficients of one strip class: beta[s*n + a], s = 0 for the flux
+// written onto the west neighbour's east face, s = 1 onto the east neighbour's
+// west face.  Zero rows where the class has no neighbour.
+void face_flux_rows(const Geometry& g, int cls, std::vector<double>& beta);
+
+// Banded LU with partial pivoting (column band storage, LAPACK layout).
+struct BandLU {
+    int n = 0, kl = 0, ku = 0, ldab = 0;
+    std::vector<double> ab;
+    std::vector<int> piv;
+    void init(int n_, int kl_, int ku_);
+    double& at(int i, int j) { return ab[(size_t)(kl + ku + i - j) + (size_t)j * ldab]; }
+    double at(int i, int j) const { return ab[(size_t)(kl + ku + i - j) + (size_t)j * ldab]; }
+    bool in_band(int i, int j) const { return i - j <= kl && j - i <= ku; }
+    bool factor();                        // false if an exact zero pivot occurs
+    void solve(double* b) const;          // A x = b  (in place)
+    void solve_T(double* b) const;        // A^T x = b (in place)
+};
+
+// Unit left null vector of a dense-given banded singular matrix (row-major),
+// by inverse iteration with (M - sigma I)^T.
+bool left_null_banded(const std::vector<double>& M, int n, int bw, std::vector<double>& v,
+                      std::string& msg);
+// Unit left null vectors of the full 1-D x-operator (nx) and of the z-operator
+// (fz); u_L = u_Lx (x) u_Lz is the left null vector of L (Kronecker sum).
+bool left_null_x(const Geometry& g, std::vector<double>& v, std::string& msg);
+bool left_null_z(const Geometry& g, std::vector<double>& v, std::string& msg);
+
+// Coarse operator K (d x d row-major) of the deflation: for singular C
+// (k^2 = 0) K = (C + a uC 1^T / sqrt d)^-1 (I - uC uC^T) (the zero-mean
+// solution of the consistent coarse system), else K = C^-1.
+bool coarse_operator(const std::vector<double>& C, int d, int fz_over_ng, const double* uC,
+                     std::vector<double>& K, std::string& msg);
+
+// ---------------------------------------------------------------------------
+// Device side (kernels.cu)
+// ---------------------------------------------------------------------------
+
+// One tile of a class GEMM: columns c in [0, nu*nr) map to unit u0 + c / nr and
+// right-hand side r0 + c % nr; every column of a tile uses matrix `mat`.
+struct Tile {
+    int mat, u0, nu, r0, nr;
+};
+
+struct GemmArgs {
+    const double* mats;       // matrix m at mats + m * mat_stride, row-major M x K
+    long long mat_stride;
+    int M, K;
+    const int* row_lo;        // per matrix: output rows [row_lo, row_hi) are stored
+    const int* row_hi;
+    const double* in;         // column (u, r) at in + r*in_rs + u*in_us + in_off
+    long long in_rs, in_us, in_off;
+    double* out;              // row < msplit: out + r*out_rs + u*out_us + out_off0 + row
+    long long out_rs, out_us, out_off0, out_off1;   // row >= msplit: ... + out_off1 + row - msplit
+    int msplit;
+    const double* add;        // EPI 1: out = add[same address] + acc
+    const int* active;        // per rhs: skip tiles whose columns are all inactive (may be null)
+    unsigned long long* flops;  // if set: each working CTA adds 2 * rows * K * active columns
+};
+
+// Number of kernels libsmpm has launched in this process.
+long long launch_count();
+void count_launches(int n);
+
+void launch_class_gemm(const GemmArgs& a, const Tile* d_tiles, int ntiles, int epi, void* stream);
+
+// Describes the vector batch layout shared by the small kernels.
+struct VecLayout {
+    int R;                    // right-hand sides in the batch
+    long long ld;             // stride between the face vectors of consecutive rhs
+    long long kp;             // padded face-vector length (2 fz mx)
+    int fz, mx, ng, d, n;
+};
+
+}  // namespace smpm

@@ -1,0 +1,210 @@
+"""ctypes binding of libsmpm.so (include/smpm.h): argument marshalling only.
+
+Every step of the solve runs in the library's CUDA kernels; this module only
+converts Python arguments (torch tensors on the GPU, or numpy arrays / host
+tensors) into the pointers and sizes of the C ABI.  There is no fallback: if
+the library cannot be loaded, ``load()`` raises.
+"""
+import ctypes
+import os
+
+import numpy as np
+
+_PKG = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_PKG, "libsmpm.so")
+
+SMPM_OK, SMPM_EINVAL, SMPM_ENOMEM, SMPM_ENOCONV, SMPM_EBREAKDOWN, SMPM_ECUDA, SMPM_EBUSY = 0, -1, -2, -3, -4, -5, -6
+
+# every entry point include/smpm.h declares
+EXPORTS = ["smpm_setup", "smpm_solve", "smpm_solve_batch", "smpm_setup_multi", "smpm_solve_multi",
+           "smpm_sizes", "smpm_node_coords", "smpm_device_bytes", "smpm_release", "smpm_probe_fp64",
+           "smpm_profile", "smpm_profile_read", "smpm_kernel_launches", "smpm_apply", "smpm_last_residuals", "smpm_last_error"]
+
+
+class Grid(ctypes.Structure):
+    _fields_ = [("mx", ctypes.c_int), ("mz", ctypes.c_int), ("order", ctypes.c_int),
+                ("lx", ctypes.c_double), ("lz", ctypes.c_double), ("z_ratio", ctypes.c_double),
+                ("tau_scale", ctypes.c_double), ("deflation_groups", ctypes.c_int),
+                ("restart", ctypes.c_int), ("max_iter", ctypes.c_int), ("precision", ctypes.c_int)]
+
+
+class Stats(ctypes.Structure):
+    _fields_ = [("iters", ctypes.c_int), ("restarts", ctypes.c_int), ("status", ctypes.c_int),
+                ("rel_resid_true", ctypes.c_double), ("setup_ms", ctypes.c_double),
+                ("solve_ms", ctypes.c_double)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+class SmpmError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__(f"smpm error {code}: {msg}")
+        self.code = code
+
+
+_lib = None
+
+
+def load():
+    """Load libsmpm.so from the package directory (raises if it is missing)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(LIB_PATH):
+        raise RuntimeError(f"{LIB_PATH} not built: run __graft_entry__.build() (no CPU fallback exists)")
+    lib = ctypes.CDLL(LIB_PATH)
+    H = ctypes.c_void_p
+    P = ctypes.c_void_p
+    lib.smpm_setup.argtypes = [ctypes.POINTER(Grid), ctypes.c_double, P, ctypes.POINTER(H)]
+    lib.smpm_setup_multi.argtypes = [ctypes.POINTER(Grid), ctypes.c_int, P, P, ctypes.POINTER(H)]
+    lib.smpm_solve.argtypes = [H, P, P, ctypes.c_double, P, ctypes.POINTER(Stats)]
+    lib.smpm_solve_batch.argtypes = [H, ctypes.c_int, P, P, ctypes.c_double, P, ctypes.POINTER(Stats)]
+    lib.smpm_solve_multi.argtypes = [H, ctypes.c_int, P, P, P, ctypes.c_double, P, ctypes.POINTER(Stats)]
+    lib.smpm_sizes.argtypes = [H, ctypes.POINTER(ctypes.c_longlong), ctypes.POINTER(ctypes.c_longlong),
+                               ctypes.POINTER(ctypes.c_longlong)]
+    lib.smpm_node_coords.argtypes = [H, P, P]
+    lib.smpm_device_bytes.argtypes = [H]
+    lib.smpm_device_bytes.restype = ctypes.c_longlong
+    lib.smpm_release.argtypes = [H]
+    lib.smpm_release.restype = None
+    lib.smpm_probe_fp64.argtypes = [P, ctypes.POINTER(ctypes.c_double)]
+    lib.smpm_last_error.restype = ctypes.c_char_p
+    lib.smpm_profile.argtypes = [H, ctypes.c_int]
+    lib.smpm_profile_read.argtypes = [H, ctypes.POINTER(ctypes.c_longlong), ctypes.POINTER(ctypes.c_double),
+                                      ctypes.POINTER(ctypes.c_double), ctypes.c_int]
+    lib.smpm_apply.argtypes = [H, ctypes.c_int, ctypes.c_int, P, P]
+    lib.smpm_last_residuals.argtypes = [H, ctypes.c_int, P]
+    lib.smpm_kernel_launches.argtypes = []
+    lib.smpm_kernel_launches.restype = ctypes.c_longlong
+    for name in EXPORTS:
+        if not hasattr(lib, name):
+            raise RuntimeError(f"libsmpm.so does not export {name}")
+    for name in EXPORTS:
+        if name not in ("smpm_device_bytes", "smpm_release", "smpm_last_error", "smpm_kernel_launches"):
+            getattr(lib, name).restype = ctypes.c_int
+    _lib = lib
+    return lib
+
+
+def _check(code):
+    if code != SMPM_OK and code != SMPM_ENOCONV:
+        raise SmpmError(code, load().smpm_last_error().decode())
+    return code
+
+
+def _ptr(x):
+    """Pointer of a torch tensor (any device) or a numpy array; None -> NULL."""
+    if x is None:
+        return None
+    if hasattr(x, "data_ptr"):
+        if not x.is_contiguous():
+            raise ValueError("tensor must be contiguous")
+        if str(x.dtype) != "torch.float64" and str(x.dtype) != "torch.int32":
+            raise ValueError("tensor must be float64")
+        return ctypes.c_void_p(x.data_ptr())
+    if isinstance(x, np.ndarray):
+        if not x.flags["C_CONTIGUOUS"]:
+            raise ValueError("array must be C-contiguous")
+        return x.ctypes.data_as(ctypes.c_void_p)
+    raise TypeError(f"unsupported buffer type {type(x)}")
+
+
+def _stream_ptr(stream):
+    if stream is None:
+        return None
+    if hasattr(stream, "cuda_stream"):
+        return ctypes.c_void_p(stream.cuda_stream)
+    return ctypes.c_void_p(int(stream))
+
+
+def make_grid(mx, mz, order, lx, lz, z_ratio=1.0, tau_scale=10.0, deflation_groups=0, restart=64,
+              max_iter=2000, precision=0):
+    return Grid(mx, mz, order, lx, lz, z_ratio, tau_scale, deflation_groups, restart, max_iter, precision)
+
+
+class Solver:
+    """One smpm handle (operators for one or several k^2 values)."""
+
+    def __init__(self, grid: Grid, k2=0.0, stream=None):
+        lib = load()
+        self._h = ctypes.c_void_p()
+        self.grid = grid
+        if np.ndim(k2) == 0:
+            self.k2 = np.array([float(k2)])
+            _check(lib.smpm_setup(ctypes.byref(grid), float(k2), _stream_ptr(stream), ctypes.byref(self._h)))
+        else:
+            self.k2 = np.ascontiguousarray(k2, dtype=np.float64)
+            _check(lib.smpm_setup_multi(ctypes.byref(grid), len(self.k2), self.k2.ctypes.data_as(ctypes.c_void_p),
+                                        _stream_ptr(stream), ctypes.byref(self._h)))
+        r, nb, k = ctypes.c_longlong(), ctypes.c_longlong(), ctypes.c_longlong()
+        _check(lib.smpm_sizes(self._h, ctypes.byref(r), ctypes.byref(nb), ctypes.byref(k)))
+        self.r, self.nb, self.k = r.value, nb.value, k.value
+
+    def coords(self):
+        x = np.empty(self.r)
+        z = np.empty(self.r)
+        _check(load().smpm_node_coords(self._h, _ptr(x), _ptr(z)))
+        return x, z
+
+    def device_bytes(self):
+        return load().smpm_device_bytes(self._h)
+
+    def solve(self, f, u, g=None, tol=1e-10):
+        """f, u: one r-vector or [nrhs, r]; g: [nrhs, nb] or None.  Returns Stats."""
+        st = Stats()
+        nrhs = 1 if len(f.shape) == 1 else int(f.shape[0])
+        if nrhs == 1:
+            code = load().smpm_solve(self._h, _ptr(f), _ptr(g), float(tol), _ptr(u), ctypes.byref(st))
+        else:
+            code = load().smpm_solve_batch(self._h, nrhs, _ptr(f), _ptr(g), float(tol), _ptr(u), ctypes.byref(st))
+        _check(code)
+        return st
+
+    def solve_multi(self, op_of_rhs, f, u, g=None, tol=1e-10):
+        ops = np.ascontiguousarray(op_of_rhs, dtype=np.int32)
+        st = Stats()
+        _check(load().smpm_solve_multi(self._h, len(ops), ops.ctypes.data_as(ctypes.c_void_p), _ptr(f), _ptr(g),
+                                       float(tol), _ptr(u), ctypes.byref(st)))
+        return st
+
+    def last_residuals(self, n):
+        out = np.empty(n)
+        _check(load().smpm_last_residuals(self._h, int(n), _ptr(out)))
+        return out
+
+    APPLY = {"S": 0, "Minv": 1, "P": 2, "bS": 3, "Ainv": 4}
+
+    def apply(self, kind, x, y):
+        """y = op(x) for op in APPLY (x, y: [nrhs, len] or one vector)."""
+        nrhs = 1 if len(x.shape) == 1 else int(x.shape[0])
+        _check(load().smpm_apply(self._h, self.APPLY[kind], nrhs, _ptr(x), _ptr(y)))
+
+    def profile(self, enable=True):
+        _check(load().smpm_profile(self._h, 1 if enable else 0))
+
+    def profile_read(self, reset=True):
+        n, fl, ms = ctypes.c_longlong(), ctypes.c_double(), ctypes.c_double()
+        _check(load().smpm_profile_read(self._h, ctypes.byref(n), ctypes.byref(fl), ctypes.byref(ms), int(reset)))
+        return {"launches": n.value, "flops": fl.value, "ms": ms.value}
+
+    def close(self):
+        if self._h:
+            load().smpm_release(self._h)
+            self._h = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def kernel_launches():
+    return load().smpm_kernel_launches()
+
+
+def probe_fp64(stream=None):
+    t = ctypes.c_double()
+    _check(load().smpm_probe_fp64(_stream_ptr(stream), ctypes.byref(t)))
+    return t.value

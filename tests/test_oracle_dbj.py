@@ -109,3 +109,15 @@ def test_iteration_counts_table2_behaviour():
     assert its[("bj", 32)] >= 1.4 * its[("bj", 16)]
     assert its[("dbj", 32)] < its[("bj", 32)]
     assert 10 <= its[("dbj", 32)] <= 60
+
+
+@pytest.mark.parametrize("mx", [2, 3])
+def test_two_and_three_strips(mx):
+    """With m_x <= 3 the one block-Jacobi block is all of the singular S and is
+    replaced by the identity; the deflated solve still equals the direct one."""
+    g = Grid(mx, 2, 5, 1.0, 1.0)
+    f = np.random.default_rng(4).uniform(0, 1, g.r)
+    u_d, _ = direct_solve(g, f)
+    for method in ("dbj", "bj", "2las"):
+        u, info = dbj.solve(g, f, method=method, tol=1e-13)
+        assert np.linalg.norm(u - u_d) < 1e-10 * np.linalg.norm(u_d), method
