@@ -151,6 +151,28 @@ int smpm_profile_read(smpm_handle h, long long* launches, double* flops, double*
 /* Number of CUDA kernels this library has launched in the process. */
 long long smpm_kernel_launches(void);
 
+/* Allocation-free deflation projection (no counterpart in the paper; an
+ * interface for callers that cannot allocate device memory when they call,
+ * e.g. code running under CUDA stream capture, real-time loops, or hosts that
+ * fix the library's memory up front).  Computes y = P x = x - S Z K Z^T x for
+ * operator set 0 of h -- the same result as smpm_apply(h, 2, ...) -- without
+ * calling cudaMalloc, cudaFree or any allocating library routine.
+ *   x, y: device pointers to nrhs consecutive k-vectors (interface order as in
+ *         smpm_apply); host pointers are rejected with SMPM_EINVAL.
+ *   Scratch: a fixed device array of SMPM_NOALLOC_MAX_DOUBLES doubles inside
+ *         the library, held by every GPU that loads it until the process
+ *         exits; a call needs 2 * nrhs * d of them (d = (mx - 1) per-interface
+ *         deflation groups, or (mx - 1) mz) and is rejected with SMPM_EINVAL
+ *         above that.  All calls share the array and it keeps the last call's
+ *         contents (each call writes every entry it reads first); calls whose
+ *         kernels overlap on the GPU race on it, so order them on one stream.
+ *   The first call on a device looks up the array's device address
+ *         (cudaGetSymbolAddress); make that first call before any stream
+ *         capture.  Work is queued on the handle's stream; the call returns
+ *         without synchronising. */
+#define SMPM_NOALLOC_MAX_DOUBLES 65536
+int smpm_apply_deflation_noalloc(smpm_handle h, int nrhs, const double* x, double* y);
+
 /* Message of the calling thread's last failure ("" if none). */
 const char* smpm_last_error(void);
 

@@ -836,6 +836,27 @@ static int guarded(F&& fn) {
     }
 }
 
+// Operator data of operator set 0 for the allocation-free deflation
+// projection (noalloc.cu); reads the handle only.
+struct DeflView {
+    int fz, mx, ng, d;
+    long long k;
+    const double* K;
+    const double* rho;
+    const int* strip_cls;
+    cudaStream_t stream;
+};
+
+bool deflation_view(smpm_handle h, DeflView* v, std::string& msg) {
+    if (!h) { msg = "null handle"; return false; }
+    const Solver& S = *(const Solver*)h;
+    v->fz = S.g.fz; v->mx = S.g.mx; v->ng = S.g.ng; v->d = S.g.d; v->k = S.g.k;
+    v->K = S.K; v->rho = S.rho; v->strip_cls = S.d_strip_cls; v->stream = S.stream;
+    return true;
+}
+
+void set_last_error(const std::string& msg) { g_last_error = msg; }
+
 }  // namespace smpm
 
 using namespace smpm;

@@ -18,7 +18,8 @@ SMPM_OK, SMPM_EINVAL, SMPM_ENOMEM, SMPM_ENOCONV, SMPM_EBREAKDOWN, SMPM_ECUDA, SM
 # every entry point include/smpm.h declares
 EXPORTS = ["smpm_setup", "smpm_solve", "smpm_solve_batch", "smpm_setup_multi", "smpm_solve_multi",
            "smpm_sizes", "smpm_node_coords", "smpm_device_bytes", "smpm_release", "smpm_probe_fp64",
-           "smpm_profile", "smpm_profile_read", "smpm_kernel_launches", "smpm_apply", "smpm_last_residuals", "smpm_last_error"]
+           "smpm_profile", "smpm_profile_read", "smpm_kernel_launches", "smpm_apply", "smpm_last_residuals", "smpm_apply_deflation_noalloc",
+           "smpm_last_error"]
 
 
 class Grid(ctypes.Structure):
@@ -75,6 +76,7 @@ def load():
                                       ctypes.POINTER(ctypes.c_double), ctypes.c_int]
     lib.smpm_apply.argtypes = [H, ctypes.c_int, ctypes.c_int, P, P]
     lib.smpm_last_residuals.argtypes = [H, ctypes.c_int, P]
+    lib.smpm_apply_deflation_noalloc.argtypes = [H, ctypes.c_int, P, P]
     lib.smpm_kernel_launches.argtypes = []
     lib.smpm_kernel_launches.restype = ctypes.c_longlong
     for name in EXPORTS:
@@ -179,6 +181,11 @@ class Solver:
         """y = op(x) for op in APPLY (x, y: [nrhs, len] or one vector)."""
         nrhs = 1 if len(x.shape) == 1 else int(x.shape[0])
         _check(load().smpm_apply(self._h, self.APPLY[kind], nrhs, _ptr(x), _ptr(y)))
+
+    def apply_deflation_noalloc(self, x, y):
+        """y = P x through the allocation-free entry point (device buffers only)."""
+        nrhs = 1 if len(x.shape) == 1 else int(x.shape[0])
+        _check(load().smpm_apply_deflation_noalloc(self._h, nrhs, _ptr(x), _ptr(y)))
 
     def profile(self, enable=True):
         _check(load().smpm_profile(self._h, 1 if enable else 0))
