@@ -23,7 +23,7 @@ void count_launches(int n) { g_launches.fetch_add(n); }
 
 #define CUDA_LAUNCH_CHECK() (void)0
 
-static constexpr int BM = 64, BN = 32, BK = 16, GT = 128;
+static constexpr int BM = 16, BN = 32, BK = 16, GT = 128;
 static constexpr int VB = 256;  // threads of the vector kernels
 
 __device__ __forceinline__ double warp_sum(double v) {
@@ -46,7 +46,10 @@ __device__ __forceinline__ double block_sum(double v, double* sh) {
 
 // ---------------------------------------------------------------------------
 // Class GEMM: out[:, col] = Mat_{tile} * in[:, col] (+ add) over tiles of columns
-// sharing one class matrix.  Each thread owns a 4 x 4 block of a 64 x 32 tile.
+// sharing one class matrix.  A CTA owns a 16-row x 32-column output tile; each
+// of its 128 threads one row and four columns.  The short row tile keeps the
+// padding waste of M = 2 f_z, 4 f_z, n f_z small, and the many small tiles
+// spread the FP64 work evenly over the SMs.
 // ---------------------------------------------------------------------------
 template <int EPI>
 __global__ void __launch_bounds__(GT) class_gemm_kernel(GemmArgs a, const Tile* __restrict__ tiles) {
@@ -68,17 +71,12 @@ __global__ void __launch_bounds__(GT) class_gemm_kernel(GemmArgs a, const Tile* 
                                (unsigned long long)cols);
     }
     __shared__ double As[BK][BM + 1];
-    __shared__ double Bs[BK][BN + 1];
+    __shared__ __align__(16) double Bs[BK][BN + 2];
     const double* __restrict__ A = a.mats + (long long)t.mat * a.mat_stride;
     const int tid = threadIdx.x;
-    const int tr = tid >> 3, tc = tid & 7;
-    double acc[4][4];
-#pragma unroll
-    for (int i = 0; i < 4; ++i)
-#pragma unroll
-        for (int j = 0; j < 4; ++j) acc[i][j] = 0.0;
+    const int tr = tid >> 3, tc = tid & 7;     // row 0..15, column group 0..7
+    double acc[4] = {0.0, 0.0, 0.0, 0.0};
 
-    // per-thread column pointers for the B-tile loads (4 loads per thread)
     const double* colp[(BN * BK) / GT];
 #pragma unroll
     for (int l = 0; l < (BN * BK) / GT; ++l) {
@@ -105,18 +103,18 @@ __global__ void __launch_bounds__(GT) class_gemm_kernel(GemmArgs a, const Tile* 
         __syncthreads();
 #pragma unroll
         for (int kk = 0; kk < BK; ++kk) {
-            double av[4], bv[4];
-#pragma unroll
-            for (int i = 0; i < 4; ++i) av[i] = As[kk][tr * 4 + i];
-#pragma unroll
-            for (int j = 0; j < 4; ++j) bv[j] = Bs[kk][tc * 4 + j];
-#pragma unroll
-            for (int i = 0; i < 4; ++i)
-#pragma unroll
-                for (int j = 0; j < 4; ++j) acc[i][j] = fma(av[i], bv[j], acc[i][j]);
+            const double av = As[kk][tr];
+            const double2 b01 = *reinterpret_cast<const double2*>(&Bs[kk][tc * 4]);
+            const double2 b23 = *reinterpret_cast<const double2*>(&Bs[kk][tc * 4 + 2]);
+            acc[0] = fma(av, b01.x, acc[0]);
+            acc[1] = fma(av, b01.y, acc[1]);
+            acc[2] = fma(av, b23.x, acc[2]);
+            acc[3] = fma(av, b23.y, acc[3]);
         }
         __syncthreads();
     }
+    const int row = row0 + tr;
+    if (row < lo || row >= hi || row >= a.M) return;
 #pragma unroll
     for (int j = 0; j < 4; ++j) {
         const int c = tc * 4 + j;
@@ -124,15 +122,10 @@ __global__ void __launch_bounds__(GT) class_gemm_kernel(GemmArgs a, const Tile* 
         const int u = t.u0 + c / t.nr, r = t.r0 + c % t.nr;
         if (a.active && !a.active[r]) continue;
         const long long base = (long long)r * a.out_rs + (long long)u * a.out_us;
-#pragma unroll
-        for (int i = 0; i < 4; ++i) {
-            const int row = row0 + tr * 4 + i;
-            if (row < lo || row >= hi || row >= a.M) continue;
-            const long long addr = base + (row < a.msplit ? a.out_off0 + row : a.out_off1 + (row - a.msplit));
-            double v = acc[i][j];
-            if (EPI == 1) v += a.add[addr];
-            a.out[addr] = v;
-        }
+        const long long addr = base + (row < a.msplit ? a.out_off0 + row : a.out_off1 + (row - a.msplit));
+        double v = acc[j];
+        if (EPI == 1) v += a.add[addr];
+        a.out[addr] = v;
     }
 }
 
