@@ -120,6 +120,21 @@ int smpm_solve_multi(smpm_handle h, int nrhs, const int* op_of_rhs, const double
  * device; in and out hold nrhs consecutive vectors. */
 int smpm_apply(smpm_handle h, int kind, int nrhs, const double* in, double* out);
 
+/* 3-D y-periodic problem (Sec. 5, Eqs. poisson3d / fourier_poisson, Alg. 3d)
+ * in Fourier space: u(x,y,z) = sum_j u_j(x,z) e^{i k_j y}, k_j = 2 pi j / ly,
+ * j = 0 .. my/2 (my even).  Each mode is the 2-D Helmholtz problem
+ * (L - k_j^2) u_j = f_j with its own Schur operator S(k_j) (Eq.
+ * transverse_schur), block-Jacobi and deflation; mode 0 is the singular
+ * Poisson-Neumann problem with the null-space projections.  setup builds the
+ * my/2+1 operator sets; solve runs every mode's real and imaginary parts as
+ * separate right-hand sides in the same kernel launches, each with its own
+ * Krylov space and convergence test.
+ * fhat, uhat: [my/2+1][2 (re, im)][r] doubles; ghat: [my/2+1][2][nb] or NULL.
+ * The y-transform itself (a real DFT of length my per node) is the caller's. */
+int smpm_setup_3d(const smpm_grid* grid, int my, double ly, void* stream, smpm_handle* out);
+int smpm_solve_3d(smpm_handle h, const double* fhat, const double* ghat, double tol,
+                  double* uhat, smpm_stats* st);
+
 /* Number of nodes r, Neumann values nb and Schur unknowns k of a handle. */
 int smpm_sizes(smpm_handle h, long long* r, long long* nb, long long* k);
 

@@ -919,6 +919,34 @@ int smpm_apply(smpm_handle h, int kind, int nrhs, const double* in, double* out)
     });
 }
 
+int smpm_setup_3d(const smpm_grid* grid, int my, double ly, void* stream, smpm_handle* out) {
+    return guarded([&] {
+        if (!out) throw Err{SMPM_EINVAL, "out is null"};
+        if (my < 2 || my % 2 != 0) throw Err{SMPM_EINVAL, "my must be even and >= 2"};
+        if (!(ly > 0.0)) throw Err{SMPM_EINVAL, "ly must be positive"};
+        const int nm = my / 2 + 1;
+        std::vector<double> k2(nm);
+        const double pi = 3.14159265358979323846;
+        for (int j = 0; j < nm; ++j) {
+            const double kj = 2.0 * pi * j / ly;
+            k2[j] = kj * kj;
+        }
+        *out = (smpm_handle)make_solver(grid, nm, k2.data(), stream);
+        return SMPM_OK;
+    });
+}
+
+int smpm_solve_3d(smpm_handle h, const double* fhat, const double* ghat, double tol, double* uhat,
+                  smpm_stats* st) {
+    return guarded([&] {
+        if (!h) throw Err{SMPM_EINVAL, "null handle"};
+        Solver& S = *(Solver*)h;
+        std::vector<int> ops(2 * S.nop);
+        for (int j = 0; j < S.nop; ++j) ops[2 * j] = ops[2 * j + 1] = j;
+        return solve_impl(S, ops, fhat, ghat, tol, uhat, st);
+    });
+}
+
 int smpm_sizes(smpm_handle h, long long* r, long long* nb, long long* k) {
     return guarded([&] {
         if (!h) throw Err{SMPM_EINVAL, "null handle"};

@@ -17,6 +17,7 @@ SMPM_OK, SMPM_EINVAL, SMPM_ENOMEM, SMPM_ENOCONV, SMPM_EBREAKDOWN, SMPM_ECUDA, SM
 
 # every entry point include/smpm.h declares
 EXPORTS = ["smpm_setup", "smpm_solve", "smpm_solve_batch", "smpm_setup_multi", "smpm_solve_multi",
+           "smpm_setup_3d", "smpm_solve_3d",
            "smpm_sizes", "smpm_node_coords", "smpm_device_bytes", "smpm_release", "smpm_probe_fp64",
            "smpm_profile", "smpm_profile_read", "smpm_kernel_launches", "smpm_apply", "smpm_last_residuals", "smpm_apply_deflation_noalloc",
            "smpm_last_error"]
@@ -62,6 +63,8 @@ def load():
     lib.smpm_solve.argtypes = [H, P, P, ctypes.c_double, P, ctypes.POINTER(Stats)]
     lib.smpm_solve_batch.argtypes = [H, ctypes.c_int, P, P, ctypes.c_double, P, ctypes.POINTER(Stats)]
     lib.smpm_solve_multi.argtypes = [H, ctypes.c_int, P, P, P, ctypes.c_double, P, ctypes.POINTER(Stats)]
+    lib.smpm_setup_3d.argtypes = [ctypes.POINTER(Grid), ctypes.c_int, ctypes.c_double, P, ctypes.POINTER(H)]
+    lib.smpm_solve_3d.argtypes = [H, P, P, ctypes.c_double, P, ctypes.POINTER(Stats)]
     lib.smpm_sizes.argtypes = [H, ctypes.POINTER(ctypes.c_longlong), ctypes.POINTER(ctypes.c_longlong),
                                ctypes.POINTER(ctypes.c_longlong)]
     lib.smpm_node_coords.argtypes = [H, P, P]
@@ -205,6 +208,27 @@ class Solver:
             self.close()
         except Exception:
             pass
+
+
+class Solver3D(Solver):
+    """Handle for the y-periodic 3-D problem in Fourier space (my/2+1 modes)."""
+
+    def __init__(self, grid: Grid, my, ly, stream=None):
+        lib = load()
+        self._h = ctypes.c_void_p()
+        self.grid = grid
+        self.my, self.ly = int(my), float(ly)
+        self.n_modes = self.my // 2 + 1
+        _check(lib.smpm_setup_3d(ctypes.byref(grid), self.my, self.ly, _stream_ptr(stream), ctypes.byref(self._h)))
+        r, nb, k = ctypes.c_longlong(), ctypes.c_longlong(), ctypes.c_longlong()
+        _check(lib.smpm_sizes(self._h, ctypes.byref(r), ctypes.byref(nb), ctypes.byref(k)))
+        self.r, self.nb, self.k = r.value, nb.value, k.value
+
+    def solve_3d(self, fhat, uhat, ghat=None, tol=1e-10):
+        """fhat, uhat: [n_modes, 2, r] float64 (real and imaginary parts)."""
+        st = Stats()
+        _check(load().smpm_solve_3d(self._h, _ptr(fhat), _ptr(ghat), float(tol), _ptr(uhat), ctypes.byref(st)))
+        return st
 
 
 def kernel_launches():
