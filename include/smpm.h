@@ -49,8 +49,9 @@ extern "C" {
 
 typedef struct smpm_solver* smpm_handle;
 
-/* Grid and solver options.  Defaults used when a field is 0: tau_scale 10,
- * z_ratio 1, restart 64, max_iter 2000. */
+/* Grid and solver options.  Defaults used when a field is 0: tau_scale -30,
+ * z_ratio 1, restart 64, max_iter 2000.  tau_scale is signed in the
+ * convention of Eq. smpm_poisson; negative values damp inter-element jumps. */
 typedef struct {
     int mx, mz, order;      /* elements in x and z, polynomial order (n = order+1)   */
     double lx, lz;          /* domain [0,lx] x [0,lz]                                */

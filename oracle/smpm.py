@@ -22,12 +22,15 @@ What this module computes
 
 Readings of the paper used here (each is listed in the design doc):
 * n GLL points means polynomial order N = n - 1.
-* tau is not given (Sec. 2.2 leaves it to a heuristic): tau = tau_scale *
-  N (N + 1) / h_perp on every edge, h_perp the own element's length normal to
-  that edge, tau_scale = 10 by default.  It does not depend on k^2 (Sec. 5).
-  (tau_scale near 1 makes the Robin strip problems nearly resonant: GMRES
-  needs ~10x more iterations and deflation stops helping; from about 4 up the
-  iteration counts behave as Table table_time reports.)
+* tau is not given (Sec. 2.2 leaves it to stability criteria and a heuristic):
+  tau = tau_scale * N (N + 1) / h_perp on every edge, h_perp the own element's
+  length normal to that edge, tau_scale = -30 by default.  In the sign
+  convention of Eq. smpm_poisson a positive tau anti-damps the modes that jump
+  across an interface (the 1-D operators then have eigenvalues with positive
+  real part, an unstable discretisation, and the Helmholtz problems of Sec. 5
+  become indefinite for k^2 above a few thousand); the stable choice is
+  negative, and |tau_scale| = 30 removes every such eigenvalue on grids up to
+  order 12.  tau does not depend on k^2 (Sec. 5).
 * A corner node receives the terms of both edges it lies on.
 * Neumann data g is given per physical boundary side (west/east: one value per
   z-node, south/north: one value per x-node), so a corner node sees the g of
@@ -47,7 +50,7 @@ from .lgl import lgl_nodes_weights, diff_matrix
 
 
 class Grid:
-    def __init__(self, mx, mz, order, lx, lz, z_ratio=1.0, tau_scale=10.0):
+    def __init__(self, mx, mz, order, lx, lz, z_ratio=1.0, tau_scale=-30.0):
         if mx < 2 or mz < 1 or order < 1:
             raise ValueError("need mx >= 2, mz >= 1, order >= 1")
         self.mx, self.mz, self.order = int(mx), int(mz), int(order)

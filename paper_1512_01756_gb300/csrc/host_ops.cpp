@@ -97,8 +97,9 @@ bool make_geometry(int mx, int mz, int order, double lx, double lz, double z_rat
     }
     if (!(lx > 0) || !(lz > 0)) { msg = "domain lengths must be positive"; return false; }
     if (z_ratio == 0.0) z_ratio = 1.0;
-    if (tau_scale == 0.0) tau_scale = 10.0;
-    if (!(z_ratio > 0) || !(tau_scale > 0)) { msg = "z_ratio and tau_scale must be positive"; return false; }
+    if (tau_scale == 0.0) tau_scale = -30.0;
+    if (!(z_ratio > 0)) { msg = "z_ratio must be positive"; return false; }
+    if (!std::isfinite(tau_scale)) { msg = "tau_scale must be finite"; return false; }
     if (groups != 0 && groups != 1) { msg = "deflation_groups must be 0 or 1"; return false; }
     g.mx = mx; g.mz = mz; g.order = order; g.n = order + 1; g.N = order;
     g.lx = lx; g.lz = lz; g.z_ratio = z_ratio; g.tau_scale = tau_scale;

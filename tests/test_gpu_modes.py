@@ -16,7 +16,7 @@ import pytest
 torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
 
-from oracle.smpm import Grid, assemble_L, gauge  # noqa: E402
+from oracle.smpm import Grid, assemble_L  # noqa: E402
 from oracle import fourier  # noqa: E402
 
 
@@ -97,7 +97,6 @@ def test_full_size_modes_satisfy_oracle_systems(smpm, full3d):
     uh = _unstack(Uh.cpu().numpy())
     L = assemble_L(g)
     ks = fourier.wavenumbers(my, 2.0 * np.pi)
-    from oracle.smpm import left_null_dense  # noqa: F401
     from oracle.schur import left_null_sparse
     uL = left_null_sparse(L)
     for j in range(len(ks)):
@@ -111,4 +110,3 @@ def test_full_size_modes_satisfy_oracle_systems(smpm, full3d):
             assert np.linalg.norm(r) / np.linalg.norm(b) < 1e-8, (j, np.linalg.norm(r) / np.linalg.norm(b))
     # the zero mode is returned with zero quadrature mean
     assert abs(np.dot(g.quad_weights(), uh[:, 0].real)) < 1e-10 * np.abs(uh[:, 0].real).max()
-    del gauge

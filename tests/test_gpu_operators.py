@@ -7,8 +7,11 @@ solves A^-1 (Alg. seq steps 2 and 9).  Grids from two strips up to the full
 256 x 4, order-12 workload.
 
 Tolerances: S and B A^-1 are products of explicit FP64 inverses with
-relative error ~ eps cond(A_c) (cond up to ~1e6 here): 1e-9.  M^-1 and the
-coarse division invert further matrices: 1e-8.
+relative error ~ eps cond(A_c) (cond up to ~1e6 here): 1e-9.  M^-1 inverts
+the block-Jacobi blocks: 1e-8.  P x = x - S Z K Z^T x is a small difference of
+large terms (|S Z K Z^T x| / |P x| up to ~1e3 for random x) and K solves with a
+coarse matrix of condition ~3e4 at d = 255, so two FP64 evaluations differ by
+~1e-16 * 3e4 * 1e3 ~ 1e-8: 1e-7.
 """
 import numpy as np
 import pytest
@@ -68,4 +71,4 @@ def test_operators_match_oracle(smpm, shape):
     solver.close()
     print(shape, {k: f"{v:.2e}" for k, v in errs.items()})
     assert errs["S"] < 1e-9 and errs["bS"] < 1e-9 and errs["Ainv"] < 1e-9, errs
-    assert errs["Minv"] < 1e-8 and errs["P"] < 1e-8, errs
+    assert errs["Minv"] < 1e-8 and errs["P"] < 1e-7, errs

@@ -98,7 +98,8 @@ def test_spectral_convergence_config1_shape():
         assert abs(np.dot(info["uL"], f)) / np.linalg.norm(f) < 1e-6
     errs = np.array(errs)
     assert errs[0] > 1e-4 and errs[-1] < 1e-9
-    assert np.all(errs[1:] < errs[:-1] * 0.5)       # geometric decay in the order
+    # geometric decay in the order until the round-off plateau (~1e-10 here)
+    assert np.all(errs[1:4] < errs[:3] * 1e-2)
 
 
 def test_helmholtz_spectral_convergence():
@@ -112,3 +113,17 @@ def test_helmholtz_spectral_convergence():
         u, _ = direct_solve(g, f, None, k2)
         errs.append(np.abs(u - ue).max())
     assert errs[0] > 1e-5 and errs[-1] < 1e-9 and errs[1] < errs[0] * 1e-2
+
+
+@pytest.mark.parametrize("shape", [(8, 2, 8, 4.0, 1.0, 1.0), (8, 4, 12, 2.0, 1.0, 1.0), (8, 8, 10, 2.0, 1.0, 1.0)])
+def test_default_penalty_has_no_antidamped_modes(shape):
+    """Stability reading of tau: at the default (negative) tau_scale the SMPM
+    operator has no eigenvalue with positive real part on the element shapes
+    of the 4x1, long-domain and 3-D workloads (so every Helmholtz shift k^2 > 0
+    gives a definite problem); with a positive tau the inter-element jump
+    modes come out anti-damped."""
+    mx, mz, order, lx, lz, zr = shape
+    ev = np.linalg.eigvals(assemble_L(Grid(mx, mz, order, lx, lz, z_ratio=zr)).toarray())
+    assert ev.real.max() < 1e-8 * np.abs(ev).max()
+    ev_pos = np.linalg.eigvals(assemble_L(Grid(mx, mz, order, lx, lz, z_ratio=zr, tau_scale=10.0)).toarray())
+    assert ev_pos.real.max() > 1e2
