@@ -66,6 +66,16 @@ struct Solver {
     std::vector<int> strip_cls, pair_mc, mc_single;
     long long kp = 0, ld = 0;
     int restart = 64, max_iter = 2000;
+    // fast strip solver (x-factor block diagonalisation; see kernels.cu)
+    bool fss = false;
+    double *d_Q = nullptr, *d_Qinv = nullptr, *d_beta = nullptr;   // [3][n][n], [3][n][n], [3][2][n]
+    std::vector<int> sl_start[3], sl_size[3], sl_idx[3];             // per class: slot start, size, index in its size list
+    int ns1 = 0, ns2 = 0;                                            // max size-1 / size-2 slots over the classes
+    double *S1 = nullptr, *S2 = nullptr;                             // slot inverses [nop][3][ns][m*m]
+    int *rl_S1 = nullptr, *rh_S1 = nullptr, *rl_S2 = nullptr, *rh_S2 = nullptr;
+    int* d_cls3 = nullptr;                                           // {0, 1, 2}
+    double *d_Ax3 = nullptr, *d_Lz = nullptr;                        // x-factors [3][n][n], z-operator [fz][fz]
+    int *d_zlo = nullptr, *d_zhi = nullptr;                          // nonzero window of each L_z row
     // device operators (all ops, contiguous per kind)
     double *Ainv = nullptr, *W = nullptr, *G = nullptr, *Minv = nullptr, *rho = nullptr, *K = nullptr;
     double *uL = nullptr, *uS = nullptr;
@@ -85,8 +95,10 @@ struct Solver {
         double *target = nullptr, *bnorm = nullptr, *rnorm = nullptr;
         const double** uLp = nullptr;
         const double** uSp = nullptr;
-        Tile *tM = nullptr, *tG = nullptr, *tW = nullptr, *tA = nullptr;
-        int ntM = 0, ntG = 0, ntW = 0, ntA = 0;
+        Tile *tM = nullptr, *tG = nullptr, *tW = nullptr, *tA = nullptr, *tS1 = nullptr, *tS2 = nullptr;
+        int ntM = 0, ntG = 0, ntW = 0, ntA = 0, ntS1 = 0, ntS2 = 0;
+        size_t capS1 = 0, capS2 = 0;
+        double *fs1 = nullptr, *fs2 = nullptr, *fs3 = nullptr, *k2r = nullptr;
         std::vector<void*> allocs;
     } wk;
     std::vector<int> cur_ops;               // op layout the tiles were built for
@@ -151,6 +163,77 @@ static void invert_dense(Solver& S, double* src, double* dst, int m, double* wor
     if (h_info != 0) throw Err{SMPM_EBREAKDOWN, "singular strip or block-Jacobi matrix (getrf info " + std::to_string(h_info) + ")"};
 }
 
+static void run_gemm(Solver& S, GemmArgs a, const Tile* tiles, int ntiles, int epi);
+
+// Fast strip solve out = A_c(k)^-1 (in - E x_S) on nstrips strips (classes in fa.cls)
+// for R right-hand sides: x-transform by Q^-1, the slot inverses of B_c (+) L_z - k^2
+// (class GEMMs over the size-1 and size-2 slots), x-transform by Q.
+static void fss_run(Solver& S, const FssArgs& fa, int R, const double* in, long long in_ld, double* out,
+                    long long out_ld, const double* xS, long long x_ld, double* t1, double* t2, const Tile* tS1,
+                    int nS1, const Tile* tS2, int nS2, bool accumulate = false) {
+    const int fz = S.g.fz, n = S.g.n;
+    const long long nfz = (long long)n * fz, ld = (long long)fa.nstrips * nfz;
+    k_xform(fa, R, S.d_Qinv, in, in_ld, t1, ld, xS, x_ld, S.stream);
+    for (int sz = 1; sz <= 2; ++sz) {
+        GemmArgs a;
+        std::memset(&a, 0, sizeof(a));
+        a.mats = sz == 1 ? S.S1 : S.S2;
+        a.mat_stride = (long long)sz * fz * sz * fz;
+        a.M = a.K = sz * fz;
+        a.row_lo = sz == 1 ? S.rl_S1 : S.rl_S2;
+        a.row_hi = sz == 1 ? S.rh_S1 : S.rh_S2;
+        a.in = t1; a.in_rs = ld; a.in_us = nfz; a.in_off = 0;
+        a.out = t2; a.out_rs = ld; a.out_us = nfz; a.out_off0 = 0; a.out_off1 = 0; a.msplit = sz * fz;
+        run_gemm(S, a, sz == 1 ? tS1 : tS2, sz == 1 ? nS1 : nS2, 0);
+    }
+    k_xform(fa, R, S.d_Q, t2, ld, out, out_ld, nullptr, 0, S.stream, accumulate ? out : nullptr, out_ld);
+}
+
+// Fast strip solve with one step of iterative refinement: x0 = FSS(b - E x_S),
+// res = (b - E x_S) - A_c(k) x0 in FP64 through the Kronecker-sum structure,
+// out = x0 + FSS(res).  The slot inverses (L_z + (alpha - k^2) I)^-1 are
+// individually ill-conditioned (~1e6), so one unrefined pass is accurate to
+// ~1e-10 only; the refined result matches a dense LU solve (~1e-13).
+static void fss_refined(Solver& S, const FssArgs& fa, int R, const double* in, long long in_ld, double* out,
+                        long long out_ld, const double* xS, long long x_ld, const double* k2r, double* t1, double* t2,
+                        double* t3, const Tile* tS1, int nS1, const Tile* tS2, int nS2) {
+    const long long ld = (long long)fa.nstrips * S.g.n * S.g.fz;
+    fss_run(S, fa, R, in, in_ld, out, out_ld, xS, x_ld, t1, t2, tS1, nS1, tS2, nS2);
+    k_strip_residual(fa, R, S.d_Ax3, S.d_Lz, S.d_zlo, S.d_zhi, k2r, in, in_ld, xS, x_ld, out, out_ld, t3, ld, S.stream);
+    fss_run(S, fa, R, t3, ld, out, out_ld, nullptr, 0, t1, t2, tS1, nS1, tS2, nS2, true);
+}
+
+// Slot tiles of one class on a single strip for R right-hand sides of operator o.
+static std::vector<Tile> single_strip_slot_tiles(const Solver& S, int o, int c, int R, int sz) {
+    std::vector<Tile> out;
+    const int ns = std::max(sz == 1 ? S.ns1 : S.ns2, 1);
+    for (size_t t = 0; t < S.sl_size[c].size(); ++t) {
+        if (S.sl_size[c][t] != sz) continue;
+        for (int rr = 0; rr < R; rr += kBN)
+            out.push_back(Tile{(o * 3 + c) * ns + S.sl_idx[c][t], 0, 1, rr, std::min(kBN, R - rr),
+                               (long long)S.sl_start[c][t] * S.g.fz});
+    }
+    return out;
+}
+
+// A_c(k)^-1 of R strip vectors (one strip of class c, operator o), for setup.
+static void fss_single(Solver& S, int o, int c, int R, const double* in, double* out, double* t1, double* t2,
+                       std::vector<void*>& tmp) {
+    FssArgs fa{S.g.n, S.g.fz, 1, S.d_cls3 + c};
+    auto t1v = single_strip_slot_tiles(S, o, c, R, 1);
+    auto t2v = single_strip_slot_tiles(S, o, c, R, 2);
+    Tile* d1 = S.dalloc<Tile>(std::max<size_t>(t1v.size(), 1), tmp);
+    Tile* d2 = S.dalloc<Tile>(std::max<size_t>(t2v.size(), 1), tmp);
+    if (!t1v.empty()) CK(cudaMemcpyAsync(d1, t1v.data(), t1v.size() * sizeof(Tile), cudaMemcpyHostToDevice, S.stream));
+    if (!t2v.empty()) CK(cudaMemcpyAsync(d2, t2v.data(), t2v.size() * sizeof(Tile), cudaMemcpyHostToDevice, S.stream));
+    const long long nfz = (long long)S.g.n * S.g.fz;
+    double* k2r = S.dalloc<double>((size_t)R, tmp);
+    k_fill(k2r, R, S.k2[o], S.stream);
+    double* t3 = S.dalloc<double>((size_t)R * nfz, tmp);
+    fss_refined(S, fa, R, in, nfz, out, nfz, nullptr, 0, k2r, t1, t2, t3, d1, (int)t1v.size(), d2, (int)t2v.size());
+    CK(cudaStreamSynchronize(S.stream));
+}
+
 static void setup_solver(Solver& S) {
     auto t0 = std::chrono::steady_clock::now();
     Geometry& g = S.g;
@@ -189,8 +272,78 @@ static void setup_solver(Solver& S) {
     S.sM = (long long)f4 * f4;
     S.sRho = 3LL * 2 * ng * f2;
     S.sK = (long long)d * d;
-    S.Ainv = S.dalloc<double>((size_t)nop * 3 * S.sA, S.allocs);
-    S.W = S.dalloc<double>((size_t)nop * 3 * S.sW, S.allocs);
+    // 1-D factors (host)
+    std::vector<double> Ax[3], beta[3], Lz;
+    for (int c = 0; c < 3; ++c) {
+        strip_x_operator(g, c, Ax[c]);
+        face_flux_rows(g, c, beta[c]);
+    }
+    z_operator(g, Lz);
+    // fast strip solver: block-diagonalise the three n x n x-factors (k-independent)
+    std::vector<double> Qh[3], Qih[3], al[3], be[3];
+    S.fss = true;
+    for (int c = 0; c < 3 && S.fss; ++c) {
+        std::string msg;
+        if (!real_block_diagonalise(Ax[c], n, Qh[c], Qih[c], S.sl_start[c], S.sl_size[c], al[c], be[c], msg))
+            S.fss = false;
+    }
+    if (S.fss) {
+        S.ns1 = S.ns2 = 0;
+        for (int c = 0; c < 3; ++c) {
+            int c1 = 0, c2 = 0;
+            S.sl_idx[c].resize(S.sl_size[c].size());
+            for (size_t t = 0; t < S.sl_size[c].size(); ++t) S.sl_idx[c][t] = S.sl_size[c][t] == 1 ? c1++ : c2++;
+            S.ns1 = std::max(S.ns1, c1);
+            S.ns2 = std::max(S.ns2, c2);
+        }
+        S.S1 = S.dalloc<double>((size_t)nop * 3 * std::max(S.ns1, 1) * fz * fz, S.allocs);
+        S.S2 = S.dalloc<double>((size_t)nop * 3 * std::max(S.ns2, 1) * 4 * fz * fz, S.allocs);
+        std::vector<double> q3(3 * (size_t)n * n), qi3(3 * (size_t)n * n), b3(3 * 2 * (size_t)n);
+        for (int c = 0; c < 3; ++c) {
+            std::copy(Qh[c].begin(), Qh[c].end(), q3.begin() + (size_t)c * n * n);
+            std::copy(Qih[c].begin(), Qih[c].end(), qi3.begin() + (size_t)c * n * n);
+            std::copy(beta[c].begin(), beta[c].end(), b3.begin() + (size_t)c * 2 * n);
+        }
+        S.d_Q = S.dalloc<double>(q3.size(), S.allocs);
+        S.d_Qinv = S.dalloc<double>(qi3.size(), S.allocs);
+        S.d_beta = S.dalloc<double>(b3.size(), S.allocs);
+        upload(S.d_Q, q3, st);
+        upload(S.d_Qinv, qi3, st);
+        upload(S.d_beta, b3, st);
+        std::vector<double> ax3(3 * (size_t)n * n);
+        for (int c = 0; c < 3; ++c) std::copy(Ax[c].begin(), Ax[c].end(), ax3.begin() + (size_t)c * n * n);
+        S.d_Ax3 = S.dalloc<double>(ax3.size(), S.allocs);
+        upload(S.d_Ax3, ax3, st);
+        S.d_Lz = S.dalloc<double>(Lz.size(), S.allocs);
+        upload(S.d_Lz, Lz, st);
+        std::vector<int> zlo(fz, 0), zhi(fz, 0);
+        for (int Z = 0; Z < fz; ++Z) {
+            int lo = fz, hi = 0;
+            for (int j = 0; j < fz; ++j)
+                if (Lz[(size_t)Z * fz + j] != 0.0) { lo = std::min(lo, j); hi = std::max(hi, j + 1); }
+            zlo[Z] = lo < hi ? lo : 0;
+            zhi[Z] = hi;
+        }
+        S.d_zlo = S.dalloc<int>(fz, S.allocs);
+        S.d_zhi = S.dalloc<int>(fz, S.allocs);
+        CK(cudaMemcpyAsync(S.d_zlo, zlo.data(), fz * sizeof(int), cudaMemcpyHostToDevice, st));
+        CK(cudaMemcpyAsync(S.d_zhi, zhi.data(), fz * sizeof(int), cudaMemcpyHostToDevice, st));
+        CK(cudaStreamSynchronize(st));
+        std::vector<int> c3 = {0, 1, 2};
+        S.d_cls3 = S.dalloc<int>(3, S.allocs);
+        CK(cudaMemcpyAsync(S.d_cls3, c3.data(), 3 * sizeof(int), cudaMemcpyHostToDevice, st));
+        std::vector<int> lo1(nop * 3 * std::max(S.ns1, 1), 0), hi1(lo1.size(), fz);
+        std::vector<int> lo2(nop * 3 * std::max(S.ns2, 1), 0), hi2(lo2.size(), 2 * fz);
+        auto upi = [&](int*& dptr, const std::vector<int>& v) {
+            dptr = S.dalloc<int>(v.size(), S.allocs);
+            CK(cudaMemcpyAsync(dptr, v.data(), v.size() * sizeof(int), cudaMemcpyHostToDevice, st));
+        };
+        upi(S.rl_S1, lo1); upi(S.rh_S1, hi1); upi(S.rl_S2, lo2); upi(S.rh_S2, hi2);
+        CK(cudaStreamSynchronize(st));
+    } else {
+        S.Ainv = S.dalloc<double>((size_t)nop * 3 * S.sA, S.allocs);
+        S.W = S.dalloc<double>((size_t)nop * 3 * S.sW, S.allocs);
+    }
     S.G = S.dalloc<double>((size_t)nop * 3 * S.sG, S.allocs);
     S.Minv = S.dalloc<double>((size_t)nop * S.nmc * S.sM, S.allocs);
     S.rho = S.dalloc<double>((size_t)nop * S.sRho, S.allocs);
@@ -226,13 +379,6 @@ static void setup_solver(Solver& S) {
     upload(S.d_hz, g.hz, st);
     upload(S.d_wq, g.w, st);
 
-    // 1-D factors (host), uploaded once
-    std::vector<double> Ax[3], beta[3], Lz;
-    for (int c = 0; c < 3; ++c) {
-        strip_x_operator(g, c, Ax[c]);
-        face_flux_rows(g, c, beta[c]);
-    }
-    z_operator(g, Lz);
     std::vector<void*> tmp;
     double* dAx = S.dalloc<double>(3 * (size_t)n * n, tmp);
     double* dbeta = S.dalloc<double>(3 * 2 * (size_t)n, tmp);
@@ -244,11 +390,11 @@ static void setup_solver(Solver& S) {
     upload(dLz, Lz, st);
 
     // LU workspace sized for the largest matrix
-    const int mmax = std::max(nfz, f4);
+    const int mmax = S.fss ? f4 : std::max(nfz, f4);
     double* dtmp = S.dalloc<double>((size_t)mmax * mmax, tmp);
     double* dtmp2 = S.dalloc<double>((size_t)f4 * f4, tmp);
     int lwork = 0, lw2 = 0;
-    CS(cusolverDnDgetrf_bufferSize(S.sol, nfz, nfz, dtmp, nfz, &lwork));
+    CS(cusolverDnDgetrf_bufferSize(S.sol, mmax, mmax, dtmp, mmax, &lwork));
     CS(cusolverDnDgetrf_bufferSize(S.sol, f4, f4, dtmp, f4, &lw2));
     lwork = std::max(lwork, lw2);
     double* dwork = S.dalloc<double>((size_t)std::max(lwork, 1), tmp);
@@ -290,10 +436,37 @@ static void setup_solver(Solver& S) {
 
     for (int o = 0; o < nop; ++o) {
         const double k2 = S.k2[o];
-        double* Ainv = S.Ainv + (size_t)o * 3 * S.sA;
-        double* W = S.W + (size_t)o * 3 * S.sW;
         double* G = S.G + (size_t)o * 3 * S.sG;
-        for (int c = 0; c < 3; ++c) {
+        if (S.fss) {
+            // slot inverses of B_c (+) L_z - k^2 (Sec. 5: only the shift depends on k)
+            for (int c = 0; c < 3; ++c)
+                for (size_t t = 0; t < S.sl_size[c].size(); ++t) {
+                    const int sz = S.sl_size[c][t], m = sz * fz, idx = S.sl_idx[c][t];
+                    k_build_slot(dtmp, dLz, fz, sz, al[c][t] - k2, be[c][t], st);
+                    double* dst = sz == 1 ? S.S1 + (((size_t)o * 3 + c) * std::max(S.ns1, 1) + idx) * fz * fz
+                                          : S.S2 + (((size_t)o * 3 + c) * std::max(S.ns2, 1) + idx) * 4 * fz * fz;
+                    invert_dense(S, dtmp, dst, m, dwork, lwork, dipiv, dinfo);
+                }
+            // G_c = B A_c^-1 E_c from fast solves of the 2 fz unit face vectors of one strip
+            double* U = S.dalloc<double>((size_t)f2 * nfz, tmp);
+            double* Y = S.dalloc<double>((size_t)f2 * nfz, tmp);
+            double* T1 = S.dalloc<double>((size_t)f2 * nfz, tmp);
+            double* T2 = S.dalloc<double>((size_t)f2 * nfz, tmp);
+            for (int c = 0; c < 3; ++c) {
+                if (c == 1 && mx < 3) {
+                    k_fill(G + c * S.sG, S.sG, 0.0, st);
+                    continue;
+                }
+                k_unit_faces(U, n, fz, st);
+                fss_single(S, o, c, f2, U, Y, T1, T2, tmp);
+                k_g_from_solves(G + c * S.sG, Y, S.d_beta + (size_t)c * 2 * n, n, fz, c, st);
+                k_build_rho(S.rho + (size_t)o * S.sRho + (size_t)c * 2 * ng * f2, G + c * S.sG, fz, ng, st);
+            }
+            CK(cudaStreamSynchronize(st));
+        }
+        for (int c = 0; c < 3 && !S.fss; ++c) {
+            double* Ainv = S.Ainv + (size_t)o * 3 * S.sA;
+            double* W = S.W + (size_t)o * 3 * S.sW;
             if (c == 1 && mx < 3) {  // no interior strips
                 k_fill(Ainv + c * S.sA, S.sA, 0.0, st);
                 k_fill(W + c * S.sW, S.sW, 0.0, st);
@@ -385,6 +558,8 @@ static void ensure_workspace(Solver& S, int R) {
     CK(cudaStreamSynchronize(S.stream));
     S.bytes -= S.wk_bytes;
     S.free_list(S.wk.allocs);
+    S.wk.tS1 = S.wk.tS2 = nullptr;
+    S.wk.capS1 = S.wk.capS2 = 0;
     const long long bytes_before = S.bytes;
     auto& w = S.wk;
     auto& L = w.allocs;
@@ -398,6 +573,12 @@ static void ensure_workspace(Solver& S, int R) {
     w.fstage = S.dalloc<double>((size_t)R * g.r, L);
     w.ustage = S.dalloc<double>((size_t)R * g.r, L);
     w.gstage = S.dalloc<double>((size_t)R * (2 * g.fz + 2 * g.nx), L);
+    if (S.fss) {
+        w.fs1 = S.dalloc<double>((size_t)R * g.r, L);
+        w.fs2 = S.dalloc<double>((size_t)R * g.r, L);
+        w.fs3 = S.dalloc<double>((size_t)R * g.r, L);
+        w.k2r = S.dalloc<double>((size_t)R, L);
+    }
     double** vecs[] = {&w.bS, &w.Xp, &w.t, &w.s, &w.w, &w.z, &w.xS};
     for (double** v : vecs) {
         *v = S.dalloc<double>((size_t)R * ld, L);
@@ -465,9 +646,55 @@ static std::vector<Tile> make_tiles(const std::vector<int>& unit_cls, int ncls, 
     return out;
 }
 
+static std::vector<Tile> make_slot_tiles(const Solver& S, const std::vector<int>& ops, int sz) {
+    std::vector<Tile> out;
+    const int R = (int)ops.size(), nu = (int)S.strip_cls.size();
+    const int ns = std::max(sz == 1 ? S.ns1 : S.ns2, 1);
+    int rb = 0;
+    while (rb < R) {
+        int re = rb;
+        while (re < R && ops[re] == ops[rb]) ++re;
+        int ub = 0;
+        while (ub < nu) {
+            int ue = ub;
+            while (ue < nu && S.strip_cls[ue] == S.strip_cls[ub]) ++ue;
+            const int c = S.strip_cls[ub];
+            for (size_t t = 0; t < S.sl_size[c].size(); ++t) {
+                if (S.sl_size[c][t] != sz) continue;
+                const int mat = (ops[rb] * 3 + c) * ns + S.sl_idx[c][t];
+                const long long off = (long long)S.sl_start[c][t] * S.g.fz;
+                for (int rr = rb; rr < re;) {
+                    const int nr = std::min(kBN, re - rr);
+                    const int upt = std::max(1, kBN / nr);
+                    for (int u = ub; u < ue; u += upt) out.push_back(Tile{mat, u, std::min(upt, ue - u), rr, nr, off});
+                    rr += nr;
+                }
+            }
+            ub = ue;
+        }
+        rb = re;
+    }
+    return out;
+}
+
 static void prepare_ops(Solver& S, const std::vector<int>& ops) {
     if (ops == S.cur_ops) return;
     auto& w = S.wk;
+    if (S.fss) {
+        for (int sz = 1; sz <= 2; ++sz) {
+            auto tv = make_slot_tiles(S, ops, sz);
+            Tile*& dt = sz == 1 ? w.tS1 : w.tS2;
+            int& nt = sz == 1 ? w.ntS1 : w.ntS2;
+            size_t& cap = sz == 1 ? w.capS1 : w.capS2;
+            if (tv.size() > cap || dt == nullptr) {   // grow (the old list stays in the workspace until it is freed)
+                cap = std::max<size_t>(tv.size(), 1) * 2;
+                dt = S.dalloc<Tile>(cap, w.allocs);
+            }
+            if (!tv.empty())
+                CK(cudaMemcpyAsync(dt, tv.data(), tv.size() * sizeof(Tile), cudaMemcpyHostToDevice, S.stream));
+            nt = (int)tv.size();
+        }
+    }
     const int R = (int)ops.size();
     auto tS = make_tiles(S.strip_cls, 3, ops);
     auto tM = make_tiles(S.pair_mc, S.nmc, ops);
@@ -486,6 +713,12 @@ static void prepare_ops(Solver& S, const std::vector<int>& ops) {
             gauge[r] = 1;
         }
     CK(cudaMemcpyAsync(w.op, ops.data(), R * sizeof(int), cudaMemcpyHostToDevice, S.stream));
+    if (S.fss) {
+        std::vector<double> k2r(R);
+        for (int r = 0; r < R; ++r) k2r[r] = S.k2[ops[r]];
+        CK(cudaMemcpyAsync(w.k2r, k2r.data(), R * sizeof(double), cudaMemcpyHostToDevice, S.stream));
+        CK(cudaStreamSynchronize(S.stream));
+    }
     CK(cudaMemcpyAsync(w.gauge, gauge.data(), R * sizeof(int), cudaMemcpyHostToDevice, S.stream));
     CK(cudaMemcpyAsync(w.uLp, uLp.data(), R * sizeof(double*), cudaMemcpyHostToDevice, S.stream));
     CK(cudaMemcpyAsync(w.uSp, uSp.data(), R * sizeof(double*), cudaMemcpyHostToDevice, S.stream));
@@ -582,12 +815,19 @@ static int solve_impl(Solver& S, const std::vector<int>& ops, const double* f, c
     // Alg. seq steps 1-3
     k_rhs_assemble(ga, R, f_d, g.r, g_d, nb, w.b, g.r, w.uLp, w.rpart, rch, kChunk, st_);
     k_project(R, g.r, w.b, g.r, w.uLp, w.rpart, rch, kChunk, st_);
-    GemmArgs aW = gemm_base(S);
-    aW.mats = S.W; aW.mat_stride = S.sW; aW.M = f2; aW.K = nfz;
-    aW.row_lo = S.rl_GW; aW.row_hi = S.rh_GW;
-    aW.in = w.b; aW.in_rs = g.r; aW.in_us = nfz; aW.in_off = 0;
-    aW.out = w.bS; aW.out_rs = ld; aW.out_us = f2; aW.out_off0 = -fz; aW.out_off1 = f2; aW.msplit = fz;
-    run_gemm(S, aW, w.tW, w.ntW, 0);
+    const FssArgs fa{n, fz, g.mx, S.d_strip_cls};
+    if (S.fss) {  // b_S = B (A^-1 b): fast strip solves, then the face fluxes
+        fss_refined(S, fa, R, w.b, g.r, w.t2, g.r, nullptr, 0, w.k2r, w.fs1, w.fs2, w.fs3, w.tS1, w.ntS1, w.tS2,
+                    w.ntS2);
+        k_face_flux(fa, R, S.d_beta, w.t2, g.r, w.bS, ld, S.kp, st_);
+    } else {
+        GemmArgs aW = gemm_base(S);
+        aW.mats = S.W; aW.mat_stride = S.sW; aW.M = f2; aW.K = nfz;
+        aW.row_lo = S.rl_GW; aW.row_hi = S.rh_GW;
+        aW.in = w.b; aW.in_rs = g.r; aW.in_us = nfz; aW.in_off = 0;
+        aW.out = w.bS; aW.out_rs = ld; aW.out_us = f2; aW.out_off0 = -fz; aW.out_off1 = f2; aW.msplit = fz;
+        run_gemm(S, aW, w.tW, w.ntW, 0);
+    }
     k_dot_partial(R, S.kp, w.bS, ld, w.uSp, w.rpart, nch, kChunk, st_);
     k_project(R, S.kp, w.bS, ld, w.uSp, w.rpart, nch, kChunk, st_);
 
@@ -682,8 +922,10 @@ static int solve_impl(Solver& S, const std::vector<int>& ops, const double* f, c
         first = false;
     }
     // recovery: u = A^-1 (b - E x_S)  (Alg. seq step 9)
-    k_recovery_rhs(ga, R, w.b, g.r, w.xS, ld, w.t2, st_);
-    {
+    if (S.fss) {
+        fss_refined(S, fa, R, w.b, g.r, u_d, g.r, w.xS, ld, w.k2r, w.fs1, w.fs2, w.fs3, w.tS1, w.ntS1, w.tS2, w.ntS2);
+    } else {
+        k_recovery_rhs(ga, R, w.b, g.r, w.xS, ld, w.t2, st_);
         GemmArgs a = gemm_base(S);
         a.mats = S.Ainv; a.mat_stride = S.sA; a.M = nfz; a.K = nfz;
         a.row_lo = S.rl_A; a.row_hi = S.rh_A;
@@ -774,6 +1016,14 @@ static int apply_impl(Solver& S, int kind, int R, const double* in, double* out)
         k_deflate_sum(ka, w.w, nullptr, st_);
         k_coarse(ka, st_);
         k_cgs(ka, -1, 0, st_);  // w -= S Z c, no dot products
+    } else if (kind == 3 && S.fss) {
+        const FssArgs fa{g.n, fz, g.mx, S.d_strip_cls};
+        fss_refined(S, fa, R, w.t2, r, w.b, r, nullptr, 0, w.k2r, w.fs1, w.fs2, w.fs3, w.tS1, w.ntS1, w.tS2, w.ntS2);
+        k_face_flux(fa, R, S.d_beta, w.b, r, w.w, ld, S.kp, st_);
+    } else if (kind == 4 && S.fss) {
+        const FssArgs fa{g.n, fz, g.mx, S.d_strip_cls};
+        fss_refined(S, fa, R, w.t2, r, w.b, r, nullptr, 0, w.k2r, w.fs1, w.fs2, w.fs3, w.tS1, w.ntS1, w.tS2, w.ntS2);
+        res = w.b;
     } else if (kind == 3) {
         a.mats = S.W; a.mat_stride = S.sW; a.M = f2; a.K = nfz; a.row_lo = S.rl_GW; a.row_hi = S.rh_GW;
         a.in = w.t2; a.in_rs = r; a.in_us = nfz; a.in_off = 0;

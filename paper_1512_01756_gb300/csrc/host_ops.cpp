@@ -13,6 +13,8 @@
 
 #include <algorithm>
 #include <cmath>
+#include <complex>
+#include <cstdio>
 #include <functional>
 
 namespace smpm {
@@ -424,6 +426,212 @@ bool coarse_operator(const std::vector<double>& C, int d, int fz_over_ng, const 
             }
     }
     if (!dense_solve(A, d, K, d)) { msg = "coarse matrix factorisation hit a zero pivot"; return false; }
+    return true;
+}
+
+// --- real block diagonalisation of a small nonsymmetric matrix ----------------
+//
+// Ax = Q B Q^-1 with B block diagonal: a 1 x 1 block per real eigenvalue and a
+// 2 x 2 block [[alpha, beta], [-beta, alpha]] per complex pair alpha +- i beta,
+// whose columns in Q are (Re v, Im v) of the eigenvector of alpha + i beta.
+// Eigenvalues by the shifted QR iteration (Wilkinson shift, complex arithmetic,
+// deflation from the bottom), eigenvectors by inverse iteration.  Intended for
+// the n x n (n <= 33) strip x-factors; the caller checks ||Q B Q^-1 - Ax||.
+
+using cplx = std::complex<double>;
+
+static void qr_step(std::vector<cplx>& H, int n, int m, cplx mu) {
+    // one shifted QR step on the leading m x m block of the n x n row-major H
+    std::vector<cplx> A((size_t)m * m), Qm((size_t)m * m, 0.0);
+    for (int i = 0; i < m; ++i)
+        for (int j = 0; j < m; ++j) A[(size_t)i * m + j] = H[(size_t)i * n + j] - (i == j ? mu : 0.0);
+    // Householder QR: A = Q R, accumulate Q
+    for (int i = 0; i < m; ++i) Qm[(size_t)i * m + i] = 1.0;
+    for (int k = 0; k < m - 1; ++k) {
+        double nx = 0.0;
+        for (int i = k; i < m; ++i) nx += std::norm(A[(size_t)i * m + k]);
+        nx = std::sqrt(nx);
+        if (nx == 0.0) continue;
+        cplx a0 = A[(size_t)k * m + k];
+        cplx ph = std::abs(a0) > 0 ? a0 / std::abs(a0) : cplx(1.0, 0.0);
+        std::vector<cplx> v(m, 0.0);
+        v[k] = a0 + ph * nx;
+        for (int i = k + 1; i < m; ++i) v[i] = A[(size_t)i * m + k];
+        double vn = 0.0;
+        for (int i = k; i < m; ++i) vn += std::norm(v[i]);
+        if (vn == 0.0) continue;
+        for (int j = 0; j < m; ++j) {             // A <- (I - 2 v v^H / |v|^2) A
+            cplx s = 0.0;
+            for (int i = k; i < m; ++i) s += std::conj(v[i]) * A[(size_t)i * m + j];
+            s *= 2.0 / vn;
+            for (int i = k; i < m; ++i) A[(size_t)i * m + j] -= v[i] * s;
+        }
+        for (int i = 0; i < m; ++i) {             // Q <- Q (I - 2 v v^H / |v|^2)
+            cplx s = 0.0;
+            for (int j = k; j < m; ++j) s += Qm[(size_t)i * m + j] * v[j];
+            s *= 2.0 / vn;
+            for (int j = k; j < m; ++j) Qm[(size_t)i * m + j] -= s * std::conj(v[j]);
+        }
+    }
+    // H_m <- R Q + mu I
+    for (int i = 0; i < m; ++i)
+        for (int j = 0; j < m; ++j) {
+            cplx s = 0.0;
+            for (int l = i; l < m; ++l) s += A[(size_t)i * m + l] * Qm[(size_t)l * m + j];
+            H[(size_t)i * n + j] = s + (i == j ? mu : 0.0);
+        }
+}
+
+static bool eigenvalues(const std::vector<double>& Ax, int n, std::vector<cplx>& lam) {
+    std::vector<cplx> H((size_t)n * n);
+    double scale = 0.0;
+    for (int i = 0; i < n * n; ++i) {
+        H[i] = Ax[i];
+        scale = std::max(scale, std::fabs(Ax[i]));
+    }
+    lam.assign(n, 0.0);
+    int m = n, iters = 0;
+    while (m > 1) {
+        const cplx sub = H[(size_t)(m - 1) * n + (m - 2)];
+        double offrow = 0.0;
+        for (int j = 0; j < m - 1; ++j) offrow = std::max(offrow, std::abs(H[(size_t)(m - 1) * n + j]));
+        if (offrow <= 1e-15 * scale) {
+            lam[m - 1] = H[(size_t)(m - 1) * n + (m - 1)];
+            --m;
+            iters = 0;
+            continue;
+        }
+        (void)sub;
+        if (++iters > 200) return false;
+        // Wilkinson shift: eigenvalue of the trailing 2 x 2 closer to the corner
+        const cplx a = H[(size_t)(m - 2) * n + (m - 2)], b = H[(size_t)(m - 2) * n + (m - 1)];
+        const cplx c = H[(size_t)(m - 1) * n + (m - 2)], d = H[(size_t)(m - 1) * n + (m - 1)];
+        const cplx tr = a + d, det = a * d - b * c;
+        const cplx disc = std::sqrt(tr * tr - 4.0 * det);
+        const cplx l1 = 0.5 * (tr + disc), l2 = 0.5 * (tr - disc);
+        cplx mu = std::abs(l1 - d) < std::abs(l2 - d) ? l1 : l2;
+        if (iters % 11 == 10) mu += cplx(0.0, 1e-3 * scale * 1e-6);  // exceptional shift
+        qr_step(H, n, m, mu);
+    }
+    lam[0] = H[0];
+    return true;
+}
+
+// complex LU solve (A - mu I) x = b in place, A real n x n
+static bool shifted_solve(const std::vector<double>& Ax, int n, cplx mu, std::vector<cplx>& x) {
+    std::vector<cplx> A((size_t)n * n);
+    for (int i = 0; i < n; ++i)
+        for (int j = 0; j < n; ++j) A[(size_t)i * n + j] = Ax[(size_t)i * n + j] - (i == j ? mu : 0.0);
+    for (int k = 0; k < n; ++k) {
+        int p = k;
+        for (int i = k + 1; i < n; ++i)
+            if (std::abs(A[(size_t)i * n + k]) > std::abs(A[(size_t)p * n + k])) p = i;
+        if (std::abs(A[(size_t)p * n + k]) == 0.0) return false;
+        if (p != k) {
+            for (int j = 0; j < n; ++j) std::swap(A[(size_t)k * n + j], A[(size_t)p * n + j]);
+            std::swap(x[k], x[p]);
+        }
+        for (int i = k + 1; i < n; ++i) {
+            const cplx l = A[(size_t)i * n + k] / A[(size_t)k * n + k];
+            for (int j = k + 1; j < n; ++j) A[(size_t)i * n + j] -= l * A[(size_t)k * n + j];
+            x[i] -= l * x[k];
+        }
+    }
+    for (int k = n - 1; k >= 0; --k) {
+        cplx s = x[k];
+        for (int j = k + 1; j < n; ++j) s -= A[(size_t)k * n + j] * x[j];
+        x[k] = s / A[(size_t)k * n + k];
+    }
+    return true;
+}
+
+bool real_block_diagonalise(const std::vector<double>& Ax, int n, std::vector<double>& Q, std::vector<double>& Qinv,
+                            std::vector<int>& slot_start, std::vector<int>& slot_size, std::vector<double>& alpha,
+                            std::vector<double>& beta, std::string& msg) {
+    std::vector<cplx> lam;
+    if (!eigenvalues(Ax, n, lam)) { msg = "x-factor eigenvalue iteration did not converge"; return false; }
+    double scale = 0.0;
+    for (double v : Ax) scale = std::max(scale, std::fabs(v));
+    // order: real eigenvalues and one representative (Im > 0) per complex pair
+    std::vector<cplx> reps;
+    std::vector<bool> used(n, false);
+    for (int i = 0; i < n; ++i) {
+        if (used[i]) continue;
+        used[i] = true;
+        if (std::fabs(lam[i].imag()) <= 1e-10 * std::abs(lam[i]) + 1e-14 * scale) {
+            reps.push_back(cplx(lam[i].real(), 0.0));
+            continue;
+        }
+        int best = -1;
+        double bd = 1e300;
+        for (int j = 0; j < n; ++j)
+            if (!used[j] && std::abs(lam[j] - std::conj(lam[i])) < bd) { bd = std::abs(lam[j] - std::conj(lam[i])); best = j; }
+        if (best < 0 || bd > 1e-6 * std::abs(lam[i])) { msg = "unpaired complex eigenvalue"; return false; }
+        used[best] = true;
+        reps.push_back(lam[i].imag() > 0 ? lam[i] : std::conj(lam[i]));
+    }
+    Q.assign((size_t)n * n, 0.0);
+    slot_start.clear(); slot_size.clear(); alpha.clear(); beta.clear();
+    int col = 0;
+    for (const cplx& l : reps) {
+        std::vector<cplx> v(n);
+        for (int i = 0; i < n; ++i) v[i] = cplx(1.0 + 0.1 * std::sin(1.0 + 7.0 * i), 0.3 * std::cos(2.0 + 5.0 * i));
+        const cplx mu = l + cplx(1e-12 * scale, 1e-12 * scale);
+        for (int it = 0; it < 3; ++it) {
+            if (!shifted_solve(Ax, n, mu, v)) { msg = "eigenvector solve failed"; return false; }
+            double nv = 0.0;
+            for (const cplx& x : v) nv += std::norm(x);
+            nv = std::sqrt(nv);
+            for (cplx& x : v) x /= nv;
+        }
+        // rotate the phase so the largest entry is real
+        int im = 0;
+        for (int i = 1; i < n; ++i) if (std::abs(v[i]) > std::abs(v[im])) im = i;
+        const cplx ph = std::conj(v[im]) / std::abs(v[im]);
+        for (cplx& x : v) x *= ph;
+        if (l.imag() == 0.0) {
+            if (col >= n) { msg = "too many eigenvectors"; return false; }
+            double nr = 0.0;
+            for (int i = 0; i < n; ++i) nr += v[i].real() * v[i].real();
+            nr = std::sqrt(nr);
+            for (int i = 0; i < n; ++i) Q[(size_t)i * n + col] = v[i].real() / nr;
+            slot_start.push_back(col); slot_size.push_back(1); alpha.push_back(l.real()); beta.push_back(0.0);
+            col += 1;
+        } else {
+            if (col + 1 >= n) { msg = "too many eigenvectors"; return false; }
+            for (int i = 0; i < n; ++i) {
+                Q[(size_t)i * n + col] = v[i].real();
+                Q[(size_t)i * n + col + 1] = v[i].imag();
+            }
+            slot_start.push_back(col); slot_size.push_back(2); alpha.push_back(l.real()); beta.push_back(l.imag());
+            col += 2;
+        }
+    }
+    if (col != n) { msg = "eigenvector count mismatch"; return false; }
+    std::vector<double> A = Q;
+    Qinv.assign((size_t)n * n, 0.0);
+    for (int i = 0; i < n; ++i) Qinv[(size_t)i * n + i] = 1.0;
+    if (!dense_solve(A, n, Qinv, n)) { msg = "eigenvector matrix singular"; return false; }
+    // check Q B Q^-1 = Ax
+    double err = 0.0;
+    for (int i = 0; i < n; ++i)
+        for (int j = 0; j < n; ++j) {
+            double s = 0.0;
+            for (size_t t = 0; t < slot_start.size(); ++t) {
+                const int c0 = slot_start[t];
+                if (slot_size[t] == 1) {
+                    s += Q[(size_t)i * n + c0] * alpha[t] * Qinv[(size_t)c0 * n + j];
+                } else {
+                    const double a = alpha[t], b = beta[t];
+                    const double q0 = Q[(size_t)i * n + c0], q1 = Q[(size_t)i * n + c0 + 1];
+                    const double r0 = Qinv[(size_t)c0 * n + j], r1 = Qinv[(size_t)(c0 + 1) * n + j];
+                    s += q0 * (a * r0 + b * r1) + q1 * (-b * r0 + a * r1);
+                }
+            }
+            err = std::max(err, std::fabs(s - Ax[(size_t)i * n + j]));
+        }
+    if (!(err <= 1e-10 * scale)) { msg = "x-factor block diagonalisation check failed: " + std::to_string(err / scale); return false; }
+    { char buf[32]; snprintf(buf, sizeof buf, "%.2e", err / scale); msg = buf; }
     return true;
 }
 

@@ -84,7 +84,7 @@ __global__ void __launch_bounds__(GT) class_gemm_kernel(GemmArgs a, const Tile* 
         colp[l] = nullptr;
         if (c < ncol) {
             const int u = t.u0 + c / t.nr, r = t.r0 + c % t.nr;
-            colp[l] = a.in + (long long)r * a.in_rs + (long long)u * a.in_us + a.in_off;
+            colp[l] = a.in + (long long)r * a.in_rs + (long long)u * a.in_us + a.in_off + t.off;
         }
     }
     for (int k0 = 0; k0 < a.K; k0 += BK) {
@@ -121,7 +121,7 @@ __global__ void __launch_bounds__(GT) class_gemm_kernel(GemmArgs a, const Tile* 
         if (c >= ncol) continue;
         const int u = t.u0 + c / t.nr, r = t.r0 + c % t.nr;
         if (a.active && !a.active[r]) continue;
-        const long long base = (long long)r * a.out_rs + (long long)u * a.out_us;
+        const long long base = (long long)r * a.out_rs + (long long)u * a.out_us + t.off;
         const long long addr = base + (row < a.msplit ? a.out_off0 + row : a.out_off1 + (row - a.msplit));
         double v = acc[j];
         if (EPI == 1) v += a.add[addr];
@@ -831,6 +831,185 @@ __global__ void fill_kernel(double* x, long long n, double v) {
 void k_fill(double* x, long long n, double v, cudaStream_t s) {
     if (n <= 0) return;
     fill_kernel<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(x, n, v);
+    count_launches(1);
+}
+
+// ---------------------------------------------------------------------------
+// Fast strip solver: A_c(k)^-1 = (Q_c (x) I) (B_c (+) L_z - k^2)^-1 (Q_c^-1 (x) I)
+// with Ax_c = Q_c B_c Q_c^-1 (real block form).  The x-transforms below apply
+// an n x n class matrix along every x-line of every strip; the block solves
+// are class GEMMs over the slots of B_c.
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(VB) xform_kernel(FssArgs f, const double* __restrict__ T, const double* __restrict__ in,
+                                                  long long in_ld, double* __restrict__ out, long long out_ld,
+                                                  const double* __restrict__ xS, long long x_ld,
+                                                  const double* __restrict__ addv, long long add_ld) {
+    extern __shared__ double Ts[];                       // [3][n][n]
+    const int n = f.n, fz = f.fz;
+    for (int i = threadIdx.x; i < 3 * n * n; i += VB) Ts[i] = T[i];
+    __syncthreads();
+    const int r = blockIdx.y;
+    const long long line = (long long)blockIdx.x * VB + threadIdx.x;   // strip * fz + Z
+    if (line >= (long long)f.nstrips * fz) return;
+    const int strip = (int)(line / fz), Z = (int)(line - (long long)strip * fz);
+    const double* Tc = Ts + f.cls[strip] * n * n;
+    const double* src = in + (long long)r * in_ld + (long long)strip * n * fz + Z;
+    double u[33];
+#pragma unroll 4
+    for (int b = 0; b < n; ++b) u[b] = src[(long long)b * fz];
+    if (xS) {   // recovery input b - E x_S: x_S on the strip's west (a = 0) and east (a = N) faces
+        const double* x = xS + (long long)r * x_ld;
+        u[0] -= x[(long long)(2 * strip) * fz + Z];
+        u[n - 1] -= x[(long long)(2 * strip + 1) * fz + Z];
+    }
+    double* dst = out + (long long)r * out_ld + (long long)strip * n * fz + Z;
+    const double* ad = addv ? addv + (long long)r * add_ld + (long long)strip * n * fz + Z : nullptr;
+    for (int a = 0; a < n; ++a) {
+        double s = ad ? ad[(long long)a * fz] : 0.0;
+        for (int b = 0; b < n; ++b) s = fma(Tc[a * n + b], u[b], s);
+        dst[(long long)a * fz] = s;
+    }
+}
+
+void k_xform(const FssArgs& f, int R, const double* T, const double* in, long long in_ld, double* out,
+             long long out_ld, const double* xS, long long x_ld, cudaStream_t s, const double* addv, long long add_ld) {
+    dim3 grid((unsigned)(((long long)f.nstrips * f.fz + VB - 1) / VB), R);
+    xform_kernel<<<grid, VB, (size_t)3 * f.n * f.n * sizeof(double), s>>>(f, T, in, in_ld, out, out_ld, xS, x_ld,
+                                                                            addv, add_ld);
+    count_launches(1);
+}
+
+// Residual of the strip systems in FP64: res = (b - E x_S) - A_c(k) x with
+// A_c(k) = Ax_c (+) L_z - k^2 applied through its Kronecker-sum structure
+// (n + |window| FMAs per node: L_z row Z is nonzero only on [zlo[Z], zhi[Z])).
+__global__ void __launch_bounds__(VB) strip_residual_kernel(FssArgs f, const double* __restrict__ Ax3,
+                                                           const double* __restrict__ Lz, const int* __restrict__ zlo,
+                                                           const int* __restrict__ zhi, const double* __restrict__ k2r,
+                                                           const double* __restrict__ b, long long b_ld,
+                                                           const double* __restrict__ xS, long long x_ld,
+                                                           const double* __restrict__ x, long long xv_ld,
+                                                           double* __restrict__ res, long long r_ld) {
+    const int r = blockIdx.y;
+    const int n = f.n, fz = f.fz;
+    const long long node = (long long)blockIdx.x * VB + threadIdx.x;
+    const long long per = (long long)n * fz;
+    if (node >= (long long)f.nstrips * per) return;
+    const int strip = (int)(node / per);
+    const int rem = (int)(node - (long long)strip * per);
+    const int a = rem / fz, Z = rem - a * fz;
+    const double* xs = x + (long long)r * xv_ld + (long long)strip * per;
+    const double* Axc = Ax3 + (long long)f.cls[strip] * n * n + a * n;
+    double ax = 0.0;
+    for (int bb = 0; bb < n; ++bb) ax = fma(Axc[bb], xs[(long long)bb * fz + Z], ax);
+    const double* lz = Lz + (long long)Z * fz;
+    const double* xa = xs + (long long)a * fz;
+    for (int zz = zlo[Z]; zz < zhi[Z]; ++zz) ax = fma(lz[zz], xa[zz], ax);
+    ax -= k2r[r] * xa[Z];
+    double bv = b[(long long)r * b_ld + node];
+    if (xS) {
+        const double* xsr = xS + (long long)r * x_ld;
+        if (a == 0) bv -= xsr[(long long)(2 * strip) * fz + Z];
+        if (a == n - 1) bv -= xsr[(long long)(2 * strip + 1) * fz + Z];
+    }
+    res[(long long)r * r_ld + node] = bv - ax;
+}
+
+void k_strip_residual(const FssArgs& f, int R, const double* Ax3, const double* Lz, const int* zlo, const int* zhi,
+                      const double* k2r, const double* b, long long b_ld, const double* xS, long long x_ld,
+                      const double* x, long long xv_ld, double* res, long long r_ld, cudaStream_t s) {
+    const long long tot = (long long)f.nstrips * f.n * f.fz;
+    dim3 grid((unsigned)((tot + VB - 1) / VB), R);
+    strip_residual_kernel<<<grid, VB, 0, s>>>(f, Ax3, Lz, zlo, zhi, k2r, b, b_ld, xS, x_ld, x, xv_ld, res, r_ld);
+    count_launches(1);
+}
+
+// b_S = B y: face (strip i, side s) receives -tau (u +- d/dx u) of the neighbour
+// strip's solution y at the coincident face, i.e. sum_a beta_c[.][a] y[a][Z].
+__global__ void __launch_bounds__(VB) face_flux_kernel(FssArgs f, const double* __restrict__ beta,
+                                                      const double* __restrict__ y, long long y_ld,
+                                                      double* __restrict__ bS, long long b_ld, long long kp) {
+    const int r = blockIdx.y;
+    const long long e = (long long)blockIdx.x * VB + threadIdx.x;
+    if (e >= kp) return;
+    const int n = f.n, fz = f.fz;
+    const int F = (int)(e / fz), Z = (int)(e - (long long)F * fz);
+    const int i = F >> 1, side = F & 1;
+    double v = 0.0;
+    if (F > 0 && F < 2 * f.nstrips - 1) {
+        const int src = side == 1 ? i + 1 : i - 1;      // neighbour strip
+        const int sel = side == 1 ? 0 : 1;              // its flux onto its west / east neighbour
+        const double* bt = beta + (f.cls[src] * 2 + sel) * n;
+        const double* ys = y + (long long)r * y_ld + (long long)src * n * fz + Z;
+        for (int a = 0; a < n; ++a) v = fma(bt[a], ys[(long long)a * fz], v);
+    }
+    bS[(long long)r * b_ld + e] = v;
+}
+
+void k_face_flux(const FssArgs& f, int R, const double* beta, const double* y, long long y_ld, double* bS,
+                 long long b_ld, long long kp, cudaStream_t s) {
+    dim3 grid((unsigned)((kp + VB - 1) / VB), R);
+    face_flux_kernel<<<grid, VB, 0, s>>>(f, beta, y, y_ld, bS, b_ld, kp);
+    count_launches(1);
+}
+
+// Slot matrix of B_c (+) L_z - k^2: size 1: L_z + (alpha - k^2) I (fz x fz);
+// size 2: [[L_z + (alpha - k^2) I, beta I], [-beta I, L_z + (alpha - k^2) I]].
+__global__ void build_slot_kernel(double* __restrict__ M, const double* __restrict__ Lz, int fz, int size,
+                                  double shift, double beta) {
+    const int m = size * fz;
+    const long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx >= (long long)m * m) return;
+    const int row = (int)(idx / m), col = (int)(idx - (long long)row * m);
+    const int bi = row / fz, zi = row - bi * fz, bj = col / fz, zj = col - bj * fz;
+    double v = 0.0;
+    if (bi == bj) v = Lz[(long long)zi * fz + zj] + (zi == zj ? shift : 0.0);
+    else if (zi == zj) v = (bi == 0) ? beta : -beta;
+    M[idx] = v;
+}
+
+void k_build_slot(double* M, const double* Lz, int fz, int size, double shift, double beta, cudaStream_t s) {
+    const long long tot = (long long)size * fz * size * fz;
+    build_slot_kernel<<<(unsigned)((tot + 255) / 256), 256, 0, s>>>(M, Lz, fz, size, shift, beta);
+    count_launches(1);
+}
+
+// Unit right-hand sides for the Schur blocks: column j < fz is the west-face
+// node (a = 0, Z = j) of one strip, column j >= fz the east-face node (a = N).
+__global__ void unit_faces_kernel(double* __restrict__ U, int n, int fz) {
+    const long long nfz = (long long)n * fz;
+    const long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx >= 2LL * fz * nfz) return;
+    const int j = (int)(idx / nfz);
+    const long long p = idx - (long long)j * nfz;
+    const long long hot = j < fz ? (long long)j : (long long)(n - 1) * fz + (j - fz);
+    U[idx] = (p == hot) ? 1.0 : 0.0;
+}
+
+void k_unit_faces(double* U, int n, int fz, cudaStream_t s) {
+    const long long tot = 2LL * fz * n * fz;
+    unit_faces_kernel<<<(unsigned)((tot + 255) / 256), 256, 0, s>>>(U, n, fz);
+    count_launches(1);
+}
+
+// G_c[(s, Z)][j] = sum_a beta_c[s][a] Y_j[a][Z] (Y_j = A_c^-1 of unit column j);
+// the physical face's columns of a boundary class are zero.
+__global__ void g_from_solves_kernel(double* __restrict__ G, const double* __restrict__ Y, const double* __restrict__ beta,
+                                     int n, int fz, int cls) {
+    const int f2 = 2 * fz;
+    const int idx = blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx >= f2 * f2) return;
+    const int row = idx / f2, j = idx - row * f2;
+    const int s = row / fz, Z = row - s * fz;
+    const double* y = Y + (long long)j * n * fz + Z;
+    double v = 0.0;
+    for (int a = 0; a < n; ++a) v = fma(beta[s * n + a], y[(long long)a * fz], v);
+    if ((cls == 0 && j < fz) || (cls == 2 && j >= fz)) v = 0.0;
+    G[idx] = v;
+}
+
+void k_g_from_solves(double* G, const double* Y, const double* beta, int n, int fz, int cls, cudaStream_t s) {
+    const int tot = 4 * fz * fz;
+    g_from_solves_kernel<<<(tot + 255) / 256, 256, 0, s>>>(G, Y, beta, n, fz, cls);
     count_launches(1);
 }
 

@@ -102,6 +102,27 @@ void k_pad_block(double* dst, const double* src, int m_src, int m_dst, cudaStrea
 void k_build_rho(double* rho, const double* G, int fz, int ng, cudaStream_t s);
 void k_fill(double* x, long long n, double v, cudaStream_t s);
 
+// Fast strip solver pieces.
+struct FssArgs {
+    int n, fz, nstrips;
+    const int* cls;                // [nstrips] class of each strip (device)
+};
+// out[r][strip][a][Z] = sum_b T_cls[a][b] (in[r][strip][b][Z] - (E x_S)[...]);
+// T holds the 3 class matrices [3][n][n]; xS (face layout) may be null.
+void k_xform(const FssArgs& f, int R, const double* T, const double* in, long long in_ld, double* out,
+             long long out_ld, const double* xS, long long x_ld, cudaStream_t s, const double* addv = nullptr,
+             long long add_ld = 0);
+// res = (b - E x_S) - A_c(k) x per strip (k^2 per right-hand side in k2r).
+void k_strip_residual(const FssArgs& f, int R, const double* Ax3, const double* Lz, const int* zlo, const int* zhi,
+                      const double* k2r, const double* b, long long b_ld, const double* xS, long long x_ld,
+                      const double* x, long long xv_ld, double* res, long long r_ld, cudaStream_t s);
+// b_S = B y on the padded face layout (beta: [3][2][n]).
+void k_face_flux(const FssArgs& f, int R, const double* beta, const double* y, long long y_ld, double* bS,
+                 long long b_ld, long long kp, cudaStream_t s);
+void k_build_slot(double* M, const double* Lz, int fz, int size, double shift, double beta, cudaStream_t s);
+void k_unit_faces(double* U, int n, int fz, cudaStream_t s);
+void k_g_from_solves(double* G, const double* Y, const double* beta, int n, int fz, int cls, cudaStream_t s);
+
 // FP64 DFMA throughput probe: each thread runs `iters` dependent-chain-free
 // FMA groups; returns nothing, writes a checksum to out.
 void k_fp64_probe(double* out, int blocks, int iters, cudaStream_t s);

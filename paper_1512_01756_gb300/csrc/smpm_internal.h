@@ -75,6 +75,13 @@ bool left_null_z(const Geometry& g, std::vector<double>& v, std::string& msg);
 bool coarse_operator(const std::vector<double>& C, int d, int fz_over_ng, const double* uC,
                      std::vector<double>& K, std::string& msg);
 
+// Ax = Q B Q^-1 with B block diagonal in real form: slot t covers columns
+// [slot_start, slot_start + slot_size) of Q; size 1: eigenvalue alpha; size 2:
+// the pair alpha +- i beta as the block [[alpha, beta], [-beta, alpha]].
+bool real_block_diagonalise(const std::vector<double>& Ax, int n, std::vector<double>& Q, std::vector<double>& Qinv,
+                            std::vector<int>& slot_start, std::vector<int>& slot_size, std::vector<double>& alpha,
+                            std::vector<double>& beta, std::string& msg);
+
 // ---------------------------------------------------------------------------
 // Device side (kernels.cu)
 // ---------------------------------------------------------------------------
@@ -83,6 +90,7 @@ bool coarse_operator(const std::vector<double>& C, int d, int fz_over_ng, const 
 // right-hand side r0 + c % nr; every column of a tile uses matrix `mat`.
 struct Tile {
     int mat, u0, nu, r0, nr;
+    long long off;            // added to both the input and the output address
 };
 
 struct GemmArgs {
