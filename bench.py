@@ -45,6 +45,12 @@ def parse():
     p.add_argument("--impl", default="ours", choices=["ours", "reference"])
     p.add_argument("--cpu-sample", type=int, default=2, help="oracle right-hand sides in the cpu_baseline leg")
     p.add_argument("--no-cpu-baseline", action="store_true")
+    p.add_argument("--workload", default="poisson2d", choices=["poisson2d", "modes3d", "mixed", "serve"],
+                   help="poisson2d: the default bench line; modes3d / mixed / serve: the 3-D, mixed-precision "
+                        "and serving configurations, measured separately (not the driver's bench line)")
+    p.add_argument("--requests", type=int, default=200, help="serve: requests in the stream")
+    p.add_argument("--workers", type=int, default=4, help="serve: server worker threads (one stream each)")
+    p.add_argument("--max-batch", type=int, default=16, help="serve: requests per batch at most")
     return p.parse_args()
 
 
@@ -309,10 +315,229 @@ def run_ours(args):
     return 0
 
 
+def run_other(args):
+    """Separate measurements of the 3-D mode batch and of the mixed-precision
+    solve (one JSON line each; the default bench line is poisson2d)."""
+    import numpy as np
+    import torch
+    import __graft_entry__
+    __graft_entry__.build()
+    from paper_1512_01756_gb300 import smpm, inputs
+    dev = torch.device("cuda", 0)
+    stream = torch.cuda.current_stream()
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
+    lines = []
+
+    def timed(fn):
+        for _ in range(args.warmup):
+            fn()
+        ts = []
+        for _ in range(args.steps):
+            flush.fill_(1.0)
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            st = fn()
+            e1.record(stream)
+            e1.synchronize()
+            ts.append(e0.elapsed_time(e1))
+        return sum(ts) / len(ts), st
+
+    if args.workload == "modes3d":
+        s = smpm.Solver3D(smpm.make_grid(128, 8, 10, 32.0, 1.0), 128, 2 * np.pi, stream)
+        f3 = inputs.uniform((s.r, 128), inputs.seed_for(2))
+        fh = np.fft.rfft(f3, axis=1) / 128
+        F = torch.from_numpy(np.ascontiguousarray(np.stack([fh.real.T, fh.imag.T], axis=1))).to(dev)
+        U = torch.empty_like(F)
+        ms, st = timed(lambda: s.solve_3d(F, U, tol=TOL))
+        lines.append({"workload": "3-D via Fourier: 128x8 elements, order 10, domain 32x1, m_y = 128 (65 modes, "
+                                  "k_j = j), U[0,1] right-hand side, all modes in one batched solve",
+                      "metric": "3-D solves/s at 1e-10 rel. residual (every mode)", "value": 1e3 / ms,
+                      "ms_per_solve": ms, "iters": st.iters, "worst_rel_resid": st.rel_resid_true,
+                      "setup_ms": st.setup_ms, "device_bytes": s.device_bytes()})
+        s.close()
+    else:
+        shape = dict(mx=512, mz=16, order=16, lx=32.0, lz=1.0, z_ratio=1.2)
+        R = 4
+        for prec in (0, 1):
+            s = smpm.Solver(smpm.make_grid(**shape, precision=prec), 0.0, stream)
+            x, z = s.coords()
+            F = np.stack([inputs.cos_modes(x, z, 32.0, 1.0, inputs.cos_modes_spec(inputs.seed_for(3) + i))[0]
+                          for i in range(R)])
+            Fd = torch.from_numpy(F).to(dev)
+            Ud = torch.empty_like(Fd)
+            ms, st = timed(lambda: s.solve(Fd, Ud, tol=TOL))
+            lines.append({"workload": "2-D Poisson-Neumann 512x16 elements, order 16, domain 32x1, z stretched "
+                                      "geometrically (ratio 1.2), cos-cos modes, 4 right-hand sides per step",
+                          "precision": "mixed: FP64 FGMRES, FP32 block-Jacobi" if prec else "FP64",
+                          "metric": "solves/s at 1e-10 rel. residual", "value": R * 1e3 / ms, "ms_per_step": ms,
+                          "iters": st.iters, "worst_rel_resid": st.rel_resid_true, "setup_ms": st.setup_ms,
+                          "device_bytes": s.device_bytes()})
+            if prec == 0:
+                U64 = Ud.clone()
+            else:
+                lines[-1]["rel_diff_vs_fp64"] = float(torch.linalg.norm(Ud - U64) / torch.linalg.norm(U64))
+            s.close()
+    for ln in lines:
+        print(json.dumps(ln), flush=True)
+    return 0
+
+
+SERVE_GRIDS = [(64, 2), (128, 4), (256, 8), (512, 16), (1024, 16)]
+SERVE_ORDERS = [6, 8, 12, 16]
+
+
+def serve_stream(n, seed):
+    """The request stream: grid uniform from SERVE_GRIDS on [0, mx/mz] x [0, 1],
+    order uniform from SERVE_ORDERS, k^2 = 0 with probability 0.1 else
+    log-uniform on [1e-2, 1e4], f a seeded sum of 32 cos-cos modes (per-request
+    seed)."""
+    from paper_1512_01756_gb300 import inputs
+    r = inputs.rng(seed)
+    out = []
+    for i in range(n):
+        mx, mz = SERVE_GRIDS[int(r.integers(len(SERVE_GRIDS)))]
+        order = SERVE_ORDERS[int(r.integers(len(SERVE_ORDERS)))]
+        k2 = 0.0 if r.random() < 0.1 else float(10.0 ** r.uniform(-2.0, 4.0))
+        out.append({"mx": mx, "mz": mz, "order": order, "k2": k2, "seed": seed + 1 + i})
+    return out
+
+
+def serve_rhs(smpm, grid, lx, seed):
+    """f = sum_m c_m cos(a_m pi x / lx) cos(b_m pi z) at the grid's nodes, as
+    the product of per-column and per-row cosine tables (node order X*fz + Z)."""
+    import numpy as np
+    from paper_1512_01756_gb300 import inputs
+    x, z = smpm.grid_coords(grid)
+    fz = (grid.order + 1) * grid.mz
+    xs, zs = x[::fz], z[:fz]
+    c, a, b = inputs.cos_modes_spec(seed)
+    Cx = np.cos(np.outer(xs, a * np.pi / lx))
+    Cz = np.cos(np.outer(zs, b * np.pi))
+    return ((Cx * c) @ Cz.T).reshape(-1)
+
+
+def run_serve(args):
+    """Serving: the request stream served one at a time by the plain FP64 path
+    (smpm_setup + smpm_solve + smpm_release per request) and by the server
+    (continuous batching over worker streams), with Poisson arrivals at the
+    rate where the plain path saturates (its measured mean service rate)."""
+    import numpy as np
+    import torch
+    import __graft_entry__
+    __graft_entry__.build()
+    from paper_1512_01756_gb300 import smpm, inputs
+    dev = torch.device("cuda", 0)
+    torch.cuda.set_device(dev)
+    stream = torch.cuda.current_stream()
+    reqs = serve_stream(args.requests, inputs.seed_for(5))
+    for q in reqs:
+        q["grid"] = smpm.make_grid(q["mx"], q["mz"], q["order"], q["mx"] / q["mz"], 1.0)
+        q["f"] = torch.from_numpy(serve_rhs(smpm, q["grid"], q["mx"] / q["mz"], q["seed"])).to(dev)
+        q["u_plain"] = torch.zeros_like(q["f"])
+        q["u_served"] = torch.zeros_like(q["f"])
+    # warm-up (library, cuSOLVER and allocator start-up) on the smallest grid
+    wg = smpm.make_grid(64, 2, 6, 32.0, 1.0)
+    wf = torch.from_numpy(serve_rhs(smpm, wg, 32.0, 1)).to(dev)
+    wu = torch.zeros_like(wf)
+    for _ in range(max(args.warmup, 1)):
+        s = smpm.Solver(wg, 1.0, stream)
+        s.solve(wf, wu, tol=TOL)
+        s.close()
+    srv = smpm.Server(nworkers=args.workers, max_batch=args.max_batch)
+    t = srv.submit(wg, 2.0, wf, wu, tol=TOL)
+    while srv.poll(t) is None:
+        time.sleep(0.001)
+    torch.cuda.synchronize()
+
+    # plain FP64, one request at a time
+    clocks = Clocks(0)
+    clocks.start()
+    service, iters_plain, res_plain = [], [], []
+    for q in reqs:
+        torch.cuda.synchronize()
+        w0 = time.perf_counter()
+        s = smpm.Solver(q["grid"], q["k2"], stream)
+        st = s.solve(q["f"], q["u_plain"], tol=TOL)
+        s.close()
+        torch.cuda.synchronize()
+        service.append(time.perf_counter() - w0)
+        iters_plain.append(st.iters)
+        res_plain.append(st.rel_resid_true)
+        q["setup_ms"], q["solve_ms"] = st.setup_ms, st.solve_ms
+    lam = len(reqs) / sum(service)
+    arrivals = np.cumsum(inputs.rng(inputs.seed_for(5) + 7).exponential(1.0 / lam, len(reqs)))
+    end, lat_plain = 0.0, []
+    for a, sv in zip(arrivals, service):
+        end = max(end, a) + sv
+        lat_plain.append(end - a)
+    plain_rate = len(reqs) / (end - arrivals[0])
+
+    # served: submit at the arrival times, poll until every ticket is done
+    l0 = smpm.kernel_launches()
+    tickets, done, lat_served, batch_sizes, res_served = {}, {}, [], [], []
+    t0 = time.perf_counter()
+    nxt = 0
+    while len(done) < len(reqs):
+        now = time.perf_counter() - t0
+        while nxt < len(reqs) and arrivals[nxt] - arrivals[0] <= now:
+            q = reqs[nxt]
+            tickets[srv.submit(q["grid"], q["k2"], q["f"], q["u_served"], tol=TOL)] = nxt
+            nxt += 1
+        for tk, i in list(tickets.items()):
+            st = srv.poll(tk)
+            if st is not None:
+                done[i] = time.perf_counter() - t0
+                lat_served.append(st.solve_ms * 1e-3)
+                batch_sizes.append(st.restarts)
+                res_served.append(st.rel_resid_true)
+                del tickets[tk]
+        time.sleep(0.0002)
+    served_span = max(done.values())
+    torch.cuda.synchronize()
+    launches = smpm.kernel_launches() - l0
+    clk = clocks.stop()
+    srv.close()
+    diffs = [float(torch.linalg.norm(q["u_served"] - q["u_plain"]) / torch.linalg.norm(q["u_plain"])) for q in reqs]
+
+    def pct(v, p):
+        return float(np.percentile(np.asarray(v) * 1e3, p))
+
+    by_grid = {}
+    for q, sv in zip(reqs, service):
+        key = f'{q["mx"]}x{q["mz"]} p{q["order"]}'
+        e = by_grid.setdefault(key, {"n": 0, "service_ms": 0.0, "setup_ms": 0.0})
+        e["n"] += 1
+        e["service_ms"] += sv * 1e3
+        e["setup_ms"] += q["setup_ms"]
+    for e in by_grid.values():
+        e["service_ms"] /= e["n"]
+        e["setup_ms"] /= e["n"]
+    line = {"workload": f"serving: {len(reqs)} Poisson/Helmholtz requests, grids {SERVE_GRIDS} on [0, mx/mz] x [0, 1], "
+                        f"orders {SERVE_ORDERS}, k^2 = 0 (10 %) else log-uniform [1e-2, 1e4], cos-cos f; Poisson "
+                        f"arrivals at the plain path's saturation rate {lam:.2f}/s",
+            "metric": "solves/s at 1e-10 rel. residual, p50/p99 latency: served vs plain FP64",
+            "unit": "solves/s", "value": len(reqs) / served_span, "dtype": "f64", "data": "synthetic",
+            "served": {"solves_per_s": len(reqs) / served_span, "p50_ms": pct(lat_served, 50),
+                       "p99_ms": pct(lat_served, 99), "workers": args.workers, "max_batch": args.max_batch,
+                       "mean_batch": float(np.mean(batch_sizes)), "worst_rel_resid": max(res_served)},
+            "plain_fp64": {"solves_per_s": plain_rate, "p50_ms": pct(lat_plain, 50), "p99_ms": pct(lat_plain, 99),
+                           "mean_service_ms": 1e3 * float(np.mean(service)), "worst_rel_resid": max(res_plain)},
+            "served_vs_plain_max_rel_diff": max(diffs),
+            "latency": "completion - arrival, operator setup included",
+            "gpu_launches": launches, "clocks": clk, "per_grid_plain": by_grid}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
 def main():
     args = parse()
     if args.impl == "reference":
         return run_reference(args)
+    if args.workload == "serve":
+        return run_serve(args)
+    if args.workload != "poisson2d":
+        return run_other(args)
     return run_ours(args)
 
 

@@ -61,7 +61,11 @@ typedef struct {
                                1: one per interface and element row                  */
     int restart;            /* GMRES restart length m                                */
     int max_iter;           /* GMRES iteration cap per solve                         */
-    int precision;          /* 0: FP64 throughout                                     */
+    int precision;          /* 0: FP64 throughout; 1: mixed -- FP64 flexible GMRES
+                               (Schur product, deflation, CGS2 Arnoldi, Givens,
+                               true residual, projections, strip solves) with the
+                               block-Jacobi preconditioner in FP32 (FP32 blocks,
+                               FP32 accumulation)                                    */
 } smpm_grid;
 
 typedef struct {
@@ -139,8 +143,11 @@ int smpm_solve_3d(smpm_handle h, const double* fhat, const double* ghat, double 
 /* Number of nodes r, Neumann values nb and Schur unknowns k of a handle. */
 int smpm_sizes(smpm_handle h, long long* r, long long* nb, long long* k);
 
-/* Node coordinates in node order (x and z: r doubles each, host memory). */
+/* Node coordinates in node order (x and z: r doubles each, host memory).
+ * smpm_grid_coords gives the same for a grid without building a handle
+ * (host work only; SMPM_EINVAL for a grid smpm_setup would reject). */
 int smpm_node_coords(smpm_handle h, double* x, double* z);
+int smpm_grid_coords(const smpm_grid* grid, double* x, double* z);
 
 /* Per right-hand side relative Schur residual ||S x_S - b_S|| / ||b_S|| of the
  * handle's last solve (first n of them, host memory). */
@@ -188,6 +195,40 @@ long long smpm_kernel_launches(void);
  *         without synchronising. */
 #define SMPM_NOALLOC_MAX_DOUBLES 65536
 int smpm_apply_deflation_noalloc(smpm_handle h, int nrhs, const double* x, double* y);
+
+/* Serving runtime (continuous batching; no counterpart in the paper, which
+ * solves one problem at a time).  A server owns nworkers host threads, each
+ * with its own CUDA stream on the device current at create time.
+ * smpm_submit() queues one solve of L u - k2 u = f + tau g on the given grid
+ * (Sec. 2.3, Alg. seq; the Helmholtz form of Sec. 5) and returns a ticket at
+ * once.  A free worker takes the oldest pending request together with up to
+ * max_batch - 1 other pending requests of the same grid options and tol (any
+ * k2), builds one multi-operator handle for their distinct k2 values
+ * (smpm_setup_multi) and solves them in one batched call (smpm_solve_multi):
+ * each request keeps its own Krylov space and convergence test, so its result
+ * is the one a lone smpm_setup + smpm_solve gives, to the solver tolerance.
+ * Requests that arrive while batches run are taken by the next free worker and
+ * run concurrently with them on its stream.  Admission: a batch starts only if
+ * its estimated device footprint (operators of each k2, Krylov bases and work
+ * vectors per request) fits device_budget_bytes beside the batches in flight
+ * (<= 0: 80 % of the free device memory at create time); a batch that fits
+ * nowhere runs alone.
+ *   f, g, u: host or device pointers of r, nb and r doubles, owned by the
+ *   caller, which must keep them valid and unchanged until smpm_poll() has
+ *   returned something other than SMPM_EBUSY for the ticket.  g may be NULL.
+ *   smpm_poll(): SMPM_EBUSY while the request is pending or running; else the
+ *   solve's status, with st (may be NULL) filled: iters and rel_resid_true of
+ *   the request, setup_ms of its batch, solve_ms = completion - submission
+ *   (wall ms, setup included), restarts = the number of requests in its batch.
+ *   A ticket is forgotten once it has been polled to completion.
+ *   smpm_server_destroy(): finishes every queued request, joins the workers
+ *   and frees the server. */
+typedef struct smpm_server* smpm_server_t;
+int smpm_server_create(int nworkers, long long device_budget_bytes, int max_batch, smpm_server_t* out);
+int smpm_submit(smpm_server_t srv, const smpm_grid* grid, double k2, const double* f, const double* g,
+                double tol, double* u, unsigned long long* ticket);
+int smpm_poll(smpm_server_t srv, unsigned long long ticket, smpm_stats* st);
+int smpm_server_destroy(smpm_server_t srv);
 
 /* Message of the calling thread's last failure ("" if none). */
 const char* smpm_last_error(void);

@@ -21,6 +21,8 @@
 #include <algorithm>
 #include <array>
 #include <chrono>
+#include <cstdlib>
+#include <cstdio>
 #include <cmath>
 #include <cstring>
 #include <memory>
@@ -78,6 +80,8 @@ struct Solver {
     int *d_zlo = nullptr, *d_zhi = nullptr;                          // nonzero window of each L_z row
     // device operators (all ops, contiguous per kind)
     double *Ainv = nullptr, *W = nullptr, *G = nullptr, *Minv = nullptr, *rho = nullptr, *K = nullptr;
+    float* Minv32 = nullptr;              // FP32 block-Jacobi inverses (precision 1)
+    int precision = 0;
     double *uL = nullptr, *uS = nullptr;
     int *rl_GW = nullptr, *rh_GW = nullptr, *rl_M = nullptr, *rh_M = nullptr, *rl_A = nullptr, *rh_A = nullptr;
     int* d_strip_cls = nullptr;
@@ -99,6 +103,7 @@ struct Solver {
         int ntM = 0, ntG = 0, ntW = 0, ntA = 0, ntS1 = 0, ntS2 = 0;
         size_t capS1 = 0, capS2 = 0;
         double *fs1 = nullptr, *fs2 = nullptr, *fs3 = nullptr, *k2r = nullptr;
+        double* Zb = nullptr;             // FGMRES preconditioned vectors [R][m][ld] (precision 1)
         std::vector<void*> allocs;
     } wk;
     std::vector<int> cur_ops;               // op layout the tiles were built for
@@ -119,7 +124,9 @@ struct Solver {
     T* dalloc(size_t n, std::vector<void*>& list) {
         void* p = nullptr;
         if (n == 0) n = 1;
-        cudaError_t e = cudaMalloc(&p, n * sizeof(T));
+        // stream-ordered: no device-wide synchronisation, so handles on other
+        // streams (the serving workers) keep running while this one allocates
+        cudaError_t e = cudaMallocAsync(&p, n * sizeof(T), stream);
         if (e != cudaSuccess) {
             cudaGetLastError();
             throw Err{SMPM_ENOMEM, std::string("device allocation of ") + std::to_string(n * sizeof(T)) +
@@ -130,7 +137,7 @@ struct Solver {
         return (T*)p;
     }
     void free_list(std::vector<void*>& list) {
-        for (void* p : list) cudaFree(p);
+        for (void* p : list) cudaFreeAsync(p, stream);
         list.clear();
     }
     ~Solver() {
@@ -138,6 +145,7 @@ struct Solver {
         for (cudaEvent_t e : ev) cudaEventDestroy(e);
         free_list(wk.allocs);
         free_list(allocs);
+        if (stream) cudaStreamSynchronize(stream);
         if (sol) cusolverDnDestroy(sol);
     }
 };
@@ -236,6 +244,19 @@ static void fss_single(Solver& S, int o, int c, int R, const double* in, double*
 
 static void setup_solver(Solver& S) {
     auto t0 = std::chrono::steady_clock::now();
+    // SMPM_TRACE_SETUP=1: per-phase wall times of the setup on stderr
+    const bool trace = std::getenv("SMPM_TRACE_SETUP") != nullptr;
+    auto tp = t0;
+    std::string trace_line;
+    auto phase = [&](const char* name) {
+        if (!trace) return;
+        cudaStreamSynchronize(S.stream);
+        const auto t = std::chrono::steady_clock::now();
+        char buf[96];
+        snprintf(buf, sizeof(buf), " %s=%.2f", name, std::chrono::duration<double, std::milli>(t - tp).count());
+        trace_line += buf;
+        tp = t;
+    };
     Geometry& g = S.g;
     const int n = g.n, fz = g.fz, nfz = n * fz, f2 = 2 * fz, f4 = 4 * fz, mx = g.mx, ng = g.ng, d = g.d;
     cudaStream_t st = S.stream;
@@ -279,6 +300,7 @@ static void setup_solver(Solver& S) {
         face_flux_rows(g, c, beta[c]);
     }
     z_operator(g, Lz);
+    phase("host_1d");
     // fast strip solver: block-diagonalise the three n x n x-factors (k-independent)
     std::vector<double> Qh[3], Qih[3], al[3], be[3];
     S.fss = true;
@@ -344,6 +366,7 @@ static void setup_solver(Solver& S) {
         S.Ainv = S.dalloc<double>((size_t)nop * 3 * S.sA, S.allocs);
         S.W = S.dalloc<double>((size_t)nop * 3 * S.sW, S.allocs);
     }
+    phase("fss_factors");
     S.G = S.dalloc<double>((size_t)nop * 3 * S.sG, S.allocs);
     S.Minv = S.dalloc<double>((size_t)nop * S.nmc * S.sM, S.allocs);
     S.rho = S.dalloc<double>((size_t)nop * S.sRho, S.allocs);
@@ -401,6 +424,7 @@ static void setup_solver(Solver& S) {
     int* dipiv = S.dalloc<int>((size_t)mmax, tmp);
     int* dinfo = S.dalloc<int>(1, tmp);
 
+    phase("alloc_upload");
     // null vectors (k^2 = 0): u_L = u_Lx (x) u_Lz, u_S = E^T u_L / ||E^T u_L||
     std::vector<double> uS_h;
     for (int o = 0; o < nop; ++o)
@@ -434,6 +458,7 @@ static void setup_solver(Solver& S) {
         CK(cudaStreamSynchronize(st));
     }
 
+    phase("null_vectors");
     for (int o = 0; o < nop; ++o) {
         const double k2 = S.k2[o];
         double* G = S.G + (size_t)o * 3 * S.sG;
@@ -447,6 +472,7 @@ static void setup_solver(Solver& S) {
                                           : S.S2 + (((size_t)o * 3 + c) * std::max(S.ns2, 1) + idx) * 4 * fz * fz;
                     invert_dense(S, dtmp, dst, m, dwork, lwork, dipiv, dinfo);
                 }
+            phase("slot_inverses");
             // G_c = B A_c^-1 E_c from fast solves of the 2 fz unit face vectors of one strip
             double* U = S.dalloc<double>((size_t)f2 * nfz, tmp);
             double* Y = S.dalloc<double>((size_t)f2 * nfz, tmp);
@@ -479,6 +505,7 @@ static void setup_solver(Solver& S) {
             k_build_G(G + c * S.sG, W + c * S.sW, n, fz, c, st);
             k_build_rho(S.rho + (size_t)o * S.sRho + (size_t)c * 2 * ng * f2, G + c * S.sG, fz, ng, st);
         }
+        phase("G");
         for (int mc = 0; mc < S.nmc; ++mc) {
             const double* gA = G + sig[mc][0] * S.sG;
             const double* gB = G + sig[mc][1] * S.sG;
@@ -497,6 +524,7 @@ static void setup_solver(Solver& S) {
                 k_pad_block(dst, dtmp2, m, f4, st);
             }
         }
+        phase("M_inverses");
         // coarse matrix C = Z^T S Z from the row sums (host), then K
         std::vector<double> rho_h((size_t)S.sRho);
         CK(cudaMemcpyAsync(rho_h.data(), S.rho + (size_t)o * S.sRho, sizeof(double) * S.sRho, cudaMemcpyDeviceToHost, st));
@@ -543,10 +571,18 @@ static void setup_solver(Solver& S) {
         if (!coarse_operator(C, d, fz / ng, uCp, Kh, msg)) throw Err{SMPM_EBREAKDOWN, msg};
         upload(S.K + (size_t)o * S.sK, Kh, st);
         CK(cudaStreamSynchronize(st));
+        phase("coarse");
+    }
+    if (S.precision == 1) {
+        S.Minv32 = S.dalloc<float>((size_t)nop * S.nmc * S.sM, S.allocs);
+        k_to_fp32(S.Minv32, S.Minv, (long long)nop * S.nmc * S.sM, st);
     }
     CK(cudaStreamSynchronize(st));
     S.free_list(tmp);
     S.setup_ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+    if (trace)
+        fprintf(stderr, "smpm setup %dx%d p%d nop=%d fss=%d total=%.2f:%s\n", g.mx, g.mz, g.N, S.nop, (int)S.fss,
+                S.setup_ms, trace_line.c_str());
 }
 
 // ---------------------------------------------------------------------------
@@ -586,6 +622,10 @@ static void ensure_workspace(Solver& S, int R) {
     }
     w.V = S.dalloc<double>((size_t)R * (m + 1) * ld, L);
     k_fill(w.V, (long long)R * (m + 1) * ld, 0.0, S.stream);
+    if (S.precision == 1) {
+        w.Zb = S.dalloc<double>((size_t)R * m * ld, L);
+        k_fill(w.Zb, (long long)R * m * ld, 0.0, S.stream);
+    }
     w.Hc = S.dalloc<double>((size_t)R * m * (m + 1), L);
     w.htmp = S.dalloc<double>((size_t)R * (m + 1), L);
     w.cs = S.dalloc<double>((size_t)R * m, L);
@@ -844,9 +884,11 @@ static int solve_impl(Solver& S, const std::vector<int>& ops, const double* f, c
 
     // block-Jacobi apply: out = Minv_p in over pairs p (faces [(4p+1) fz, (4p+5) fz))
     auto bj = [&](const double* in, long long in_rs, long long in_off, double* out, long long out_rs,
-                  long long out_off, const int* active) {
+                  long long out_off, const int* active, bool fp32 = false) {
         GemmArgs a = gemm_base(S);
-        a.mats = S.Minv; a.mat_stride = S.sM; a.M = f4; a.K = f4;
+        a.mats = fp32 ? reinterpret_cast<const double*>(S.Minv32) : S.Minv;
+        a.fp32 = fp32 ? 1 : 0;
+        a.mat_stride = S.sM; a.M = f4; a.K = f4;
         a.row_lo = S.rl_M; a.row_hi = S.rh_M;
         a.in = in; a.in_rs = in_rs; a.in_us = f4; a.in_off = in_off + fz;
         a.out = out; a.out_rs = out_rs; a.out_us = f4; a.out_off0 = out_off + fz; a.out_off1 = 0; a.msplit = f4;
@@ -891,8 +933,14 @@ static int solve_impl(Solver& S, const std::vector<int>& ops, const double* f, c
         if (total_it >= S.max_iter) { status = SMPM_ENOCONV; break; }
         const int last_allowed = std::min(m, S.max_iter - total_it);
         int j = 0;
+        const bool mixed = S.precision == 1;
         for (; j < last_allowed; ++j) {
-            bj(w.V, (long long)(m + 1) * ld, (long long)j * ld, w.z, ld, 0, w.active);
+            // z_j = M^-1 v_j (FP32 block-Jacobi in the mixed form: the flexible
+            // variant keeps z_j, so the cycle's correction is exactly sum y_j z_j)
+            bj(w.V, (long long)(m + 1) * ld, (long long)j * ld, w.z, ld, 0, w.active, mixed);
+            if (mixed)
+                CK(cudaMemcpy2DAsync(w.Zb + (long long)j * ld, (size_t)m * ld * 8, w.z, (size_t)ld * 8,
+                                     (size_t)S.kp * 8, R, cudaMemcpyDeviceToDevice, st_));
             schur(w.z, ld, 0, w.w, w.active);
             k_deflate_sum(ka, w.w, nullptr, st_);
             k_coarse(ka, st_);
@@ -909,8 +957,12 @@ static int solve_impl(Solver& S, const std::vector<int>& ops, const double* f, c
             }
         }
         CK(cudaMemcpyAsync(h_nit.data(), w.nit, R * sizeof(int), cudaMemcpyDeviceToHost, st_));
-        k_cycle_update(ka, w.Xp, st_);                 // Y = V y
-        bj(w.Xp, ld, 0, w.t, ld, 0, nullptr);          // t = M^-1 Y
+        if (mixed) {
+            k_cycle_update(ka, w.t, st_, w.Zb, (long long)m * ld);  // t = sum y_j z_j (FGMRES)
+        } else {
+            k_cycle_update(ka, w.Xp, st_);             // Y = V y
+            bj(w.Xp, ld, 0, w.t, ld, 0, nullptr);      // t = M^-1 Y
+        }
         schur(w.t, ld, 0, w.s, nullptr);               // S t
         k_deflate_coarse_pending(ka, w.s, st_);        // c = K Z^T S t
         k_xs_update(ka, w.xS, w.t, w.c0, st_);         // x_S += t + Z (c0 - c)
@@ -1055,7 +1107,7 @@ static Solver* make_solver(const smpm_grid* grid, int nop, const double* k2, voi
     if (!make_geometry(grid->mx, grid->mz, grid->order, grid->lx, grid->lz, grid->z_ratio, grid->tau_scale,
                        grid->deflation_groups, S->g, msg))
         throw Err{SMPM_EINVAL, msg};
-    if (grid->precision != 0) throw Err{SMPM_EINVAL, "precision mode not supported by this entry point"};
+    if (grid->precision != 0 && grid->precision != 1) throw Err{SMPM_EINVAL, "precision must be 0 (FP64) or 1 (mixed)"};
     S->nop = nop;
     S->k2.assign(k2, k2 + nop);
     int nzero = 0;
@@ -1065,6 +1117,7 @@ static Solver* make_solver(const smpm_grid* grid, int nop, const double* k2, voi
     }
     if (nzero > 1) throw Err{SMPM_EINVAL, "at most one k2 = 0 operator per handle"};
     S->stream = (cudaStream_t)stream;
+    S->precision = grid->precision;
     setup_solver(*S);
     return S.release();
 }
@@ -1208,19 +1261,35 @@ int smpm_sizes(smpm_handle h, long long* r, long long* nb, long long* k) {
     });
 }
 
+static void fill_coords(const Geometry& g, double* x, double* z) {
+    for (int X = 0; X < g.nx; ++X) {
+        const int ex = X / g.n, a = X % g.n;
+        const double xv = ex * g.hx + (g.xi[a] + 1.0) * g.hx * 0.5;
+        for (int Z = 0; Z < g.fz; ++Z) {
+            const int ez = Z / g.n, b = Z % g.n;
+            x[(size_t)X * g.fz + Z] = xv;
+            z[(size_t)X * g.fz + Z] = g.zb[ez] + (g.xi[b] + 1.0) * g.hz[ez] * 0.5;
+        }
+    }
+}
+
 int smpm_node_coords(smpm_handle h, double* x, double* z) {
     return guarded([&] {
         if (!h || !x || !z) throw Err{SMPM_EINVAL, "null argument"};
-        const Geometry& g = ((Solver*)h)->g;
-        for (int X = 0; X < g.nx; ++X) {
-            const int ex = X / g.n, a = X % g.n;
-            const double xv = ex * g.hx + (g.xi[a] + 1.0) * g.hx * 0.5;
-            for (int Z = 0; Z < g.fz; ++Z) {
-                const int ez = Z / g.n, b = Z % g.n;
-                x[(size_t)X * g.fz + Z] = xv;
-                z[(size_t)X * g.fz + Z] = g.zb[ez] + (g.xi[b] + 1.0) * g.hz[ez] * 0.5;
-            }
-        }
+        fill_coords(((Solver*)h)->g, x, z);
+        return SMPM_OK;
+    });
+}
+
+int smpm_grid_coords(const smpm_grid* grid, double* x, double* z) {
+    return guarded([&] {
+        if (!grid || !x || !z) throw Err{SMPM_EINVAL, "null argument"};
+        Geometry g;
+        std::string msg;
+        if (!make_geometry(grid->mx, grid->mz, grid->order, grid->lx, grid->lz, grid->z_ratio, grid->tau_scale,
+                           grid->deflation_groups, g, msg))
+            throw Err{SMPM_EINVAL, msg};
+        fill_coords(g, x, z);
         return SMPM_OK;
     });
 }

@@ -51,7 +51,10 @@ __device__ __forceinline__ double block_sum(double v, double* sh) {
 // padding waste of M = 2 f_z, 4 f_z, n f_z small, and the many small tiles
 // spread the FP64 work evenly over the SMs.
 // ---------------------------------------------------------------------------
-template <int EPI>
+// TM: element type of the class matrices and of the arithmetic (double, or
+// float for the FP32 block-Jacobi of the mixed-precision solve: FP64 vectors are
+// rounded to FP32 on load, products accumulate in FP32, results are stored in FP64).
+template <int EPI, typename TM>
 __global__ void __launch_bounds__(GT) class_gemm_kernel(GemmArgs a, const Tile* __restrict__ tiles) {
     const Tile t = tiles[blockIdx.x];
     const int row0 = blockIdx.y * BM;
@@ -70,12 +73,12 @@ __global__ void __launch_bounds__(GT) class_gemm_kernel(GemmArgs a, const Tile* 
         atomicAdd(a.flops, 2ULL * (unsigned long long)max(0, r_hi - r_lo) * (unsigned long long)a.K *
                                (unsigned long long)cols);
     }
-    __shared__ double As[BK][BM + 1];
-    __shared__ __align__(16) double Bs[BK][BN + 2];
-    const double* __restrict__ A = a.mats + (long long)t.mat * a.mat_stride;
+    __shared__ TM As[BK][BM + 1];
+    __shared__ __align__(16) TM Bs[BK][BN + 4];
+    const TM* __restrict__ A = reinterpret_cast<const TM*>(a.mats) + (long long)t.mat * a.mat_stride;
     const int tid = threadIdx.x;
     const int tr = tid >> 3, tc = tid & 7;     // row 0..15, column group 0..7
-    double acc[4] = {0.0, 0.0, 0.0, 0.0};
+    TM acc[4] = {TM(0), TM(0), TM(0), TM(0)};
 
     const double* colp[(BN * BK) / GT];
 #pragma unroll
@@ -92,24 +95,20 @@ __global__ void __launch_bounds__(GT) class_gemm_kernel(GemmArgs a, const Tile* 
         for (int l = 0; l < (BM * BK) / GT; ++l) {
             const int e = tid + l * GT, i = e >> 4, kk = e & 15;
             const int row = row0 + i, k = k0 + kk;
-            As[kk][i] = (row < a.M && k < a.K) ? A[(long long)row * a.K + k] : 0.0;
+            As[kk][i] = (row < a.M && k < a.K) ? A[(long long)row * a.K + k] : TM(0);
         }
 #pragma unroll
         for (int l = 0; l < (BN * BK) / GT; ++l) {
             const int e = tid + l * GT, c = e >> 4, kk = e & 15;
             const int k = k0 + kk;
-            Bs[kk][c] = (colp[l] != nullptr && k < a.K) ? colp[l][k] : 0.0;
+            Bs[kk][c] = (colp[l] != nullptr && k < a.K) ? TM(colp[l][k]) : TM(0);
         }
         __syncthreads();
 #pragma unroll
         for (int kk = 0; kk < BK; ++kk) {
-            const double av = As[kk][tr];
-            const double2 b01 = *reinterpret_cast<const double2*>(&Bs[kk][tc * 4]);
-            const double2 b23 = *reinterpret_cast<const double2*>(&Bs[kk][tc * 4 + 2]);
-            acc[0] = fma(av, b01.x, acc[0]);
-            acc[1] = fma(av, b01.y, acc[1]);
-            acc[2] = fma(av, b23.x, acc[2]);
-            acc[3] = fma(av, b23.y, acc[3]);
+            const TM av = As[kk][tr];
+#pragma unroll
+            for (int j = 0; j < 4; ++j) acc[j] = fma(av, Bs[kk][tc * 4 + j], acc[j]);
         }
         __syncthreads();
     }
@@ -123,7 +122,7 @@ __global__ void __launch_bounds__(GT) class_gemm_kernel(GemmArgs a, const Tile* 
         if (a.active && !a.active[r]) continue;
         const long long base = (long long)r * a.out_rs + (long long)u * a.out_us + t.off;
         const long long addr = base + (row < a.msplit ? a.out_off0 + row : a.out_off1 + (row - a.msplit));
-        double v = acc[j];
+        double v = (double)acc[j];
         if (EPI == 1) v += a.add[addr];
         a.out[addr] = v;
     }
@@ -133,10 +132,12 @@ void launch_class_gemm(const GemmArgs& a, const Tile* d_tiles, int ntiles, int e
     if (ntiles <= 0) return;
     dim3 grid(ntiles, (a.M + BM - 1) / BM);
     cudaStream_t s = (cudaStream_t)stream;
-    if (epi == 1)
-        class_gemm_kernel<1><<<grid, GT, 0, s>>>(a, d_tiles);
+    if (a.fp32)
+        class_gemm_kernel<0, float><<<grid, GT, 0, s>>>(a, d_tiles);
+    else if (epi == 1)
+        class_gemm_kernel<1, double><<<grid, GT, 0, s>>>(a, d_tiles);
     else
-        class_gemm_kernel<0><<<grid, GT, 0, s>>>(a, d_tiles);
+        class_gemm_kernel<0, double><<<grid, GT, 0, s>>>(a, d_tiles);
     count_launches(1);
 }
 
@@ -496,7 +497,8 @@ void k_deflate_coarse_pending(const KArgs& a, const double* v, cudaStream_t s) {
     k_coarse_gate(a, 1, s);
 }
 
-__global__ void __launch_bounds__(VB) cycle_update_kernel(KArgs a, double* __restrict__ Xp) {
+__global__ void __launch_bounds__(VB) cycle_update_kernel(KArgs a, double* __restrict__ Xp,
+                                                         const double* __restrict__ basis, long long basis_rs) {
     const int r = blockIdx.y;
     if (a.done[r]) return;
     const int ni = a.nit[r];
@@ -514,7 +516,7 @@ __global__ void __launch_bounds__(VB) cycle_update_kernel(KArgs a, double* __res
     __syncthreads();
     const long long e0 = (long long)blockIdx.x * a.ch;
     const long long e1 = min(e0 + (long long)a.ch, a.kp);
-    const double* Vr = a.V + (long long)r * (a.m + 1) * a.ld;
+    const double* Vr = basis + (long long)r * basis_rs;
     double* x = Xp + (long long)r * a.ld;
     for (long long e = e0 + threadIdx.x; e < e1; e += VB) {
         double s = 0.0;
@@ -523,9 +525,13 @@ __global__ void __launch_bounds__(VB) cycle_update_kernel(KArgs a, double* __res
     }
 }
 
-void k_cycle_update(const KArgs& a, double* Xp, cudaStream_t s) {
+void k_cycle_update(const KArgs& a, double* Xp, cudaStream_t s, const double* basis, long long basis_rs) {
     dim3 grid(a.nch, a.R);
-    cycle_update_kernel<<<grid, VB, (size_t)(a.m + 1) * sizeof(double), s>>>(a, Xp);
+    if (!basis) {
+        basis = a.V;
+        basis_rs = (long long)(a.m + 1) * a.ld;
+    }
+    cycle_update_kernel<<<grid, VB, (size_t)(a.m + 1) * sizeof(double), s>>>(a, Xp, basis, basis_rs);
     count_launches(1);
 }
 
@@ -826,6 +832,17 @@ void k_build_rho(double* rho, const double* G, int fz, int ng, cudaStream_t s) {
 __global__ void fill_kernel(double* x, long long n, double v) {
     const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (i < n) x[i] = v;
+}
+
+__global__ void to_fp32_kernel(float* dst, const double* src, long long n) {
+    const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) dst[i] = (float)src[i];
+}
+
+void k_to_fp32(float* dst, const double* src, long long n, cudaStream_t s) {
+    if (n <= 0) return;
+    to_fp32_kernel<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(dst, src, n);
+    count_launches(1);
 }
 
 void k_fill(double* x, long long n, double v, cudaStream_t s) {

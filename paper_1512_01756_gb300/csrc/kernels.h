@@ -58,8 +58,10 @@ void k_normalize(const KArgs& a, int j, int last_allowed, cudaStream_t s);
 // tol ||b_S||, normalises V[0] and saves c into c0.
 void k_residual(const KArgs& a, const double* bS, const double* sv, cudaStream_t s);
 void k_cycle_start(const KArgs& a, double* c0, int first, double tol, cudaStream_t s);
-// Y = V y with y from the rotated Hessenberg system of the cycle.
-void k_cycle_update(const KArgs& a, double* Y, cudaStream_t s);
+// Y = basis y with y from the rotated Hessenberg system of the cycle (basis:
+// the Arnoldi vectors V by default, or the preconditioned vectors of FGMRES).
+void k_cycle_update(const KArgs& a, double* Y, cudaStream_t s, const double* basis = nullptr,
+                    long long basis_rs = 0);
 // c = K Z^T v for every unconverged rhs.
 void k_deflate_coarse_pending(const KArgs& a, const double* v, cudaStream_t s);
 // x_S += t + Z (c0 - c) for rhs that ran this cycle.
@@ -101,6 +103,7 @@ void k_build_M(double* M, const double* gA, const double* gB, const double* gC, 
 void k_pad_block(double* dst, const double* src, int m_src, int m_dst, cudaStream_t s);
 void k_build_rho(double* rho, const double* G, int fz, int ng, cudaStream_t s);
 void k_fill(double* x, long long n, double v, cudaStream_t s);
+void k_to_fp32(float* dst, const double* src, long long n, cudaStream_t s);
 
 // Fast strip solver pieces.
 struct FssArgs {

@@ -107,6 +107,7 @@ struct GemmArgs {
     const double* add;        // EPI 1: out = add[same address] + acc
     const int* active;        // per rhs: skip tiles whose columns are all inactive (may be null)
     unsigned long long* flops;  // if set: each working CTA adds 2 * rows * K * active columns
+    int fp32;                 // 1: mats are float, arithmetic in FP32 (EPI 0 only)
 };
 
 // Number of kernels libsmpm has launched in this process.
