@@ -18,9 +18,9 @@ SMPM_OK, SMPM_EINVAL, SMPM_ENOMEM, SMPM_ENOCONV, SMPM_EBREAKDOWN, SMPM_ECUDA, SM
 # every entry point include/smpm.h declares
 EXPORTS = ["smpm_setup", "smpm_solve", "smpm_solve_batch", "smpm_setup_multi", "smpm_solve_multi",
            "smpm_setup_3d", "smpm_solve_3d",
-           "smpm_sizes", "smpm_node_coords", "smpm_device_bytes", "smpm_release", "smpm_probe_fp64",
+           "smpm_sizes", "smpm_node_coords", "smpm_grid_coords", "smpm_device_bytes", "smpm_release", "smpm_probe_fp64",
            "smpm_profile", "smpm_profile_read", "smpm_kernel_launches", "smpm_apply", "smpm_last_residuals", "smpm_apply_deflation_noalloc",
-           "smpm_last_error"]
+           "smpm_server_create", "smpm_submit", "smpm_poll", "smpm_server_destroy", "smpm_last_error"]
 
 
 class Grid(ctypes.Structure):
@@ -68,6 +68,7 @@ def load():
     lib.smpm_sizes.argtypes = [H, ctypes.POINTER(ctypes.c_longlong), ctypes.POINTER(ctypes.c_longlong),
                                ctypes.POINTER(ctypes.c_longlong)]
     lib.smpm_node_coords.argtypes = [H, P, P]
+    lib.smpm_grid_coords.argtypes = [ctypes.POINTER(Grid), P, P]
     lib.smpm_device_bytes.argtypes = [H]
     lib.smpm_device_bytes.restype = ctypes.c_longlong
     lib.smpm_release.argtypes = [H]
@@ -80,6 +81,11 @@ def load():
     lib.smpm_apply.argtypes = [H, ctypes.c_int, ctypes.c_int, P, P]
     lib.smpm_last_residuals.argtypes = [H, ctypes.c_int, P]
     lib.smpm_apply_deflation_noalloc.argtypes = [H, ctypes.c_int, P, P]
+    lib.smpm_server_create.argtypes = [ctypes.c_int, ctypes.c_longlong, ctypes.c_int, ctypes.POINTER(H)]
+    lib.smpm_submit.argtypes = [H, ctypes.POINTER(Grid), ctypes.c_double, P, P, ctypes.c_double, P,
+                                ctypes.POINTER(ctypes.c_ulonglong)]
+    lib.smpm_poll.argtypes = [H, ctypes.c_ulonglong, ctypes.POINTER(Stats)]
+    lib.smpm_server_destroy.argtypes = [H]
     lib.smpm_kernel_launches.argtypes = []
     lib.smpm_kernel_launches.restype = ctypes.c_longlong
     for name in EXPORTS:
@@ -229,6 +235,58 @@ class Solver3D(Solver):
         st = Stats()
         _check(load().smpm_solve_3d(self._h, _ptr(fhat), _ptr(ghat), float(tol), _ptr(uhat), ctypes.byref(st)))
         return st
+
+
+def grid_coords(grid: Grid):
+    """Node coordinates (x, z) of a grid in node order, without a handle."""
+    r = (grid.order + 1) ** 2 * grid.mx * grid.mz
+    x = np.empty(r)
+    z = np.empty(r)
+    _check(load().smpm_grid_coords(ctypes.byref(grid), _ptr(x), _ptr(z)))
+    return x, z
+
+
+class Server:
+    """Serving runtime (smpm_server_*): submit solves, poll their tickets.
+
+    The buffers of a submitted request are kept referenced here until its
+    ticket has been polled to completion (the library reads f, g and writes u
+    asynchronously)."""
+
+    def __init__(self, nworkers=2, device_budget_bytes=0, max_batch=16):
+        self._s = ctypes.c_void_p()
+        _check(load().smpm_server_create(int(nworkers), int(device_budget_bytes), int(max_batch),
+                                         ctypes.byref(self._s)))
+        self._keep = {}
+
+    def submit(self, grid: Grid, k2, f, u, g=None, tol=1e-10):
+        t = ctypes.c_ulonglong()
+        _check(load().smpm_submit(self._s, ctypes.byref(grid), float(k2), _ptr(f), _ptr(g), float(tol), _ptr(u),
+                                  ctypes.byref(t)))
+        self._keep[t.value] = (grid, f, g, u)
+        return t.value
+
+    def poll(self, ticket):
+        """None while the request runs; else its Stats (raises on a failed solve)."""
+        st = Stats()
+        code = load().smpm_poll(self._s, ctypes.c_ulonglong(ticket), ctypes.byref(st))
+        if code == SMPM_EBUSY:
+            return None
+        self._keep.pop(ticket, None)
+        _check(code)
+        return st
+
+    def close(self):
+        if self._s:
+            _check(load().smpm_server_destroy(self._s))
+            self._s = ctypes.c_void_p()
+            self._keep.clear()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 def kernel_launches():

@@ -48,3 +48,16 @@ def test_struct_layout_matches_header():
 
 def test_last_error_without_gpu_call(lib):
     assert lib.smpm_last_error() in (b"",)
+
+
+def test_grid_coords_match_oracle(lib):
+    """smpm_grid_coords is host logic: it needs no GPU and must give the oracle's
+    node positions (LGL nodes mapped to each element, Sec. 2.1)."""
+    import numpy as np
+    from paper_1512_01756_gb300 import smpm
+    from oracle.smpm import Grid
+    x, z = smpm.grid_coords(smpm.make_grid(5, 3, 6, 2.5, 1.0, z_ratio=1.2))
+    X, Z = Grid(5, 3, 6, 2.5, 1.0, z_ratio=1.2).coords()
+    assert np.abs(x - X).max() < 1e-14 and np.abs(z - Z).max() < 1e-14
+    with pytest.raises(smpm.SmpmError):
+        smpm.grid_coords(smpm.make_grid(1, 1, 6, 2.5, 1.0))
