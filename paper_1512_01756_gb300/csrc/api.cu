@@ -242,6 +242,61 @@ static void fss_single(Solver& S, int o, int c, int R, const double* in, double*
     CK(cudaStreamSynchronize(S.stream));
 }
 
+// Setup lanes: extra streams, each with its own cuSOLVER handle, on which a
+// setup runs its independent small factorisations (slot inverses, block-Jacobi
+// inverses) concurrently.  One pool per host thread, reused by every setup
+// that thread runs, so the stream and handle creation is paid once.
+struct Lane {
+    cudaStream_t s = nullptr;
+    cusolverDnHandle_t h = nullptr;
+    cudaEvent_t ev = nullptr;
+};
+struct LanePool {
+    int device = -1;
+    std::vector<Lane> lanes;
+    void clear() {
+        for (Lane& l : lanes) {
+            if (l.h) cusolverDnDestroy(l.h);
+            if (l.ev) cudaEventDestroy(l.ev);
+            if (l.s) cudaStreamDestroy(l.s);
+        }
+        lanes.clear();
+    }
+    ~LanePool() { clear(); }
+};
+static thread_local LanePool t_lanes;
+static constexpr int kSetupLanes = 8;
+
+static std::vector<Lane>& setup_lanes() {
+    int dev = 0;
+    CK(cudaGetDevice(&dev));
+    if (t_lanes.device != dev) {
+        t_lanes.clear();
+        t_lanes.device = dev;
+    }
+    while ((int)t_lanes.lanes.size() < kSetupLanes) {
+        Lane l;
+        CK(cudaStreamCreateWithFlags(&l.s, cudaStreamNonBlocking));
+        t_lanes.lanes.push_back(l);
+        CK(cudaEventCreateWithFlags(&t_lanes.lanes.back().ev, cudaEventDisableTiming));
+        CS(cusolverDnCreate(&t_lanes.lanes.back().h));
+        CS(cusolverDnSetStream(t_lanes.lanes.back().h, l.s));
+    }
+    return t_lanes.lanes;
+}
+
+// Waits for every lane when a setup ends, normally or by an exception, so
+// that no lane still uses the setup's temporary buffers when they are freed.
+struct LaneGuard {
+    std::vector<Lane>* lanes = nullptr;
+    cudaEvent_t ev = nullptr;
+    ~LaneGuard() {
+        if (lanes)
+            for (Lane& l : *lanes) cudaStreamSynchronize(l.s);
+        if (ev) cudaEventDestroy(ev);
+    }
+};
+
 static void setup_solver(Solver& S) {
     auto t0 = std::chrono::steady_clock::now();
     // SMPM_TRACE_SETUP=1: per-phase wall times of the setup on stderr
@@ -412,17 +467,19 @@ static void setup_solver(Solver& S) {
     }
     upload(dLz, Lz, st);
 
-    // LU workspace sized for the largest matrix
+    // LU workspace sized for the largest matrix (the dense strip inverses of
+    // the path without the fast strip solver, else the block-Jacobi blocks)
     const int mmax = S.fss ? f4 : std::max(nfz, f4);
-    double* dtmp = S.dalloc<double>((size_t)mmax * mmax, tmp);
-    double* dtmp2 = S.dalloc<double>((size_t)f4 * f4, tmp);
-    int lwork = 0, lw2 = 0;
-    CS(cusolverDnDgetrf_bufferSize(S.sol, mmax, mmax, dtmp, mmax, &lwork));
-    CS(cusolverDnDgetrf_bufferSize(S.sol, f4, f4, dtmp, f4, &lw2));
-    lwork = std::max(lwork, lw2);
-    double* dwork = S.dalloc<double>((size_t)std::max(lwork, 1), tmp);
-    int* dipiv = S.dalloc<int>((size_t)mmax, tmp);
-    int* dinfo = S.dalloc<int>(1, tmp);
+    double *dtmp = nullptr, *dwork = nullptr;
+    int *dipiv = nullptr, *dinfo = nullptr;
+    int lwork = 0;
+    CS(cusolverDnDgetrf_bufferSize(S.sol, mmax, mmax, nullptr, mmax, &lwork));
+    if (!S.fss) {
+        dtmp = S.dalloc<double>((size_t)mmax * mmax, tmp);
+        dwork = S.dalloc<double>((size_t)std::max(lwork, 1), tmp);
+        dipiv = S.dalloc<int>((size_t)mmax, tmp);
+        dinfo = S.dalloc<int>(1, tmp);
+    }
 
     phase("alloc_upload");
     // null vectors (k^2 = 0): u_L = u_Lx (x) u_Lz, u_S = E^T u_L / ||E^T u_L||
@@ -459,25 +516,82 @@ static void setup_solver(Solver& S) {
     }
 
     phase("null_vectors");
+
+    // Independent factorisations run on the setup lanes; every getrf/getrs
+    // writes its own status word, checked once after the last join.
+    std::vector<Lane>& lanes = setup_lanes();
+    LaneGuard guard;
+    guard.lanes = &lanes;
+    const int L = (int)lanes.size();
+    const int mlane = std::max(f4, S.fss ? f2 : 0);
+    struct LaneBuf { double *a, *b, *work; int* ipiv; };
+    std::vector<LaneBuf> lb(L);
+    for (int l = 0; l < L; ++l) {
+        lb[l].a = S.dalloc<double>((size_t)mlane * mlane, tmp);
+        lb[l].b = S.dalloc<double>((size_t)f2 * f2, tmp);
+        lb[l].work = S.dalloc<double>((size_t)std::max(lwork, 1), tmp);
+        lb[l].ipiv = S.dalloc<int>((size_t)mlane, tmp);
+    }
+    int n_inv = 0;
+    for (int c = 0; c < 3 && S.fss; ++c) n_inv += (int)S.sl_size[c].size();
+    n_inv = nop * (n_inv + S.nmc + 1);
+    int* d_infos = S.dalloc<int>((size_t)2 * n_inv, tmp);
+    CK(cudaMemsetAsync(d_infos, 0, sizeof(int) * 2 * n_inv, st));
+    int inv_used = 0, next_lane = 0;
+    cudaEvent_t fork_ev = nullptr;
+    CK(cudaEventCreateWithFlags(&fork_ev, cudaEventDisableTiming));
+    guard.ev = fork_ev;
+    auto fork = [&] {
+        CK(cudaEventRecord(fork_ev, st));
+        for (Lane& ln : lanes) CK(cudaStreamWaitEvent(ln.s, fork_ev, 0));
+        next_lane = 0;
+    };
+    auto join = [&] {
+        for (Lane& ln : lanes) {
+            CK(cudaEventRecord(ln.ev, ln.s));
+            CK(cudaStreamWaitEvent(st, ln.ev, 0));
+        }
+    };
+    // dst <- src^-1 on lane l (row-major; src destroyed)
+    auto invert_on = [&](int l, double* src, double* dst, int m) {
+        if (inv_used >= n_inv) throw Err{SMPM_ECUDA, "setup: inversion count exceeded"};
+        int* info = d_infos + 2 * inv_used++;
+        k_identity(dst, m, lanes[l].s);
+        CS(cusolverDnDgetrf(lanes[l].h, m, m, src, m, lb[l].work, lb[l].ipiv, info));
+        CS(cusolverDnDgetrs(lanes[l].h, CUBLAS_OP_N, m, m, src, m, lb[l].ipiv, dst, m, info + 1));
+    };
+
+    // phase 1: slot inverses of B_c (+) L_z - k^2 for every operator (Sec. 5:
+    // only the shift depends on k)
+    if (S.fss) {
+        fork();
+        for (int o = 0; o < nop; ++o)
+            for (int c = 0; c < 3; ++c)
+                for (size_t t = 0; t < S.sl_size[c].size(); ++t) {
+                    const int l = next_lane++ % L;
+                    const int sz = S.sl_size[c][t], m = sz * fz, idx = S.sl_idx[c][t];
+                    k_build_slot(lb[l].a, dLz, fz, sz, al[c][t] - S.k2[o], be[c][t], lanes[l].s);
+                    double* dst = sz == 1 ? S.S1 + (((size_t)o * 3 + c) * std::max(S.ns1, 1) + idx) * fz * fz
+                                          : S.S2 + (((size_t)o * 3 + c) * std::max(S.ns2, 1) + idx) * 4 * fz * fz;
+                    invert_on(l, lb[l].a, dst, m);
+                }
+        join();
+        phase("slot_inverses");
+    }
+
+    // phase 2: G_c = B A_c^-1 E_c and the coarse row sums, per operator
+    double *U = nullptr, *Y = nullptr, *T1 = nullptr, *T2 = nullptr;
+    if (S.fss) {
+        U = S.dalloc<double>((size_t)f2 * nfz, tmp);
+        Y = S.dalloc<double>((size_t)f2 * nfz, tmp);
+        T1 = S.dalloc<double>((size_t)f2 * nfz, tmp);
+        T2 = S.dalloc<double>((size_t)f2 * nfz, tmp);
+    }
     for (int o = 0; o < nop; ++o) {
         const double k2 = S.k2[o];
         double* G = S.G + (size_t)o * 3 * S.sG;
         if (S.fss) {
-            // slot inverses of B_c (+) L_z - k^2 (Sec. 5: only the shift depends on k)
-            for (int c = 0; c < 3; ++c)
-                for (size_t t = 0; t < S.sl_size[c].size(); ++t) {
-                    const int sz = S.sl_size[c][t], m = sz * fz, idx = S.sl_idx[c][t];
-                    k_build_slot(dtmp, dLz, fz, sz, al[c][t] - k2, be[c][t], st);
-                    double* dst = sz == 1 ? S.S1 + (((size_t)o * 3 + c) * std::max(S.ns1, 1) + idx) * fz * fz
-                                          : S.S2 + (((size_t)o * 3 + c) * std::max(S.ns2, 1) + idx) * 4 * fz * fz;
-                    invert_dense(S, dtmp, dst, m, dwork, lwork, dipiv, dinfo);
-                }
-            phase("slot_inverses");
-            // G_c = B A_c^-1 E_c from fast solves of the 2 fz unit face vectors of one strip
-            double* U = S.dalloc<double>((size_t)f2 * nfz, tmp);
-            double* Y = S.dalloc<double>((size_t)f2 * nfz, tmp);
-            double* T1 = S.dalloc<double>((size_t)f2 * nfz, tmp);
-            double* T2 = S.dalloc<double>((size_t)f2 * nfz, tmp);
+            // from fast solves of the 2 fz unit face vectors of one strip
             for (int c = 0; c < 3; ++c) {
                 if (c == 1 && mx < 3) {
                     k_fill(G + c * S.sG, S.sG, 0.0, st);
@@ -488,9 +602,9 @@ static void setup_solver(Solver& S) {
                 k_g_from_solves(G + c * S.sG, Y, S.d_beta + (size_t)c * 2 * n, n, fz, c, st);
                 k_build_rho(S.rho + (size_t)o * S.sRho + (size_t)c * 2 * ng * f2, G + c * S.sG, fz, ng, st);
             }
-            CK(cudaStreamSynchronize(st));
+            continue;
         }
-        for (int c = 0; c < 3 && !S.fss; ++c) {
+        for (int c = 0; c < 3; ++c) {
             double* Ainv = S.Ainv + (size_t)o * 3 * S.sA;
             double* W = S.W + (size_t)o * 3 * S.sW;
             if (c == 1 && mx < 3) {  // no interior strips
@@ -505,40 +619,65 @@ static void setup_solver(Solver& S) {
             k_build_G(G + c * S.sG, W + c * S.sW, n, fz, c, st);
             k_build_rho(S.rho + (size_t)o * S.sRho + (size_t)c * 2 * ng * f2, G + c * S.sG, fz, ng, st);
         }
-        phase("G");
+    }
+    phase("G");
+
+    // phase 3: block-Jacobi pair blocks and their inverses (Sec. 3.2)
+    fork();
+    for (int o = 0; o < nop; ++o) {
+        const double* G = S.G + (size_t)o * 3 * S.sG;
         for (int mc = 0; mc < S.nmc; ++mc) {
+            const int l = next_lane++ % L;
+            cudaStream_t ls = lanes[l].s;
             const double* gA = G + sig[mc][0] * S.sG;
             const double* gB = G + sig[mc][1] * S.sG;
             const double* gC = sig[mc][2] >= 0 ? G + sig[mc][2] * S.sG : nullptr;
             const int m = gC ? f4 : f2;
-            k_build_M(dtmp, gA, gB, gC, fz, st);
             double* dst = S.Minv + ((size_t)o * S.nmc + mc) * S.sM;
-            if (S.P == 1 && k2 == 0.0) {
+            if (S.P == 1 && S.k2[o] == 0.0) {
                 // m_x <= 3: the one block is all of the singular S; use M = I
-                k_identity(dtmp2, m, st);
-                k_pad_block(dst, dtmp2, m, f4, st);
-            } else if (m == f4) {
-                invert_dense(S, dtmp, dst, m, dwork, lwork, dipiv, dinfo);
+                k_identity(lb[l].a, m, ls);
+                k_pad_block(dst, lb[l].a, m, f4, ls);
+                continue;
+            }
+            k_build_M(lb[l].a, gA, gB, gC, fz, ls);
+            if (m == f4) {
+                invert_on(l, lb[l].a, dst, m);
             } else {
-                invert_dense(S, dtmp, dtmp2, m, dwork, lwork, dipiv, dinfo);
-                k_pad_block(dst, dtmp2, m, f4, st);
+                invert_on(l, lb[l].a, lb[l].b, m);
+                k_pad_block(dst, lb[l].b, m, f4, ls);
             }
         }
-        phase("M_inverses");
-        // coarse matrix C = Z^T S Z from the row sums (host), then K
-        std::vector<double> rho_h((size_t)S.sRho);
-        CK(cudaMemcpyAsync(rho_h.data(), S.rho + (size_t)o * S.sRho, sizeof(double) * S.sRho, cudaMemcpyDeviceToHost, st));
-        CK(cudaStreamSynchronize(st));
-        const int gs = fz / ng;
+    }
+    join();
+    phase("M_inverses");
+
+    // phase 4: coarse matrix C = Z^T S Z from the row sums (host), then its
+    // division K on the GPU (Sec. 3.3)
+    std::vector<double> rho_h((size_t)nop * S.sRho);
+    CK(cudaMemcpyAsync(rho_h.data(), S.rho, sizeof(double) * rho_h.size(), cudaMemcpyDeviceToHost, st));
+    CK(cudaStreamSynchronize(st));
+    const int gs = fz / ng;
+    int lwork_d = 0;
+    CS(cusolverDnDgetrf_bufferSize(S.sol, d, d, S.K, d, &lwork_d));
+    double* dC = S.dalloc<double>((size_t)d * d, tmp);
+    double* dwork_d = S.dalloc<double>((size_t)std::max(lwork_d, 1), tmp);
+    int* dipiv_d = S.dalloc<int>((size_t)d, tmp);
+    double* duC = S.dalloc<double>((size_t)d, tmp);
+    double* dw = S.dalloc<double>((size_t)d, tmp);
+    std::vector<double> C((size_t)d * d), uC;
+    for (int o = 0; o < nop; ++o) {
+        const double k2 = S.k2[o];
+        const double* rho_o = rho_h.data() + (size_t)o * S.sRho;
         // gsum[cls][side][g][half][g'] = sum over group g' of half `half` of rho[cls][side][g]
-        auto rh = [&](int cls, int side, int gg) { return rho_h.data() + ((size_t)(cls * 2 + side) * ng + gg) * f2; };
+        auto rh = [&](int cls, int side, int gg) { return rho_o + ((size_t)(cls * 2 + side) * ng + gg) * f2; };
         auto gsum = [&](int cls, int side, int gg, int half, int gp) {
             const double* v = rh(cls, side, gg) + half * fz + gp * gs;
-            double s = 0.0;
-            for (int z = 0; z < gs; ++z) s += v[z];
-            return s;
+            double sm = 0.0;
+            for (int z = 0; z < gs; ++z) sm += v[z];
+            return sm;
         };
-        std::vector<double> C((size_t)d * d, 0.0);
+        std::fill(C.begin(), C.end(), 0.0);
         for (int t = 0; t < nif; ++t)
             for (int gg = 0; gg < ng; ++gg) {
                 const int col = t * ng + gg;
@@ -550,29 +689,44 @@ static void setup_solver(Solver& S) {
                     if (t + 1 <= nif - 1) C[(size_t)((t + 1) * ng + gp) * d + col] += gsum(cl_r, 0, gg, 1, gp);
                 }
             }
-        std::vector<double> Kh, uC;
         const double* uCp = nullptr;
         if (k2 == 0.0) {  // u_C = Z^T u_S normalised (Sec. 3.3)
             uC.assign(d, 0.0);
             double nrm = 0.0;
             for (int t = 0; t < nif; ++t)
                 for (int gg = 0; gg < ng; ++gg) {
-                    double s = 0.0;
+                    double sm = 0.0;
                     for (int z = 0; z < gs; ++z)
-                        s += uS_h[(size_t)(2 * t + 1) * fz + gg * gs + z] + uS_h[(size_t)(2 * t + 2) * fz + gg * gs + z];
-                    uC[t * ng + gg] = s;
-                    nrm += s * s;
+                        sm += uS_h[(size_t)(2 * t + 1) * fz + gg * gs + z] + uS_h[(size_t)(2 * t + 2) * fz + gg * gs + z];
+                    uC[t * ng + gg] = sm;
+                    nrm += sm * sm;
                 }
             nrm = std::sqrt(nrm);
             for (double& v : uC) v /= nrm;
             uCp = uC.data();
         }
-        std::string msg;
-        if (!coarse_operator(C, d, fz / ng, uCp, Kh, msg)) throw Err{SMPM_EBREAKDOWN, msg};
-        upload(S.K + (size_t)o * S.sK, Kh, st);
-        CK(cudaStreamSynchronize(st));
-        phase("coarse");
+        coarse_matrix(C, d, fz / ng, uCp);   // C + alpha u_C 1^T / sqrt(d) when singular
+        double* K = S.K + (size_t)o * S.sK;
+        upload(dC, C, st);
+        if (inv_used >= n_inv) throw Err{SMPM_ECUDA, "setup: inversion count exceeded"};
+        int* info = d_infos + 2 * inv_used++;
+        k_identity(K, d, st);
+        CS(cusolverDnDgetrf(S.sol, d, d, dC, d, dwork_d, dipiv_d, info));
+        CS(cusolverDnDgetrs(S.sol, CUBLAS_OP_N, d, d, dC, d, dipiv_d, K, d, info + 1));
+        if (uCp) {
+            upload(duC, uC, st);
+            k_project_coarse(K, dw, duC, d, st);
+        }
+        CK(cudaStreamSynchronize(st));   // C and uC are reused by the next operator
     }
+    std::vector<int> infos((size_t)2 * inv_used);
+    if (inv_used > 0) {
+        CK(cudaMemcpyAsync(infos.data(), d_infos, sizeof(int) * infos.size(), cudaMemcpyDeviceToHost, st));
+        CK(cudaStreamSynchronize(st));
+    }
+    for (int v : infos)
+        if (v != 0) throw Err{SMPM_EBREAKDOWN, "singular strip slot, block-Jacobi or coarse matrix (getrf info " + std::to_string(v) + ")"};
+    phase("coarse");
     if (S.precision == 1) {
         S.Minv32 = S.dalloc<float>((size_t)nop * S.nmc * S.sM, S.allocs);
         k_to_fp32(S.Minv32, S.Minv, (long long)nop * S.nmc * S.sM, st);

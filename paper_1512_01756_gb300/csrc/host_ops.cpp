@@ -402,31 +402,22 @@ static bool dense_solve(std::vector<double>& A, int d, std::vector<double>& X, i
     return true;
 }
 
-bool coarse_operator(const std::vector<double>& C, int d, int fz_over_ng, const double* uC,
-                     std::vector<double>& K, std::string& msg) {
+void coarse_matrix(std::vector<double>& C, int d, int fz_over_ng, const double* uC) {
     // Singular C (k^2 = 0): C 1 = 0 and u_C^T C = 0.  The regularised division
     // C \ (I - u_C u_C^T) q is taken as the zero-mean solution of the consistent
     // system, obtained from the nonsingular C + alpha u_C 1^T / sqrt(d): for
     // q' = (I - u_C u_C^T) q it returns c with C c = q' and 1^T c = 0, and it
-    // absorbs the rounding-level part of q' outside range(C) smoothly.
-    // Nonsingular C (k^2 > 0): K = C^-1.
-    std::vector<double> A = C;
-    K.assign((size_t)d * d, 0.0);
-    for (int i = 0; i < d; ++i) K[(size_t)i * d + i] = 1.0;
-    if (uC) {
-        double amax = 0.0;
-        for (double v : C) amax = std::max(amax, std::fabs(v));
-        // scale of the rank-1 term: |C| plus the identity part of each coarse
-        // entry (2 fz / ng), so that a ~0 1 x 1 coarse matrix (mx = 2) stays regular
-        const double a = (amax + 2.0 * (double)fz_over_ng) / std::sqrt((double)d);
-        for (int i = 0; i < d; ++i)
-            for (int j = 0; j < d; ++j) {
-                A[(size_t)i * d + j] += a * uC[i];
-                K[(size_t)i * d + j] -= uC[i] * uC[j];
-            }
-    }
-    if (!dense_solve(A, d, K, d)) { msg = "coarse matrix factorisation hit a zero pivot"; return false; }
-    return true;
+    // absorbs the rounding-level part of q' outside range(C) smoothly.  The
+    // caller forms K = (C + alpha u_C 1^T / sqrt(d))^-1 (I - u_C u_C^T).
+    // Nonsingular C (k^2 > 0): C is left as it is and K = C^-1.
+    if (!uC) return;
+    double amax = 0.0;
+    for (double v : C) amax = std::max(amax, std::fabs(v));
+    // scale of the rank-1 term: |C| plus the identity part of each coarse
+    // entry (2 fz / ng), so that a ~0 1 x 1 coarse matrix (mx = 2) stays regular
+    const double a = (amax + 2.0 * (double)fz_over_ng) / std::sqrt((double)d);
+    for (int i = 0; i < d; ++i)
+        for (int j = 0; j < d; ++j) C[(size_t)i * d + j] += a * uC[i];
 }
 
 // --- real block diagonalisation of a small nonsymmetric matrix ----------------

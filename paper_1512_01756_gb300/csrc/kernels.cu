@@ -723,6 +723,33 @@ void k_identity(double* X, int m, cudaStream_t s) {
     count_launches(1);
 }
 
+// Coarse division of the singular coarse matrix (Sec. 3.3): K = A^-1 (I - u u^T)
+// = A^-1 - (A^-1 u) u^T in place on the row-major d x d buffer holding A^-1.
+// w = A^-1 u: one warp per row.
+__global__ void rowdot_kernel(double* __restrict__ w, const double* __restrict__ A, const double* __restrict__ u, int d) {
+    const int row = blockIdx.x * (blockDim.x / 32) + threadIdx.x / 32, lane = threadIdx.x & 31;
+    if (row >= d) return;
+    const double* a = A + (size_t)row * d;
+    double acc = 0.0;
+    for (int j = lane; j < d; j += 32) acc += a[j] * u[j];
+    for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+    if (lane == 0) w[row] = acc;
+}
+
+__global__ void rank1_sub_kernel(double* __restrict__ A, const double* __restrict__ w, const double* __restrict__ u, int d) {
+    const long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx >= (long long)d * d) return;
+    const int i = (int)(idx / d), j = (int)(idx - (long long)i * d);
+    A[idx] -= w[i] * u[j];
+}
+
+void k_project_coarse(double* K, double* w, const double* u, int d, cudaStream_t s) {
+    rowdot_kernel<<<(d + 7) / 8, 256, 0, s>>>(w, K, u, d);
+    const long long tot = (long long)d * d;
+    rank1_sub_kernel<<<(unsigned)((tot + 255) / 256), 256, 0, s>>>(K, w, u, d);
+    count_launches(2);
+}
+
 // W = B_c A_c^-1 (2 fz x n fz): row (s, Z) = sum_a beta[s][a] Ainv[(a, Z), :]
 __global__ void build_W_kernel(double* __restrict__ W, const double* __restrict__ Ainv,
                                const double* __restrict__ beta, int n, int fz) {

@@ -94,6 +94,8 @@ void k_gauge(const GridArgs& g, int R, double* u, long long u_ld, const int* app
 void k_build_strip_op(double* A, const double* Ax, const double* Lz, double k2, int n, int fz,
                       cudaStream_t s);
 void k_identity(double* X, int m, cudaStream_t s);
+// K <- K - (K u) u^T (row-major d x d, w: d scratch): the projected coarse division
+void k_project_coarse(double* K, double* w, const double* u, int d, cudaStream_t s);
 void k_build_W(double* W, const double* Ainv, const double* beta, int n, int fz, cudaStream_t s);
 void k_build_G(double* G, const double* W, int n, int fz, int cls, cudaStream_t s);
 // Pair block of block-Jacobi (Sec. 3.2) from the G of strips 2p, 2p+1, 2p+2

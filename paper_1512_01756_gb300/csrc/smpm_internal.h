@@ -69,11 +69,11 @@ bool left_null_banded(const std::vector<double>& M, int n, int bw, std::vector<d
 bool left_null_x(const Geometry& g, std::vector<double>& v, std::string& msg);
 bool left_null_z(const Geometry& g, std::vector<double>& v, std::string& msg);
 
-// Coarse operator K (d x d row-major) of the deflation: for singular C
-// (k^2 = 0) K = (C + a uC 1^T / sqrt d)^-1 (I - uC uC^T) (the zero-mean
-// solution of the consistent coarse system), else K = C^-1.
-bool coarse_operator(const std::vector<double>& C, int d, int fz_over_ng, const double* uC,
-                     std::vector<double>& K, std::string& msg);
+// Coarse matrix of the deflation (d x d row-major, in place): for singular C
+// (k^2 = 0, uC given) C + a uC 1^T / sqrt d, whose inverse times
+// (I - uC uC^T) is the coarse division K (the zero-mean solution of the
+// consistent coarse system); else C unchanged (K = C^-1).
+void coarse_matrix(std::vector<double>& C, int d, int fz_over_ng, const double* uC);
 
 // Ax = Q B Q^-1 with B block diagonal in real form: slot t covers columns
 // [slot_start, slot_start + slot_size) of Q; size 1: eigenvalue alpha; size 2:
