@@ -496,8 +496,28 @@ def run_serve(args):
     served_span = max(done.values())
     torch.cuda.synchronize()
     launches = smpm.kernel_launches() - l0
+
+    # served capacity: the whole stream submitted at once (offered load above
+    # what the server completes), results checked against the first pass
+    for q in reqs:
+        q["u_burst"] = torch.zeros_like(q["f"])
+    t0 = time.perf_counter()
+    burst = [srv.submit(q["grid"], q["k2"], q["f"], q["u_burst"], tol=TOL) for q in reqs]
+    pend = set(burst)
+    res_burst = []
+    while pend:
+        for tk in list(pend):
+            st = srv.poll(tk)
+            if st is not None:
+                res_burst.append(st.rel_resid_true)
+                pend.discard(tk)
+        time.sleep(0.0002)
+    burst_span = time.perf_counter() - t0
+    torch.cuda.synchronize()
     clk = clocks.stop()
     srv.close()
+    diffs_burst = [float(torch.linalg.norm(q["u_burst"] - q["u_plain"]) / torch.linalg.norm(q["u_plain"]))
+                   for q in reqs]
     diffs = [float(torch.linalg.norm(q["u_served"] - q["u_plain"]) / torch.linalg.norm(q["u_plain"])) for q in reqs]
 
     def pct(v, p):
@@ -517,13 +537,17 @@ def run_serve(args):
                         f"orders {SERVE_ORDERS}, k^2 = 0 (10 %) else log-uniform [1e-2, 1e4], cos-cos f; Poisson "
                         f"arrivals at the plain path's saturation rate {lam:.2f}/s",
             "metric": "solves/s at 1e-10 rel. residual, p50/p99 latency: served vs plain FP64",
-            "unit": "solves/s", "value": len(reqs) / served_span, "dtype": "f64", "data": "synthetic",
-            "served": {"solves_per_s": len(reqs) / served_span, "p50_ms": pct(lat_served, 50),
+            "unit": "solves/s", "value": len(reqs) / burst_span, "dtype": "f64", "data": "synthetic",
+            "value_is": "served capacity: the stream submitted at once",
+            "served": {"capacity_solves_per_s": len(reqs) / burst_span,
+                       "solves_per_s_at_arrival_rate": len(reqs) / served_span, "p50_ms": pct(lat_served, 50),
                        "p99_ms": pct(lat_served, 99), "workers": args.workers, "max_batch": args.max_batch,
-                       "mean_batch": float(np.mean(batch_sizes)), "worst_rel_resid": max(res_served)},
-            "plain_fp64": {"solves_per_s": plain_rate, "p50_ms": pct(lat_plain, 50), "p99_ms": pct(lat_plain, 99),
+                       "mean_batch": float(np.mean(batch_sizes)),
+                       "worst_rel_resid": max(max(res_served), max(res_burst))},
+            "plain_fp64": {"capacity_solves_per_s": lam, "solves_per_s_at_arrival_rate": plain_rate,
+                           "p50_ms": pct(lat_plain, 50), "p99_ms": pct(lat_plain, 99),
                            "mean_service_ms": 1e3 * float(np.mean(service)), "worst_rel_resid": max(res_plain)},
-            "served_vs_plain_max_rel_diff": max(diffs),
+            "served_vs_plain_max_rel_diff": max(max(diffs), max(diffs_burst)),
             "latency": "completion - arrival, operator setup included",
             "gpu_launches": launches, "clocks": clk, "per_grid_plain": by_grid}
     print(json.dumps(line), flush=True)
