@@ -14,6 +14,8 @@ Test infrastructure only (see ``oracle/__init__.py``).
   u_C = Z^T u_S normalised, the projections P and Q.  "C \\" on the singular
   coarse matrix is read as the minimum-norm least-squares solve.  Optional
   finer groups: one indicator per interface and element row.
+* ``RangeProjected``: for k^2 = 0 the Krylov operator is (I - u_S u_S^T) S,
+  the range-projected Schur matrix (equal to S in exact arithmetic).
 * ``solve``: Alg. seq (method "dbj") and the comparison methods of
   Table table_methods ("schur", "bj", "2las"), with P applied literally
   (a second S product per iteration, as the paper does).
@@ -24,6 +26,30 @@ import scipy.sparse as sp
 
 from .smpm import Grid, rhs, gauge
 from .schur import StripSchur
+
+
+class RangeProjected:
+    """S_reg = (I - u_S u_S^T) S, the singular Schur matrix with its range
+    projected out of the left null vector u_S.
+
+    Eq. regularize_schur makes the system consistent by projecting b_S out of
+    u_S, which presumes u_S^T S = 0.  The assembled S (from rounded strip
+    solves) satisfies that only to rounding, ~1e-13 |S|, so S x_S keeps a u_S
+    component of that relative size times |x_S| that no iterate removes; when
+    |x_S| >> |b_S| (right-hand sides dominated by long x-waves) GMRES then
+    stops on that floor with an error of ~1e-9 in u.  Projecting the range the
+    same way keeps the system consistent in floating point; in exact
+    arithmetic S_reg = S.  Vectors only (the coarse matrix is corrected in
+    ``Deflation``)."""
+
+    def __init__(self, S, uS):
+        self.S = S
+        self.uS = uS
+        self.shape = S.shape
+
+    def __matmul__(self, v):
+        y = self.S @ v
+        return y - self.uS * np.dot(self.uS, y)
 
 
 def householder_gmres(apply, b, tol, maxiter):
@@ -158,8 +184,13 @@ class Deflation:
         self.group_size = g.fz if groups == "interface" else g.n
         self.Z = sp.coo_matrix((np.ones(r.size), (r, c)), shape=(g.k, self.d)).tocsr()
         self.S = S
-        self.SZ = (S @ self.Z).tocsr()
-        self.C = (self.Z.T @ self.SZ).toarray()
+        if isinstance(S, RangeProjected):
+            # C = Z^T (I - u_S u_S^T) S Z = Z^T S Z - (Z^T u_S)(u_S^T S Z)
+            SZ = (S.S @ self.Z).tocsr()
+            self.C = (self.Z.T @ SZ).toarray() - np.outer(self.Z.T @ S.uS, SZ.T @ S.uS)
+        else:
+            SZ = (S @ self.Z).tocsr()
+            self.C = (self.Z.T @ SZ).toarray()
         if uS is not None:
             uC = self.Z.T @ uS
             self.uC = uC / np.linalg.norm(uC)
@@ -218,14 +249,17 @@ def solve(g: Grid, f, gb=None, k2=0.0, method="dbj", tol=1e-13, maxiter=2000,
     if k2 == 0.0:
         bS = bS - uS * np.dot(uS, bS)                # step 3
     info = {}
+    Sraw = S
+    if k2 == 0.0:
+        S = RangeProjected(Sraw, uS)                 # consistent in floating point
     if method == "schur":
         xS, it, hist = householder_gmres(lambda v: S @ v, bS, tol, maxiter)
     elif method == "bj":
-        M = BlockJacobi(g, S, singular=(k2 == 0.0))
+        M = BlockJacobi(g, Sraw, singular=(k2 == 0.0))
         y, it, hist = householder_gmres(lambda v: S @ M.solve(v), bS, tol, maxiter)
         xS = M.solve(y)
     elif method == "dbj":
-        M = BlockJacobi(g, S, singular=(k2 == 0.0))
+        M = BlockJacobi(g, Sraw, singular=(k2 == 0.0))
         Df = Deflation(g, S, uS, groups, coarse)
         x1, it, hist = householder_gmres(lambda v: Df.P(S @ M.solve(v)), Df.P(bS), tol, maxiter)  # step 4
         x1 = Df.Q(M.solve(x1))                       # step 5
@@ -233,7 +267,7 @@ def solve(g: Grid, f, gb=None, k2=0.0, method="dbj", tol=1e-13, maxiter=2000,
         xS = x1 + x2                                 # step 8
         info["coarse_dim"] = Df.d
     elif method == "2las":
-        M = BlockJacobi(g, S, singular=(k2 == 0.0))
+        M = BlockJacobi(g, Sraw, singular=(k2 == 0.0))
         Df = Deflation(g, S, uS, groups, coarse)
         prec = lambda v: M.solve(v) + Df.coarse_part(v)
         y, it, hist = householder_gmres(lambda v: S @ prec(v), bS, tol, maxiter)
