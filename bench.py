@@ -45,9 +45,10 @@ def parse():
     p.add_argument("--impl", default="ours", choices=["ours", "reference"])
     p.add_argument("--cpu-sample", type=int, default=2, help="oracle right-hand sides in the cpu_baseline leg")
     p.add_argument("--no-cpu-baseline", action="store_true")
-    p.add_argument("--workload", default="poisson2d", choices=["poisson2d", "modes3d", "mixed", "serve"],
-                   help="poisson2d: the default bench line; modes3d / mixed / serve: the 3-D, mixed-precision "
-                        "and serving configurations, measured separately (not the driver's bench line)")
+    p.add_argument("--workload", default="poisson2d", choices=["poisson2d", "small", "modes3d", "mixed", "serve"],
+                   help="poisson2d: the default bench line; small / modes3d / mixed / serve: the 8x2 latency, 3-D, "
+                        "mixed-precision and serving configurations, measured separately (not the driver's "
+                        "bench line)")
     p.add_argument("--requests", type=int, default=200, help="serve: requests in the stream")
     p.add_argument("--workers", type=int, default=4, help="serve: server worker threads (one stream each)")
     p.add_argument("--max-batch", type=int, default=16, help="serve: requests per batch at most")
@@ -328,9 +329,11 @@ def run_other(args):
     flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
     lines = []
 
-    def timed(fn):
+    def timed(fn, solver=None):
         for _ in range(args.warmup):
             fn()
+        if solver is not None:
+            solver.profile_read(reset=True)      # count only the timed solves
         ts = []
         for _ in range(args.steps):
             flush.fill_(1.0)
@@ -343,14 +346,40 @@ def run_other(args):
             ts.append(e0.elapsed_time(e1))
         return sum(ts) / len(ts), st
 
-    if args.workload == "modes3d":
+    def gemm_roofline(s, ms_total, peak, dtype):
+        p = s.profile_read(reset=True)
+        if p["ms"] <= 0:
+            return None
+        ach = p["flops"] / (p["ms"] * 1e-3) / 1e12
+        return {"bound": "alu", "kernel": f"class_gemm_kernel ({dtype})", "achieved": ach, "peak": peak,
+                "unit": "TFLOP/s", "frac": ach / peak if peak else None, "launches": p["launches"],
+                "gemm_share_of_step": p["ms"] / ms_total}
+
+    if args.workload == "small":
+        # 4 x 1 manufactured case, 8 x 2 elements, order 8: latency of one solve
+        for groups in (0, 1):
+            s = smpm.Solver(smpm.make_grid(8, 2, 8, 4.0, 1.0, deflation_groups=groups), 0.0, stream)
+            x, z = s.coords()
+            f, _ = inputs.manufactured_cos(x, z, 4.0, 1.0)
+            Fd = torch.from_numpy(f).to(dev)
+            Ud = torch.empty_like(Fd)
+            ms, st = timed(lambda: s.solve(Fd, Ud, tol=TOL))
+            lines.append({"workload": "2-D Poisson-Neumann 8x2 elements, order 8, domain 4x1, manufactured "
+                                      "u = cos(pi x/4) cos(pi z), one right-hand side",
+                          "deflation": "one vector per interface" if groups == 0 else "one per interface and element row",
+                          "metric": "us per solve at 1e-10 rel. residual", "value": ms * 1e3,
+                          "iters": st.iters, "worst_rel_resid": st.rel_resid_true, "setup_ms": st.setup_ms})
+            s.close()
+    elif args.workload == "modes3d":
         s = smpm.Solver3D(smpm.make_grid(128, 8, 10, 32.0, 1.0), 128, 2 * np.pi, stream)
         f3 = inputs.uniform((s.r, 128), inputs.seed_for(2))
         fh = np.fft.rfft(f3, axis=1) / 128
         F = torch.from_numpy(np.ascontiguousarray(np.stack([fh.real.T, fh.imag.T], axis=1))).to(dev)
         U = torch.empty_like(F)
-        ms, st = timed(lambda: s.solve_3d(F, U, tol=TOL))
-        lines.append({"workload": "3-D via Fourier: 128x8 elements, order 10, domain 32x1, m_y = 128 (65 modes, "
+        s.profile(True)
+        ms, st = timed(lambda: s.solve_3d(F, U, tol=TOL), s)
+        roof = gemm_roofline(s, ms * args.steps, FP64_NOMINAL_TFLOPS, "FP64")
+        lines.append({"roofline": roof, "workload": "3-D via Fourier: 128x8 elements, order 10, domain 32x1, m_y = 128 (65 modes, "
                                   "k_j = j), U[0,1] right-hand side, all modes in one batched solve",
                       "metric": "3-D solves/s at 1e-10 rel. residual (every mode)", "value": 1e3 / ms,
                       "ms_per_solve": ms, "iters": st.iters, "worst_rel_resid": st.rel_resid_true,
@@ -366,8 +395,12 @@ def run_other(args):
                           for i in range(R)])
             Fd = torch.from_numpy(F).to(dev)
             Ud = torch.empty_like(Fd)
-            ms, st = timed(lambda: s.solve(Fd, Ud, tol=TOL))
-            lines.append({"workload": "2-D Poisson-Neumann 512x16 elements, order 16, domain 32x1, z stretched "
+            s.profile(True)
+            ms, st = timed(lambda: s.solve(Fd, Ud, tol=TOL), s)
+            # mixed: FP64 and FP32 launches together, so no single peak applies
+            roof = gemm_roofline(s, ms * args.steps, None if prec else FP64_NOMINAL_TFLOPS,
+                                 "FP64 Schur and strip products, FP32 block-Jacobi" if prec else "FP64")
+            lines.append({"roofline": roof, "workload": "2-D Poisson-Neumann 512x16 elements, order 16, domain 32x1, z stretched "
                                       "geometrically (ratio 1.2), cos-cos modes, 4 right-hand sides per step",
                           "precision": "mixed: FP64 FGMRES, FP32 block-Jacobi" if prec else "FP64",
                           "metric": "solves/s at 1e-10 rel. residual", "value": R * 1e3 / ms, "ms_per_step": ms,

@@ -153,6 +153,12 @@ int smpm_grid_coords(const smpm_grid* grid, double* x, double* z);
  * handle's last solve (first n of them, host memory). */
 int smpm_last_residuals(smpm_handle h, int n, double* out);
 
+/* Left null vectors of the k^2 = 0 operator set (Claim 1): u_L (r doubles,
+ * node order, unit norm, L^T u_L = 0) and u_S = E^T u_L / |E^T u_L| (k doubles,
+ * interface order as in smpm_apply).  Host or device pointers.  SMPM_EINVAL if
+ * the handle has no k^2 = 0 operator set. */
+int smpm_null_vectors(smpm_handle h, double* uL, double* uS);
+
 /* Device bytes held by the handle (operators + workspace). */
 long long smpm_device_bytes(smpm_handle h);
 

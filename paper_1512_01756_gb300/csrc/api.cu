@@ -83,6 +83,7 @@ struct Solver {
     float* Minv32 = nullptr;              // FP32 block-Jacobi inverses (precision 1)
     int precision = 0;
     double *uL = nullptr, *uS = nullptr;
+    double* oneS = nullptr;                 // right null vector of S(0): 1 on the interface faces, unit norm
     int *rl_GW = nullptr, *rh_GW = nullptr, *rl_M = nullptr, *rh_M = nullptr, *rl_A = nullptr, *rh_A = nullptr;
     int* d_strip_cls = nullptr;
     double *d_tau_z = nullptr, *d_wq = nullptr, *d_hz = nullptr;
@@ -92,6 +93,7 @@ struct Solver {
     struct Work {
         double *b = nullptr, *t2 = nullptr, *bS = nullptr, *Xp = nullptr, *t = nullptr, *s = nullptr;
         double *w = nullptr, *z = nullptr, *xS = nullptr, *V = nullptr;
+        double *xSlo = nullptr, *slo = nullptr, *sxlo = nullptr;   // extended-precision refinement
         double *Hc = nullptr, *htmp = nullptr, *cs = nullptr, *sn = nullptr, *gv = nullptr;
         double *part1 = nullptr, *part2 = nullptr, *q = nullptr, *c = nullptr, *c0 = nullptr;
         double *fstage = nullptr, *gstage = nullptr, *ustage = nullptr, *rpart = nullptr;
@@ -99,6 +101,7 @@ struct Solver {
         double *target = nullptr, *bnorm = nullptr, *rnorm = nullptr;
         const double** uLp = nullptr;
         const double** uSp = nullptr;
+        const double** oneSp = nullptr;
         Tile *tM = nullptr, *tG = nullptr, *tW = nullptr, *tA = nullptr, *tS1 = nullptr, *tS2 = nullptr;
         int ntM = 0, ntG = 0, ntW = 0, ntA = 0, ntS1 = 0, ntS2 = 0;
         size_t capS1 = 0, capS2 = 0;
@@ -510,6 +513,14 @@ static void setup_solver(Solver& S) {
         for (double& v : uS_h) v /= nrm;
         S.uL = S.dalloc<double>((size_t)g.r, S.allocs);
         S.uS = S.dalloc<double>((size_t)S.ld, S.allocs);
+        {   // S 1 = 0 (constants are in the null space of the Neumann operator)
+            std::vector<double> one_h((size_t)S.ld, 0.0);
+            const double v = 1.0 / std::sqrt((double)g.k);
+            for (long long i = fz; i < S.kp - fz; ++i) one_h[(size_t)i] = v;
+            S.oneS = S.dalloc<double>((size_t)S.ld, S.allocs);
+            upload(S.oneS, one_h, st);
+            CK(cudaStreamSynchronize(st));
+        }
         upload(S.uL, uL_h, st);
         upload(S.uS, uS_h, st);
         CK(cudaStreamSynchronize(st));
@@ -769,7 +780,7 @@ static void ensure_workspace(Solver& S, int R) {
         w.fs3 = S.dalloc<double>((size_t)R * g.r, L);
         w.k2r = S.dalloc<double>((size_t)R, L);
     }
-    double** vecs[] = {&w.bS, &w.Xp, &w.t, &w.s, &w.w, &w.z, &w.xS};
+    double** vecs[] = {&w.bS, &w.Xp, &w.t, &w.s, &w.w, &w.z, &w.xS, &w.xSlo, &w.slo, &w.sxlo};
     for (double** v : vecs) {
         *v = S.dalloc<double>((size_t)R * ld, L);
         k_fill(*v, (long long)R * ld, 0.0, S.stream);
@@ -802,6 +813,7 @@ static void ensure_workspace(Solver& S, int R) {
     w.rnorm = S.dalloc<double>(R, L);
     w.uLp = (const double**)S.dalloc<double*>(R, L);
     w.uSp = (const double**)S.dalloc<double*>(R, L);
+    w.oneSp = (const double**)S.dalloc<double*>(R, L);
     // tile lists sized for the worst case (every rhs its own op): units * R
     const size_t tcap_strip = (size_t)(g.mx + 2) * R + 8;
     const size_t tcap_pair = (size_t)(S.P + 2) * R + 8;
@@ -898,12 +910,13 @@ static void prepare_ops(Solver& S, const std::vector<int>& ops) {
     CK(cudaMemcpyAsync(w.tM, tM.data(), tM.size() * sizeof(Tile), cudaMemcpyHostToDevice, S.stream));
     w.ntG = w.ntW = w.ntA = (int)tS.size();
     w.ntM = (int)tM.size();
-    std::vector<const double*> uLp(R, nullptr), uSp(R, nullptr);
+    std::vector<const double*> uLp(R, nullptr), uSp(R, nullptr), oneSp(R, nullptr);
     std::vector<int> gauge(R, 0);
     for (int r = 0; r < R; ++r)
         if (ops[r] == S.singular_op) {
             uLp[r] = S.uL;
             uSp[r] = S.uS;
+            oneSp[r] = S.oneS;
             gauge[r] = 1;
         }
     CK(cudaMemcpyAsync(w.op, ops.data(), R * sizeof(int), cudaMemcpyHostToDevice, S.stream));
@@ -916,6 +929,7 @@ static void prepare_ops(Solver& S, const std::vector<int>& ops) {
     CK(cudaMemcpyAsync(w.gauge, gauge.data(), R * sizeof(int), cudaMemcpyHostToDevice, S.stream));
     CK(cudaMemcpyAsync(w.uLp, uLp.data(), R * sizeof(double*), cudaMemcpyHostToDevice, S.stream));
     CK(cudaMemcpyAsync(w.uSp, uSp.data(), R * sizeof(double*), cudaMemcpyHostToDevice, S.stream));
+    CK(cudaMemcpyAsync(w.oneSp, oneSp.data(), R * sizeof(double*), cudaMemcpyHostToDevice, S.stream));
     CK(cudaStreamSynchronize(S.stream));
     S.cur_ops = ops;
 }
@@ -1022,8 +1036,35 @@ static int solve_impl(Solver& S, const std::vector<int>& ops, const double* f, c
         aW.out = w.bS; aW.out_rs = ld; aW.out_us = f2; aW.out_off0 = -fz; aW.out_off1 = f2; aW.msplit = fz;
         run_gemm(S, aW, w.tW, w.ntW, 0);
     }
+    // SMPM_TRACE_SOLVE=1: per-cycle true residual and iterate norms on stderr
+    const bool trace = std::getenv("SMPM_TRACE_SOLVE") != nullptr;
+    std::vector<double> tr_v;
+    auto host_norms = [&](const double* v, const char* name) {
+        tr_v.resize((size_t)R * ld);
+        CK(cudaMemcpyAsync(tr_v.data(), v, sizeof(double) * tr_v.size(), cudaMemcpyDeviceToHost, st_));
+        CK(cudaStreamSynchronize(st_));
+        for (int r = 0; r < R; ++r) {
+            double s2 = 0.0, s1 = 0.0;
+            for (long long i = 0; i < S.kp; ++i) {
+                const double x = tr_v[(size_t)r * ld + i];
+                s2 += x * x;
+                s1 += x;
+            }
+            fprintf(stderr, " %s[%d]: |v| %.3e sum %.3e", name, r, std::sqrt(s2), s1);
+        }
+    };
+    if (trace) {
+        fprintf(stderr, "smpm solve trace:");
+        host_norms(w.bS, "bS_unprojected");
+        fprintf(stderr, "\n");
+    }
     k_dot_partial(R, S.kp, w.bS, ld, w.uSp, w.rpart, nch, kChunk, st_);
     k_project(R, S.kp, w.bS, ld, w.uSp, w.rpart, nch, kChunk, st_);
+    if (trace) {
+        fprintf(stderr, "smpm solve trace:");
+        host_norms(w.bS, "bS");
+        fprintf(stderr, "\n");
+    }
 
     KArgs ka;
     std::memset(&ka, 0, sizeof(ka));
@@ -1060,6 +1101,17 @@ static int solve_impl(Solver& S, const std::vector<int>& ops, const double* f, c
         a.active = active;
         run_gemm(S, a, w.tG, w.ntG, 1);
     };
+    // compensated Schur product of x_S (hi part in out, low part in out_lo)
+    auto schur_ext = [&](const double* in, double* out, double* out_lo) {
+        GemmArgs a = gemm_base(S);
+        a.mats = S.G; a.mat_stride = S.sG; a.M = f2; a.K = f2;
+        a.row_lo = S.rl_GW; a.row_hi = S.rh_GW;
+        a.in = in; a.in_rs = ld; a.in_us = f2; a.in_off = 0;
+        a.out = out; a.out_rs = ld; a.out_us = f2; a.out_off0 = -fz; a.out_off1 = f2; a.msplit = fz;
+        a.add = in;
+        a.out_lo = out_lo;
+        run_gemm(S, a, w.tG, w.ntG, 3);
+    };
 
     CK(cudaMemsetAsync(w.done, 0, R * sizeof(int), st_));
     CK(cudaMemsetAsync(w.active, 0, R * sizeof(int), st_));
@@ -1072,15 +1124,100 @@ static int solve_impl(Solver& S, const std::vector<int>& ops, const double* f, c
     // P S M^-1 y = P d, and adds dx = t + Z K Z^T (d - S t), t = M^-1 V y
     // (= Q M^-1 y + Z C\ d of Eq. deflated_schur for this cycle's system).
     std::vector<int> h_done(R), h_active(R), h_nit(R), h_flags(R);
+    // Stagnation of the refinement: a right-hand side whose true residual is
+    // already within 1e3 tol and drops by less than 2x in two consecutive
+    // cycles has reached the FP64 floor of ||S x_S - b_S|| (rounding of the
+    // Schur product, ~ eps |G| |x_S|); it stops there with SMPM_ENOCONV instead
+    // of running to max_iter.
+    std::vector<double> prev_rel(R, -1.0), h_rn(R), h_bn(R);
+    std::vector<int> stall(R, 0);
+    const int one_i = 1, zero_i = 0;
+    bool stagnated = false;
     int total_it = 0, cycles = 0, status = SMPM_OK;
     bool first = true;
     const int check_every = 4;
+    // Extended-precision refinement: when the true residual stalls near tol
+    // (the FP64 rounding floor of S x_S, ~ eps |G| |x_S|, reached when |x_S| is
+    // far above |b_S|), the iterate is kept as x_S + x_lo (double-double), and
+    // the cycle-start residual b_S - S (x_S + x_lo) is formed with the
+    // compensated Schur product; the GMRES cycles themselves stay FP64
+    // (iterative refinement with an extra-precise residual).
+    bool ext = false;
+    if (std::getenv("SMPM_REFINE_EXTENDED") != nullptr) {   // from the first refinement step on
+        ext = true;
+        k_fill(w.xSlo, (long long)R * ld, 0.0, st_);
+        ka.xlo = w.xSlo;
+        ka.s_lo = w.slo;
+        ka.s_xlo = w.sxlo;
+    }
+    auto cycle_residual = [&](bool at_start) {
+        if (!at_start) {
+            if (ext) {
+                schur_ext(w.xS, w.s, w.slo);
+                schur(w.xSlo, ld, 0, w.sxlo, nullptr);
+            } else {
+                schur(w.xS, ld, 0, w.s, nullptr);
+            }
+            // k^2 = 0: b_S is projected out of u_S (Eq. regularize_schur), so the
+            // residual is taken in the same complement: d = (I - u_S u_S^T)(b_S - S x_S).
+            // The stored S (G from rounded strip solves) has u_S as left null
+            // vector only to ~1e-13 |S|; without this the u_S component of S x_S,
+            // ~1e-13 |S| |x_S|, is a residual floor no correction can reach
+            // (2.3e-10 on 512 x 16, order 12, where |x_S| ~ 250 |b_S|).
+            k_dot_partial(R, S.kp, w.s, ld, w.uSp, w.rpart, nch, kChunk, st_);
+            k_project(R, S.kp, w.s, ld, w.uSp, w.rpart, nch, kChunk, st_);
+        }
+        k_residual(ka, w.bS, at_start ? nullptr : w.s, st_);
+        k_cycle_start(ka, w.c0, at_start ? 1 : 0, tol, st_);
+    };
     while (true) {
-        if (!first) schur(w.xS, ld, 0, w.s, nullptr);
-        k_residual(ka, w.bS, first ? nullptr : w.s, st_);
-        k_cycle_start(ka, w.c0, first ? 1 : 0, tol, st_);
+        cycle_residual(first);
         CK(cudaMemcpyAsync(h_done.data(), w.done, R * sizeof(int), cudaMemcpyDeviceToHost, st_));
+        CK(cudaMemcpyAsync(h_rn.data(), w.rnorm, R * sizeof(double), cudaMemcpyDeviceToHost, st_));
+        CK(cudaMemcpyAsync(h_bn.data(), w.bnorm, R * sizeof(double), cudaMemcpyDeviceToHost, st_));
         CK(cudaStreamSynchronize(st_));
+        if (trace) {
+            fprintf(stderr, "smpm solve trace: cycle %d it %d", cycles, total_it);
+            for (int r = 0; r < R; ++r) fprintf(stderr, " rel[%d] %.3e", r, h_bn[r] > 0 ? h_rn[r] / h_bn[r] : 0.0);
+            host_norms(w.xS, "xS");
+            fprintf(stderr, "\n");
+        }
+        bool switch_ext = false;
+        for (int r = 0; r < R; ++r) {
+            if (h_done[r] || !(h_bn[r] > 0.0)) continue;
+            const double rel = h_rn[r] / h_bn[r];
+            stall[r] = (prev_rel[r] > 0.0 && rel > 0.5 * prev_rel[r] && rel < 1e3 * tol) ? stall[r] + 1 : 0;
+            prev_rel[r] = rel;
+            if (!ext && stall[r] >= 1) switch_ext = true;
+        }
+        if (switch_ext) {
+            ext = true;
+            k_fill(w.xSlo, (long long)R * ld, 0.0, st_);
+            ka.xlo = w.xSlo;
+            ka.s_lo = w.slo;
+            ka.s_xlo = w.sxlo;
+            std::fill(stall.begin(), stall.end(), 0);
+            cycle_residual(false);   // this cycle starts from the extra-precise residual
+            CK(cudaMemcpyAsync(h_done.data(), w.done, R * sizeof(int), cudaMemcpyDeviceToHost, st_));
+            CK(cudaMemcpyAsync(h_rn.data(), w.rnorm, R * sizeof(double), cudaMemcpyDeviceToHost, st_));
+            CK(cudaStreamSynchronize(st_));
+            for (int r = 0; r < R; ++r)
+                if (!h_done[r] && h_bn[r] > 0.0) prev_rel[r] = h_rn[r] / h_bn[r];
+            if (trace) {
+                fprintf(stderr, "smpm solve trace: extended residual");
+                for (int r = 0; r < R; ++r) fprintf(stderr, " rel[%d] %.3e", r, h_bn[r] > 0 ? h_rn[r] / h_bn[r] : 0.0);
+                fprintf(stderr, "\n");
+            }
+        }
+        for (int r = 0; r < R; ++r) {
+            if (h_done[r] || !(h_bn[r] > 0.0)) continue;
+            if (ext && stall[r] >= 2) {
+                CK(cudaMemcpyAsync(w.done + r, &one_i, sizeof(int), cudaMemcpyHostToDevice, st_));
+                CK(cudaMemcpyAsync(w.active + r, &zero_i, sizeof(int), cudaMemcpyHostToDevice, st_));
+                h_done[r] = 1;
+                stagnated = true;
+            }
+        }
         bool all = true;
         for (int r = 0; r < R; ++r) all &= h_done[r] != 0;
         if (all) break;
@@ -1120,6 +1257,12 @@ static int solve_impl(Solver& S, const std::vector<int>& ops, const double* f, c
         schur(w.t, ld, 0, w.s, nullptr);               // S t
         k_deflate_coarse_pending(ka, w.s, st_);        // c = K Z^T S t
         k_xs_update(ka, w.xS, w.t, w.c0, st_);         // x_S += t + Z (c0 - c)
+        // k^2 = 0: drop the component of x_S along the right null vector 1_S
+        // (S 1_S = 0, so S x_S is unchanged).  Left in place it grows from
+        // cycle to cycle and sets a rounding floor e |G| |x_S| on the true
+        // residual (seen as stagnation near 2e-10 on 512 x 16, order 12).
+        k_dot_partial(R, S.kp, w.xS, ld, w.oneSp, w.rpart, nch, kChunk, st_);
+        k_project(R, S.kp, w.xS, ld, w.oneSp, w.rpart, nch, kChunk, st_);
         CK(cudaStreamSynchronize(st_));
         int mx_it = 0;
         for (int r = 0; r < R; ++r) mx_it = std::max(mx_it, h_nit[r]);
@@ -1149,6 +1292,7 @@ static int solve_impl(Solver& S, const std::vector<int>& ops, const double* f, c
     CK(cudaGetLastError());
     harvest_profile(S);
     double worst = 0.0;
+    if (stagnated && status == SMPM_OK) status = SMPM_ENOCONV;
     for (int r = 0; r < R; ++r) {
         const double rel = h_b[r] > 0 ? h_r[r] / h_b[r] : 0.0;
         worst = std::max(worst, rel);
@@ -1454,6 +1598,20 @@ int smpm_last_residuals(smpm_handle h, int n, double* out) {
         const Solver& S = *(Solver*)h;
         if (n > (int)S.last_res.size()) throw Err{SMPM_EINVAL, "more values requested than the last solve had"};
         for (int i = 0; i < n; ++i) out[i] = S.last_res[i];
+        return SMPM_OK;
+    });
+}
+
+int smpm_null_vectors(smpm_handle h, double* uL, double* uS) {
+    return guarded([&] {
+        if (!h || !uL || !uS) throw Err{SMPM_EINVAL, "null argument"};
+        const Solver& S = *(Solver*)h;
+        if (S.singular_op < 0) throw Err{SMPM_EINVAL, "the handle has no k^2 = 0 operator set"};
+        const cudaMemcpyKind kl = is_device_ptr(uL) ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
+        const cudaMemcpyKind ks = is_device_ptr(uS) ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
+        CK(cudaMemcpyAsync(uL, S.uL, sizeof(double) * S.g.r, kl, S.stream));
+        CK(cudaMemcpyAsync(uS, S.uS + S.g.fz, sizeof(double) * S.g.k, ks, S.stream));
+        CK(cudaStreamSynchronize(S.stream));
         return SMPM_OK;
     });
 }

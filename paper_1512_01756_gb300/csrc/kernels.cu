@@ -79,6 +79,7 @@ __global__ void __launch_bounds__(GT) class_gemm_kernel(GemmArgs a, const Tile* 
     const int tid = threadIdx.x;
     const int tr = tid >> 3, tc = tid & 7;     // row 0..15, column group 0..7
     TM acc[4] = {TM(0), TM(0), TM(0), TM(0)};
+    double acc_lo[4] = {0.0, 0.0, 0.0, 0.0};   // EPI 3: running error of acc
 
     const double* colp[(BN * BK) / GT];
 #pragma unroll
@@ -104,11 +105,35 @@ __global__ void __launch_bounds__(GT) class_gemm_kernel(GemmArgs a, const Tile* 
             Bs[kk][c] = (colp[l] != nullptr && k < a.K) ? TM(colp[l][k]) : TM(0);
         }
         __syncthreads();
+        if (EPI == 3) {
+            // compensated dot products (Ogita, Rump & Oishi, "Accurate sum and
+            // dot product", 2005, Dot2): TwoProduct by FMA, TwoSum of the
+            // running sum, both errors gathered in acc_lo
 #pragma unroll
-        for (int kk = 0; kk < BK; ++kk) {
-            const TM av = As[kk][tr];
+            for (int kk = 0; kk < BK; ++kk) {
+                const double av = (double)As[kk][tr];
 #pragma unroll
-            for (int j = 0; j < 4; ++j) acc[j] = fma(av, Bs[kk][tc * 4 + j], acc[j]);
+                for (int j = 0; j < 4; ++j) {
+                    // __dmul_rn / __dadd_rn / __dsub_rn are never contracted
+                    // into FMAs, which the error-free transforms rely on
+                    const double bv = (double)Bs[kk][tc * 4 + j];
+                    const double p = __dmul_rn(av, bv);
+                    const double pe = fma(av, bv, -p);
+                    const double x = (double)acc[j];
+                    const double sum = __dadd_rn(x, p);
+                    const double bb = __dsub_rn(sum, x);
+                    const double se = __dadd_rn(__dsub_rn(x, __dsub_rn(sum, bb)), __dsub_rn(p, bb));
+                    acc[j] = (TM)sum;
+                    acc_lo[j] += pe + se;
+                }
+            }
+        } else {
+#pragma unroll
+            for (int kk = 0; kk < BK; ++kk) {
+                const TM av = As[kk][tr];
+#pragma unroll
+                for (int j = 0; j < 4; ++j) acc[j] = fma(av, Bs[kk][tc * 4 + j], acc[j]);
+            }
         }
         __syncthreads();
     }
@@ -123,6 +148,15 @@ __global__ void __launch_bounds__(GT) class_gemm_kernel(GemmArgs a, const Tile* 
         const long long base = (long long)r * a.out_rs + (long long)u * a.out_us + t.off;
         const long long addr = base + (row < a.msplit ? a.out_off0 + row : a.out_off1 + (row - a.msplit));
         double v = (double)acc[j];
+        if (EPI == 3) {   // (hi, lo) = add + acc + acc_lo, TwoSum for the first addition
+            const double x = a.add[addr];
+            const double sum = __dadd_rn(x, v);
+            const double bb = __dsub_rn(sum, x);
+            const double se = __dadd_rn(__dsub_rn(x, __dsub_rn(sum, bb)), __dsub_rn(v, bb));
+            a.out[addr] = sum;
+            a.out_lo[addr] = se + acc_lo[j];
+            continue;
+        }
         if (EPI == 1) v += a.add[addr];
         a.out[addr] = v;
     }
@@ -136,6 +170,8 @@ void launch_class_gemm(const GemmArgs& a, const Tile* d_tiles, int ntiles, int e
         class_gemm_kernel<0, float><<<grid, GT, 0, s>>>(a, d_tiles);
     else if (epi == 1)
         class_gemm_kernel<1, double><<<grid, GT, 0, s>>>(a, d_tiles);
+    else if (epi == 3)
+        class_gemm_kernel<3, double><<<grid, GT, 0, s>>>(a, d_tiles);
     else
         class_gemm_kernel<0, double><<<grid, GT, 0, s>>>(a, d_tiles);
     count_launches(1);
@@ -385,7 +421,8 @@ __global__ void __launch_bounds__(VB) residual_kernel(KArgs a, const double* __r
     double s2 = 0.0, b2 = 0.0, d2 = 0.0;
     for (long long e = e0 + threadIdx.x; e < e1; e += VB) {
         const double bb = b[e];
-        const double dd = bb - (sr ? sr[e] : 0.0);      // true residual b_S - S x_S
+        double dd = bb - (sr ? sr[e] : 0.0);            // true residual b_S - S x_S
+        if (sr && a.s_lo) dd = dd - a.s_lo[(long long)r * a.ld + e] - a.s_xlo[(long long)r * a.ld + e];
         const double x = dd - szc_at(a, r, e);          // deflated residual P d
         v0[e] = x;
         s2 = fma(x, x, s2);
@@ -482,7 +519,18 @@ __global__ void __launch_bounds__(VB) xs_update_kernel(KArgs a, double* __restri
             const long long ci = (long long)r * a.d + ((F - 1) >> 1) * a.ng + Z / gs;
             v += c0[ci] - a.c[ci];
         }
-        x[e] += v;
+        if (a.xlo) {   // x_S = x + xlo: TwoSum, then renormalise (Fast2Sum)
+            double* xl = a.xlo + (long long)r * a.ld;
+            const double xv = x[e];
+            const double sum = __dadd_rn(xv, v);
+            const double bb = __dsub_rn(sum, xv);
+            const double lo = __dadd_rn(xl[e], __dadd_rn(__dsub_rn(xv, __dsub_rn(sum, bb)), __dsub_rn(v, bb)));
+            const double hi = __dadd_rn(sum, lo);
+            xl[e] = __dsub_rn(lo, __dsub_rn(hi, sum));
+            x[e] = hi;
+        } else {
+            x[e] += v;
+        }
     }
 }
 

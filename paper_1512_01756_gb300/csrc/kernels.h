@@ -43,6 +43,11 @@ struct KArgs {
     double* bnorm;                 // [R] ||b_S||
     double* rnorm;                 // [R] residual norm at the last cycle start
     int* flags;                    // [R] bit 0: breakdown / non-finite
+    // extended-precision refinement (all null when off): x_S = xS + xlo, and
+    // S x_S = s + s_lo + s_xlo (compensated S xS, plain S xlo)
+    double* xlo;                   // [R][ld]
+    const double* s_lo;            // [R][ld]
+    const double* s_xlo;           // [R][ld]
 };
 
 void k_deflate_sum(const KArgs& a, const double* v, const double* vsub, cudaStream_t s);

@@ -108,6 +108,7 @@ struct GemmArgs {
     const int* active;        // per rhs: skip tiles whose columns are all inactive (may be null)
     unsigned long long* flops;  // if set: each working CTA adds 2 * rows * K * active columns
     int fp32;                 // 1: mats are float, arithmetic in FP32 (EPI 0 only)
+    double* out_lo;           // EPI 3: low parts of the compensated out = add + acc
 };
 
 // Number of kernels libsmpm has launched in this process.
