@@ -25,6 +25,7 @@
 #include <cstdio>
 #include <cmath>
 #include <cstring>
+#include <map>
 #include <memory>
 #include <string>
 #include <vector>
@@ -116,6 +117,28 @@ struct Solver {
     double setup_ms = 0.0;
     cusolverDnHandle_t sol = nullptr;
     // optional profiling of the class-GEMM launches (events + device flop counter)
+    // CUDA graphs of the Arnoldi step groups (between two convergence checks),
+    // keyed by (first step, steps, steps allowed in the cycle); valid for the
+    // current workspace, operator layout and profiling state.  A group is
+    // captured the second time it runs with the same key and replayed after.
+    struct GroupGraph {
+        cudaGraphExec_t exec = nullptr;
+        long long launches = 0;              // library kernels in the graph
+        std::vector<cudaEvent_t> ev;         // GEMM event pairs (profiling)
+    };
+    std::map<std::array<int, 3>, GroupGraph> graphs;
+    std::map<std::array<int, 3>, int> group_seen;
+    cudaStream_t cap_stream = nullptr;
+    std::vector<cudaEvent_t>* cap_events = nullptr;   // set while capturing with profiling on
+    bool graphs_ok = true;
+    void drop_graphs() {
+        for (auto& kv : graphs) {
+            if (kv.second.exec) cudaGraphExecDestroy(kv.second.exec);
+            for (cudaEvent_t e : kv.second.ev) cudaEventDestroy(e);
+        }
+        graphs.clear();
+        group_seen.clear();
+    }
     bool prof = false;
     std::vector<cudaEvent_t> ev;
     int ev_used = 0;
@@ -145,6 +168,8 @@ struct Solver {
     }
     ~Solver() {
         if (stream) cudaStreamSynchronize(stream);
+        drop_graphs();
+        if (cap_stream) cudaStreamDestroy(cap_stream);
         for (cudaEvent_t e : ev) cudaEventDestroy(e);
         free_list(wk.allocs);
         free_list(allocs);
@@ -757,6 +782,7 @@ static void setup_solver(Solver& S) {
 static void ensure_workspace(Solver& S, int R) {
     if (R <= S.Rcap) return;
     CK(cudaStreamSynchronize(S.stream));
+    S.drop_graphs();
     S.bytes -= S.wk_bytes;
     S.free_list(S.wk.allocs);
     S.wk.tS1 = S.wk.tS2 = nullptr;
@@ -885,6 +911,7 @@ static std::vector<Tile> make_slot_tiles(const Solver& S, const std::vector<int>
 
 static void prepare_ops(Solver& S, const std::vector<int>& ops) {
     if (ops == S.cur_ops) return;
+    S.drop_graphs();
     auto& w = S.wk;
     if (S.fss) {
         for (int sz = 1; sz <= 2; ++sz) {
@@ -959,6 +986,20 @@ static GemmArgs gemm_base(const Solver& S) {
 static constexpr int kEventPairs = 8192;
 
 static void run_gemm(Solver& S, GemmArgs a, const Tile* tiles, int ntiles, int epi) {
+    if (S.prof && S.cap_events) {   // inside a graph capture: the graph owns its events
+        a.flops = S.d_flops;
+        cudaEvent_t e0, e1;
+        CK(cudaEventCreate(&e0));
+        CK(cudaEventCreate(&e1));
+        S.cap_events->push_back(e0);
+        S.cap_events->push_back(e1);
+        // external records: real event-record nodes of the graph (a plain
+        // record inside a capture only orders the captured work)
+        CK(cudaEventRecordWithFlags(e0, S.stream, cudaEventRecordExternal));
+        launch_class_gemm(a, tiles, ntiles, epi, S.stream);
+        CK(cudaEventRecordWithFlags(e1, S.stream, cudaEventRecordExternal));
+        return;
+    }
     const bool rec = S.prof && S.ev_used < kEventPairs;
     if (S.prof) a.flops = S.d_flops;
     if (rec) CK(cudaEventRecord(S.ev[2 * S.ev_used], S.stream));
@@ -1136,6 +1177,7 @@ static int solve_impl(Solver& S, const std::vector<int>& ops, const double* f, c
     int total_it = 0, cycles = 0, status = SMPM_OK;
     bool first = true;
     const int check_every = 4;
+    const bool graphs_off = std::getenv("SMPM_NO_GRAPHS") != nullptr;
     // Extended-precision refinement: when the true residual stalls near tol
     // (the FP64 rounding floor of S x_S, ~ eps |G| |x_S|, reached when |x_S| is
     // far above |b_S|), the iterate is kept as x_S + x_lo (double-double), and
@@ -1225,27 +1267,89 @@ static int solve_impl(Solver& S, const std::vector<int>& ops, const double* f, c
         const int last_allowed = std::min(m, S.max_iter - total_it);
         int j = 0;
         const bool mixed = S.precision == 1;
-        for (; j < last_allowed; ++j) {
+        const bool use_graphs = S.graphs_ok && !graphs_off;
+        // one Arnoldi step j of every active right-hand side
+        auto step = [&](int jj) {
             // z_j = M^-1 v_j (FP32 block-Jacobi in the mixed form: the flexible
             // variant keeps z_j, so the cycle's correction is exactly sum y_j z_j)
-            bj(w.V, (long long)(m + 1) * ld, (long long)j * ld, w.z, ld, 0, w.active, mixed);
+            bj(w.V, (long long)(m + 1) * ld, (long long)jj * ld, w.z, ld, 0, w.active, mixed);
             if (mixed)
-                CK(cudaMemcpy2DAsync(w.Zb + (long long)j * ld, (size_t)m * ld * 8, w.z, (size_t)ld * 8,
+                CK(cudaMemcpy2DAsync(w.Zb + (long long)jj * ld, (size_t)m * ld * 8, w.z, (size_t)ld * 8,
                                      (size_t)S.kp * 8, R, cudaMemcpyDeviceToDevice, st_));
             schur(w.z, ld, 0, w.w, w.active);
             k_deflate_sum(ka, w.w, nullptr, st_);
             k_coarse(ka, st_);
-            k_cgs(ka, j, 0, st_);
-            k_cgs(ka, j, 1, st_);
-            k_cgs(ka, j, 2, st_);
-            k_normalize(ka, j, last_allowed, st_);
-            if ((j + 1) % check_every == 0 || j + 1 == last_allowed) {
-                CK(cudaMemcpyAsync(h_active.data(), w.active, R * sizeof(int), cudaMemcpyDeviceToHost, st_));
-                CK(cudaStreamSynchronize(st_));
-                bool any = false;
-                for (int r = 0; r < R; ++r) any |= h_active[r] != 0;
-                if (!any) { ++j; break; }
+            k_cgs(ka, jj, 0, st_);
+            k_cgs(ka, jj, 1, st_);
+            k_cgs(ka, jj, 2, st_);
+            k_normalize(ka, jj, last_allowed, st_);
+        };
+        while (j < last_allowed) {
+            const int cnt = std::min(check_every - j % check_every, last_allowed - j);
+            const std::array<int, 3> key{j, cnt, last_allowed};
+            Solver::GroupGraph* gg = nullptr;
+            if (use_graphs) {
+                auto it = S.graphs.find(key);
+                if (it != S.graphs.end()) {
+                    gg = &it->second;
+                } else if (++S.group_seen[key] >= 2) {
+                    // capture the group on a side stream, launch it on the solver's
+                    if (!S.cap_stream) CK(cudaStreamCreateWithFlags(&S.cap_stream, cudaStreamNonBlocking));
+                    Solver::GroupGraph g_new;
+                    cudaStream_t keep = S.stream;
+                    S.stream = st_ = S.cap_stream;
+                    if (S.prof) S.cap_events = &g_new.ev;
+                    const long long l0 = launch_count();
+                    cudaGraph_t graph = nullptr;
+                    cudaError_t e1 = cudaStreamBeginCapture(S.cap_stream, cudaStreamCaptureModeThreadLocal);
+                    if (e1 == cudaSuccess) {
+                        try {
+                            for (int jj = j; jj < j + cnt; ++jj) step(jj);
+                        } catch (...) {
+                            cudaStreamEndCapture(S.cap_stream, &graph);
+                            if (graph) cudaGraphDestroy(graph);
+                            S.stream = st_ = keep;
+                            S.cap_events = nullptr;
+                            throw;
+                        }
+                        e1 = cudaStreamEndCapture(S.cap_stream, &graph);
+                    }
+                    S.stream = st_ = keep;
+                    S.cap_events = nullptr;
+                    g_new.launches = launch_count() - l0;
+                    count_launches((int)-g_new.launches);     // counted again at every replay
+                    if (e1 == cudaSuccess && graph)
+                        e1 = cudaGraphInstantiate(&g_new.exec, graph, 0);
+                    if (graph) cudaGraphDestroy(graph);
+                    if (e1 != cudaSuccess || !g_new.exec) {
+                        cudaGetLastError();
+                        for (cudaEvent_t e : g_new.ev) cudaEventDestroy(e);
+                        S.graphs_ok = false;                 // direct launches from now on
+                    } else {
+                        gg = &(S.graphs[key] = std::move(g_new));
+                    }
+                }
             }
+            if (gg) {
+                CK(cudaGraphLaunch(gg->exec, st_));
+                count_launches((int)gg->launches);
+            } else {
+                for (int jj = j; jj < j + cnt; ++jj) step(jj);
+            }
+            j += cnt;
+            CK(cudaMemcpyAsync(h_active.data(), w.active, R * sizeof(int), cudaMemcpyDeviceToHost, st_));
+            CK(cudaStreamSynchronize(st_));
+            if (gg && S.prof) {
+                for (size_t e = 0; e + 1 < gg->ev.size(); e += 2) {
+                    float ms = 0.f;
+                    CK(cudaEventElapsedTime(&ms, gg->ev[e], gg->ev[e + 1]));
+                    S.prof_ms += ms;
+                    ++S.prof_launches;
+                }
+            }
+            bool any = false;
+            for (int r = 0; r < R; ++r) any |= h_active[r] != 0;
+            if (!any) break;
         }
         CK(cudaMemcpyAsync(h_nit.data(), w.nit, R * sizeof(int), cudaMemcpyDeviceToHost, st_));
         if (mixed) {
@@ -1636,6 +1740,10 @@ int smpm_profile(smpm_handle h, int enable) {
             for (auto& e : S.ev) CK(cudaEventCreate(&e));
             S.d_flops = S.dalloc<unsigned long long>(1, S.allocs);
             CK(cudaMemset(S.d_flops, 0, sizeof(unsigned long long)));
+        }
+        if (S.prof != (enable != 0)) {
+            CK(cudaStreamSynchronize(S.stream));
+            S.drop_graphs();
         }
         S.prof = enable != 0;
         return SMPM_OK;

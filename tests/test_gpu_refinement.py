@@ -73,3 +73,55 @@ def test_forced_extended_refinement_matches_plain(smpm, monkeypatch):
     assert np.linalg.norm(out[1] - out[0]) / np.linalg.norm(out[0]) < 1e-10
     u_ref, _ = direct_solve(Grid(*shape), f)
     assert np.linalg.norm(out[1] - u_ref) / np.linalg.norm(u_ref) < 1e-9
+
+
+def test_graph_replay_matches_direct_launches(smpm, monkeypatch):
+    """The Arnoldi step groups are captured as CUDA graphs the second time a
+    handle runs them and replayed after; the replayed solves must give the
+    direct launches' result bit for bit (same kernels, same order), for the
+    plain and the mixed-precision solve, on the legacy and on a side stream."""
+    from oracle.smpm import Grid
+    shape = (12, 4, 7, 3.0, 1.0)
+    F = np.random.default_rng(5).uniform(0, 1, (3, Grid(*shape).r))
+    for precision in (0, 1):
+        for stream in (None, torch.cuda.Stream()):
+            s = smpm.Solver(smpm.make_grid(*shape, precision=precision), 0.0, stream)
+            Fd = torch.from_numpy(F).cuda()
+            outs = []
+            for _ in range(4):                      # runs 3 and 4 replay graphs
+                Ud = torch.empty_like(Fd)
+                st = s.solve(Fd, Ud, tol=1e-10)
+                torch.cuda.synchronize()
+                assert st.status == 0 and st.rel_resid_true <= 1e-10
+                outs.append(Ud.cpu().numpy())
+            monkeypatch.setenv("SMPM_NO_GRAPHS", "1")
+            Ud = torch.empty_like(Fd)
+            s.solve(Fd, Ud, tol=1e-10)
+            torch.cuda.synchronize()
+            monkeypatch.delenv("SMPM_NO_GRAPHS")
+            s.close()
+            direct = Ud.cpu().numpy()
+            for o in outs:
+                assert np.array_equal(o, direct)
+
+
+def test_profiling_counts_replayed_gemms(smpm):
+    """GEMM profiling (events and the device FLOP counter) keeps counting when
+    the Arnoldi groups run as replayed graphs: the per-solve launch and FLOP
+    totals are the same for the direct, the capturing and the replaying solve."""
+    from oracle.smpm import Grid
+    shape = (12, 4, 7, 3.0, 1.0)
+    F = np.random.default_rng(6).uniform(0, 1, (2, Grid(*shape).r))
+    s = smpm.Solver(smpm.make_grid(*shape), 0.0, torch.cuda.Stream())
+    s.profile(True)
+    Fd = torch.from_numpy(F).cuda()
+    Ud = torch.empty_like(Fd)
+    per = []
+    for _ in range(4):
+        s.solve(Fd, Ud, tol=1e-10)
+        torch.cuda.synchronize()
+        per.append(s.profile_read(reset=True))
+    s.close()
+    for p in per:
+        assert p["ms"] > 0.0
+        assert p["launches"] == per[0]["launches"] and p["flops"] == per[0]["flops"], per
