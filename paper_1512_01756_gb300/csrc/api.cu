@@ -116,6 +116,7 @@ struct Solver {
     std::vector<double> last_res;           // per-rhs ||S x_S - b_S|| / ||b_S|| of the last solve
     double setup_ms = 0.0;
     cusolverDnHandle_t sol = nullptr;
+    int slot_cls[3] = {0, 1, 2};            // class whose slot inverses a class uses (mirror sharing)
     // optional profiling of the class-GEMM launches (events + device flop counter)
     // CUDA graphs of the Arnoldi step groups (between two convergence checks),
     // keyed by (first step, steps, steps allowed in the cycle); valid for the
@@ -246,7 +247,7 @@ static std::vector<Tile> single_strip_slot_tiles(const Solver& S, int o, int c, 
     for (size_t t = 0; t < S.sl_size[c].size(); ++t) {
         if (S.sl_size[c][t] != sz) continue;
         for (int rr = 0; rr < R; rr += kBN)
-            out.push_back(Tile{(o * 3 + c) * ns + S.sl_idx[c][t], 0, 1, rr, std::min(kBN, R - rr),
+            out.push_back(Tile{(o * 3 + S.slot_cls[c]) * ns + S.sl_idx[c][t], 0, 1, rr, std::min(kBN, R - rr),
                                (long long)S.sl_start[c][t] * S.g.fz});
     }
     return out;
@@ -293,7 +294,7 @@ struct LanePool {
     ~LanePool() { clear(); }
 };
 static thread_local LanePool t_lanes;
-static constexpr int kSetupLanes = 8;
+static constexpr int kSetupLanes = 16;
 
 static std::vector<Lane>& setup_lanes() {
     int dev = 0;
@@ -387,8 +388,36 @@ static void setup_solver(Solver& S) {
     // fast strip solver: block-diagonalise the three n x n x-factors (k-independent)
     std::vector<double> Qh[3], Qih[3], al[3], be[3];
     S.fss = true;
+    // Mirror symmetry: with uniform h_x the east boundary strip's x-factor is
+    // the west one's reflected (J Ax_0 J, J the order reversal) to rounding;
+    // then Ax_2 = (J Q_0) B_0 (J Q_0)^-1 and class 2 shares class 0's slot
+    // inverses (the refinement residual still uses the exact Ax_2).
+    {
+        double diff = 0.0, amax = 0.0;
+        for (int i = 0; i < n; ++i)
+            for (int j = 0; j < n; ++j) {
+                amax = std::max(amax, std::fabs(Ax[0][(size_t)i * n + j]));
+                diff = std::max(diff, std::fabs(Ax[0][(size_t)(n - 1 - i) * n + (n - 1 - j)] - Ax[2][(size_t)i * n + j]));
+            }
+        S.slot_cls[2] = (diff <= 1e-13 * amax) ? 0 : 2;
+    }
     for (int c = 0; c < 3 && S.fss; ++c) {
         std::string msg;
+        if (S.slot_cls[c] != c) {
+            const int c0 = S.slot_cls[c];
+            Qh[c].assign((size_t)n * n, 0.0);
+            Qih[c].assign((size_t)n * n, 0.0);
+            for (int i = 0; i < n; ++i)
+                for (int j = 0; j < n; ++j) {
+                    Qh[c][(size_t)i * n + j] = Qh[c0][(size_t)(n - 1 - i) * n + j];     // J Q_0
+                    Qih[c][(size_t)i * n + j] = Qih[c0][(size_t)i * n + (n - 1 - j)];   // Q_0^-1 J
+                }
+            al[c] = al[c0];
+            be[c] = be[c0];
+            S.sl_start[c] = S.sl_start[c0];
+            S.sl_size[c] = S.sl_size[c0];
+            continue;
+        }
         if (!real_block_diagonalise(Ax[c], n, Qh[c], Qih[c], S.sl_start[c], S.sl_size[c], al[c], be[c], msg))
             S.fss = false;
     }
@@ -602,7 +631,8 @@ static void setup_solver(Solver& S) {
     if (S.fss) {
         fork();
         for (int o = 0; o < nop; ++o)
-            for (int c = 0; c < 3; ++c)
+            for (int c = 0; c < 3; ++c) {
+                if (S.slot_cls[c] != c) continue;          // shares another class's slots
                 for (size_t t = 0; t < S.sl_size[c].size(); ++t) {
                     const int l = next_lane++ % L;
                     const int sz = S.sl_size[c][t], m = sz * fz, idx = S.sl_idx[c][t];
@@ -611,6 +641,7 @@ static void setup_solver(Solver& S) {
                                           : S.S2 + (((size_t)o * 3 + c) * std::max(S.ns2, 1) + idx) * 4 * fz * fz;
                     invert_on(l, lb[l].a, dst, m);
                 }
+            }
         join();
         phase("slot_inverses");
     }
@@ -893,7 +924,7 @@ static std::vector<Tile> make_slot_tiles(const Solver& S, const std::vector<int>
             const int c = S.strip_cls[ub];
             for (size_t t = 0; t < S.sl_size[c].size(); ++t) {
                 if (S.sl_size[c][t] != sz) continue;
-                const int mat = (ops[rb] * 3 + c) * ns + S.sl_idx[c][t];
+                const int mat = (ops[rb] * 3 + S.slot_cls[c]) * ns + S.sl_idx[c][t];
                 const long long off = (long long)S.sl_start[c][t] * S.g.fz;
                 for (int rr = rb; rr < re;) {
                     const int nr = std::min(kBN, re - rr);
