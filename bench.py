@@ -59,6 +59,24 @@ def rank_env():
     return int(os.environ.get("RANK", "0")), int(os.environ.get("LOCAL_RANK", "0")), int(os.environ.get("WORLD_SIZE", "1"))
 
 
+def rank_seed0(rank):
+    """First seed of a rank's right-hand sides: every rank solves its own
+    batch (weak scaling), seeds 1000 apart so batches never overlap."""
+    from paper_1512_01756_gb300 import inputs
+    return inputs.seed_for(1) + 1000 * rank
+
+
+def max_over_ranks(value, device, world):
+    """Max of a per-rank float over the process group (the slowest rank's
+    time decides the job's throughput); the value itself when world == 1."""
+    import torch
+    t = torch.tensor([float(value)], device=device, dtype=torch.float64)
+    if world > 1:
+        import torch.distributed as dist
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
 def make_f(x, z, nrhs, seed0):
     import numpy as np
     from paper_1512_01756_gb300 import inputs
@@ -212,7 +230,7 @@ def run_ours(args):
     grid = smpm.make_grid(**GRID)
     solver = smpm.Solver(grid, 0.0, stream)
     x, z = solver.coords()
-    F = make_f(x, z, R, inputs.seed_for(1) + 1000 * rank)
+    F = make_f(x, z, R, rank_seed0(rank))
     Fd = torch.from_numpy(F).to(dev)
     Ud = torch.empty_like(Fd)
     flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
@@ -247,11 +265,7 @@ def run_ours(args):
     solver.profile(False)
     barrier()
     clk = clocks.stop()
-    ms = sum(times) / len(times)
-    t = torch.tensor([ms], device=dev, dtype=torch.float64)
-    if world > 1:
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-    ms_max = float(t.item())
+    ms_max = max_over_ranks(sum(times) / len(times), dev, world)
     worst_res = max(s["rel_resid_true"] for s in stats)
     iters = [s["iters"] for s in stats]
 
@@ -267,10 +281,7 @@ def run_ours(args):
         w0 = time.perf_counter()
         solver.solve(Fh.numpy(), Uh.numpy(), tol=TOL)
         e2e_times.append(time.perf_counter() - w0)
-    e2 = torch.tensor([sum(e2e_times) / len(e2e_times)], device=dev, dtype=torch.float64)
-    if world > 1:
-        dist.all_reduce(e2, op=dist.ReduceOp.MAX)
-    e2e_s = float(e2.item())
+    e2e_s = max_over_ranks(sum(e2e_times) / len(e2e_times), dev, world)
     assert np.allclose(Uh.numpy(), Ud.cpu().numpy(), rtol=0, atol=1e-9 * np.abs(Uh.numpy()).max())
 
     fp64_probe = smpm.probe_fp64(stream)
