@@ -265,7 +265,8 @@ def run_ours(args):
     solver.profile(False)
     barrier()
     clk = clocks.stop()
-    ms_max = max_over_ranks(sum(times) / len(times), dev, world)
+    ms = sum(times) / len(times)
+    ms_max = max_over_ranks(ms, dev, world)
     worst_res = max(s["rel_resid_true"] for s in stats)
     iters = [s["iters"] for s in stats]
 
