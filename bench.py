@@ -400,7 +400,7 @@ def run_other(args):
     else:
         shape = dict(mx=512, mz=16, order=16, lx=32.0, lz=1.0, z_ratio=1.2)
         R = 4
-        for prec in (0, 1):
+        for prec in (0, 1, 2):
             s = smpm.Solver(smpm.make_grid(**shape, precision=prec), 0.0, stream)
             x, z = s.coords()
             F = np.stack([inputs.cos_modes(x, z, 32.0, 1.0, inputs.cos_modes_spec(inputs.seed_for(3) + i))[0]
@@ -411,10 +411,12 @@ def run_other(args):
             ms, st = timed(lambda: s.solve(Fd, Ud, tol=TOL), s)
             # mixed: FP64 and FP32 launches together, so no single peak applies
             roof = gemm_roofline(s, ms * args.steps, None if prec else FP64_NOMINAL_TFLOPS,
-                                 "FP64 Schur and strip products, FP32 block-Jacobi" if prec else "FP64")
+                                 "FP64 and FP32 launches" if prec else "FP64")
             lines.append({"roofline": roof, "workload": "2-D Poisson-Neumann 512x16 elements, order 16, domain 32x1, z stretched "
                                       "geometrically (ratio 1.2), cos-cos modes, 4 right-hand sides per step",
-                          "precision": "mixed: FP64 FGMRES, FP32 block-Jacobi" if prec else "FP64",
+                          "precision": ["FP64", "mixed: FP64 FGMRES, FP32 block-Jacobi",
+                                        "nested mixed: FP64 FGMRES, inner DBJ-GMRES with FP32 Schur "
+                                        "and block-Jacobi blocks"][prec],
                           "metric": "solves/s at 1e-10 rel. residual", "value": R * 1e3 / ms, "ms_per_step": ms,
                           "iters": st.iters, "worst_rel_resid": st.rel_resid_true, "setup_ms": st.setup_ms,
                           "device_bytes": s.device_bytes()})

@@ -65,7 +65,13 @@ typedef struct {
                                (Schur product, deflation, CGS2 Arnoldi, Givens,
                                true residual, projections, strip solves) with the
                                block-Jacobi preconditioner in FP32 (FP32 blocks,
-                               FP32 accumulation)                                    */
+                               FP32 accumulation); 2: nested mixed -- FP64
+                               flexible GMRES on S (true residual, projections,
+                               strip solves in FP64) preconditioned by an inner
+                               deflated block-Jacobi GMRES whose Schur products
+                               and block-Jacobi applies use FP32 blocks with FP32
+                               accumulation (10 inner steps or 1e-4 relative;
+                               SMPM_INNER_STEPS overrides the step count)      */
 } smpm_grid;
 
 typedef struct {

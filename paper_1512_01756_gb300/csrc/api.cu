@@ -81,7 +81,9 @@ struct Solver {
     int *d_zlo = nullptr, *d_zhi = nullptr;                          // nonzero window of each L_z row
     // device operators (all ops, contiguous per kind)
     double *Ainv = nullptr, *W = nullptr, *G = nullptr, *Minv = nullptr, *rho = nullptr, *K = nullptr;
-    float* Minv32 = nullptr;              // FP32 block-Jacobi inverses (precision 1)
+    float* Minv32 = nullptr;              // FP32 block-Jacobi inverses (precision 1 and 2)
+    float* G32 = nullptr;                 // FP32 Schur blocks (precision 2: the inner solve)
+    int inner_m = 10;                     // inner Arnoldi steps per outer step (precision 2)
     int precision = 0;
     double *uL = nullptr, *uS = nullptr;
     double* oneS = nullptr;                 // right null vector of S(0): 1 on the interface faces, unit norm
@@ -95,6 +97,12 @@ struct Solver {
         double *b = nullptr, *t2 = nullptr, *bS = nullptr, *Xp = nullptr, *t = nullptr, *s = nullptr;
         double *w = nullptr, *z = nullptr, *xS = nullptr, *V = nullptr;
         double *xSlo = nullptr, *slo = nullptr, *sxlo = nullptr;   // extended-precision refinement
+        // inner FP32-operator DBJ-GMRES of the nested mixed-precision form (precision 2)
+        double *Vi = nullptr, *Hci = nullptr, *htmpi = nullptr, *csi = nullptr, *sni = nullptr, *gvi = nullptr;
+        double *part1i = nullptr, *part2i = nullptr, *qi = nullptr, *ci = nullptr, *c0i = nullptr;
+        double *targeti = nullptr, *bnormi = nullptr, *rnormi = nullptr;
+        double *wi = nullptr, *zi = nullptr, *xi = nullptr, *ti = nullptr, *si = nullptr, *Xpi = nullptr, *vin = nullptr;
+        int *activei = nullptr, *donei = nullptr, *niti = nullptr, *flagsi = nullptr;
         double *Hc = nullptr, *htmp = nullptr, *cs = nullptr, *sn = nullptr, *gv = nullptr;
         double *part1 = nullptr, *part2 = nullptr, *q = nullptr, *c = nullptr, *c0 = nullptr;
         double *fstage = nullptr, *gstage = nullptr, *ustage = nullptr, *rpart = nullptr;
@@ -794,9 +802,13 @@ static void setup_solver(Solver& S) {
     for (int v : infos)
         if (v != 0) throw Err{SMPM_EBREAKDOWN, "singular strip slot, block-Jacobi or coarse matrix (getrf info " + std::to_string(v) + ")"};
     phase("coarse");
-    if (S.precision == 1) {
+    if (S.precision >= 1) {
         S.Minv32 = S.dalloc<float>((size_t)nop * S.nmc * S.sM, S.allocs);
         k_to_fp32(S.Minv32, S.Minv, (long long)nop * S.nmc * S.sM, st);
+    }
+    if (S.precision == 2) {
+        S.G32 = S.dalloc<float>((size_t)nop * 3 * S.sG, S.allocs);
+        k_to_fp32(S.G32, S.G, (long long)nop * 3 * S.sG, st);
     }
     CK(cudaStreamSynchronize(st));
     S.free_list(tmp);
@@ -844,9 +856,37 @@ static void ensure_workspace(Solver& S, int R) {
     }
     w.V = S.dalloc<double>((size_t)R * (m + 1) * ld, L);
     k_fill(w.V, (long long)R * (m + 1) * ld, 0.0, S.stream);
-    if (S.precision == 1) {
+    if (S.precision >= 1) {
         w.Zb = S.dalloc<double>((size_t)R * m * ld, L);
         k_fill(w.Zb, (long long)R * m * ld, 0.0, S.stream);
+    }
+    if (S.precision == 2) {
+        const int mi = S.inner_m;
+        w.Vi = S.dalloc<double>((size_t)R * (mi + 1) * ld, L);
+        k_fill(w.Vi, (long long)R * (mi + 1) * ld, 0.0, S.stream);
+        w.Hci = S.dalloc<double>((size_t)R * mi * (mi + 1), L);
+        w.htmpi = S.dalloc<double>((size_t)R * (mi + 1), L);
+        w.csi = S.dalloc<double>((size_t)R * mi, L);
+        w.sni = S.dalloc<double>((size_t)R * mi, L);
+        w.gvi = S.dalloc<double>((size_t)R * (mi + 1), L);
+        w.part1i = S.dalloc<double>((size_t)R * nch * (mi + 2), L);
+        w.part2i = S.dalloc<double>((size_t)R * nch * (mi + 2), L);
+        w.qi = S.dalloc<double>((size_t)R * g.d, L);
+        w.ci = S.dalloc<double>((size_t)R * g.d, L);
+        w.c0i = S.dalloc<double>((size_t)R * g.d, L);
+        w.targeti = S.dalloc<double>(R, L);
+        w.bnormi = S.dalloc<double>(R, L);
+        w.rnormi = S.dalloc<double>(R, L);
+        w.activei = S.dalloc<int>(R, L);
+        w.donei = S.dalloc<int>(R, L);
+        w.niti = S.dalloc<int>(R, L);
+        w.flagsi = S.dalloc<int>(R, L);
+        double** iv[] = {&w.wi, &w.zi, &w.xi, &w.ti, &w.si, &w.Xpi, &w.vin};
+        for (double** v : iv) {
+            *v = S.dalloc<double>((size_t)R * ld, L);
+            k_fill(*v, (long long)R * ld, 0.0, S.stream);
+        }
+        CK(cudaMemsetAsync(w.flagsi, 0, R * sizeof(int), S.stream));
     }
     w.Hc = S.dalloc<double>((size_t)R * m * (m + 1), L);
     w.htmp = S.dalloc<double>((size_t)R * (m + 1), L);
@@ -1149,6 +1189,21 @@ static int solve_impl(Solver& S, const std::vector<int>& ops, const double* f, c
     ka.active = w.active; ka.done = w.done; ka.nit = w.nit; ka.target = w.target;
     ka.bnorm = w.bnorm; ka.rnorm = w.rnorm; ka.flags = w.flags;
 
+    // Nested mixed-precision form (precision 2): the outer flexible GMRES runs
+    // on S itself (no deflation: K = null makes every coarse coefficient zero)
+    // and its preconditioner is an inner DBJ-GMRES with FP32 Schur blocks and
+    // FP32 block-Jacobi, inner_m steps or 1e-4 relative, from a zero guess.
+    const bool nested = S.precision == 2;
+    KArgs ki = ka;
+    if (nested) {
+        ki.m = S.inner_m;
+        ki.V = w.Vi; ki.w = w.wi; ki.Hc = w.Hci; ki.htmp = w.htmpi; ki.cs = w.csi; ki.sn = w.sni; ki.gv = w.gvi;
+        ki.part1 = w.part1i; ki.part2 = w.part2i; ki.q = w.qi; ki.c = w.ci;
+        ki.active = w.activei; ki.done = w.donei; ki.nit = w.niti; ki.target = w.targeti;
+        ki.bnorm = w.bnormi; ki.rnorm = w.rnormi; ki.flags = w.flagsi;
+        ka.K = nullptr;
+    }
+
     // block-Jacobi apply: out = Minv_p in over pairs p (faces [(4p+1) fz, (4p+5) fz))
     auto bj = [&](const double* in, long long in_rs, long long in_off, double* out, long long out_rs,
                   long long out_off, const int* active, bool fp32 = false) {
@@ -1172,6 +1227,45 @@ static int solve_impl(Solver& S, const std::vector<int>& ops, const double* f, c
         a.add = in;  // identity term, same layout when in_rs == ld and in_off == 0
         a.active = active;
         run_gemm(S, a, w.tG, w.ntG, 1);
+    };
+    // FP32 Schur product of the inner solve (FP32 blocks and accumulation)
+    auto schur32 = [&](const double* in, double* out, const int* active) {
+        GemmArgs a = gemm_base(S);
+        a.mats = reinterpret_cast<const double*>(S.G32); a.fp32 = 1;
+        a.mat_stride = S.sG; a.M = f2; a.K = f2;
+        a.row_lo = S.rl_GW; a.row_hi = S.rh_GW;
+        a.in = in; a.in_rs = ld; a.in_us = f2; a.in_off = 0;
+        a.out = out; a.out_rs = ld; a.out_us = f2; a.out_off0 = -fz; a.out_off1 = f2; a.msplit = fz;
+        a.add = in;
+        a.active = active;
+        run_gemm(S, a, w.tG, w.ntG, 1);
+    };
+    // z = inner solve of S z = V_j for the active right-hand sides (one
+    // deflated right-preconditioned GMRES cycle from z = 0, Alg. seq steps
+    // 4-8 with FP32 operators), result in w.xi
+    auto inner_solve = [&](int jj) {
+        const int mi = S.inner_m;
+        CK(cudaMemcpy2DAsync(w.vin, (size_t)ld * 8, w.V + (long long)jj * ld, (size_t)(m + 1) * ld * 8,
+                             (size_t)S.kp * 8, R, cudaMemcpyDeviceToDevice, st_));
+        k_invert_flags(w.donei, w.active, R, st_);
+        k_fill(w.xi, (long long)R * ld, 0.0, st_);
+        k_residual(ki, w.vin, nullptr, st_);
+        k_cycle_start(ki, w.c0i, 1, 1e-4, st_);
+        for (int t = 0; t < mi; ++t) {
+            bj(w.Vi, (long long)(mi + 1) * ld, (long long)t * ld, w.zi, ld, 0, w.activei, true);
+            schur32(w.zi, w.wi, w.activei);
+            k_deflate_sum(ki, w.wi, nullptr, st_);
+            k_coarse(ki, st_);
+            k_cgs(ki, t, 0, st_);
+            k_cgs(ki, t, 1, st_);
+            k_cgs(ki, t, 2, st_);
+            k_normalize(ki, t, mi, st_);
+        }
+        k_cycle_update(ki, w.Xpi, st_);
+        bj(w.Xpi, ld, 0, w.ti, ld, 0, nullptr, true);
+        schur32(w.ti, w.si, nullptr);
+        k_deflate_coarse_pending(ki, w.si, st_);
+        k_xs_update(ki, w.xi, w.ti, w.c0i, st_);
     };
     // compensated Schur product of x_S (hi part in out, low part in out_lo)
     auto schur_ext = [&](const double* in, double* out, double* out_lo) {
@@ -1297,17 +1391,24 @@ static int solve_impl(Solver& S, const std::vector<int>& ops, const double* f, c
         if (total_it >= S.max_iter) { status = SMPM_ENOCONV; break; }
         const int last_allowed = std::min(m, S.max_iter - total_it);
         int j = 0;
-        const bool mixed = S.precision == 1;
+        const bool mixed = S.precision >= 1;      // flexible: the preconditioned vectors are kept
         const bool use_graphs = S.graphs_ok && !graphs_off;
         // one Arnoldi step j of every active right-hand side
         auto step = [&](int jj) {
-            // z_j = M^-1 v_j (FP32 block-Jacobi in the mixed form: the flexible
-            // variant keeps z_j, so the cycle's correction is exactly sum y_j z_j)
-            bj(w.V, (long long)(m + 1) * ld, (long long)jj * ld, w.z, ld, 0, w.active, mixed);
+            // z_j = M^-1 v_j (FP32 block-Jacobi in the mixed form, the inner
+            // FP32 DBJ-GMRES in the nested form: the flexible variant keeps z_j,
+            // so the cycle's correction is exactly sum y_j z_j)
+            double* zj = w.z;
+            if (nested) {
+                inner_solve(jj);
+                zj = w.xi;
+            } else {
+                bj(w.V, (long long)(m + 1) * ld, (long long)jj * ld, w.z, ld, 0, w.active, mixed);
+            }
             if (mixed)
-                CK(cudaMemcpy2DAsync(w.Zb + (long long)jj * ld, (size_t)m * ld * 8, w.z, (size_t)ld * 8,
+                CK(cudaMemcpy2DAsync(w.Zb + (long long)jj * ld, (size_t)m * ld * 8, zj, (size_t)ld * 8,
                                      (size_t)S.kp * 8, R, cudaMemcpyDeviceToDevice, st_));
-            schur(w.z, ld, 0, w.w, w.active);
+            schur(zj, ld, 0, w.w, w.active);
             k_deflate_sum(ka, w.w, nullptr, st_);
             k_coarse(ka, st_);
             k_cgs(ka, jj, 0, st_);
@@ -1540,7 +1641,8 @@ static Solver* make_solver(const smpm_grid* grid, int nop, const double* k2, voi
     if (!make_geometry(grid->mx, grid->mz, grid->order, grid->lx, grid->lz, grid->z_ratio, grid->tau_scale,
                        grid->deflation_groups, S->g, msg))
         throw Err{SMPM_EINVAL, msg};
-    if (grid->precision != 0 && grid->precision != 1) throw Err{SMPM_EINVAL, "precision must be 0 (FP64) or 1 (mixed)"};
+    if (grid->precision < 0 || grid->precision > 2)
+        throw Err{SMPM_EINVAL, "precision must be 0 (FP64), 1 (FP32 block-Jacobi) or 2 (FP32 inner DBJ-GMRES)"};
     S->nop = nop;
     S->k2.assign(k2, k2 + nop);
     int nzero = 0;
@@ -1551,6 +1653,8 @@ static Solver* make_solver(const smpm_grid* grid, int nop, const double* k2, voi
     if (nzero > 1) throw Err{SMPM_EINVAL, "at most one k2 = 0 operator per handle"};
     S->stream = (cudaStream_t)stream;
     S->precision = grid->precision;
+    if (const char* e = std::getenv("SMPM_INNER_STEPS"))   // inner Arnoldi steps of precision 2
+        S->inner_m = std::min(64, std::max(2, std::atoi(e)));
     setup_solver(*S);
     return S.release();
 }

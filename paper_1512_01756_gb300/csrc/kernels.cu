@@ -166,7 +166,9 @@ void launch_class_gemm(const GemmArgs& a, const Tile* d_tiles, int ntiles, int e
     if (ntiles <= 0) return;
     dim3 grid(ntiles, (a.M + BM - 1) / BM);
     cudaStream_t s = (cudaStream_t)stream;
-    if (a.fp32)
+    if (a.fp32 && epi == 1)
+        class_gemm_kernel<1, float><<<grid, GT, 0, s>>>(a, d_tiles);
+    else if (a.fp32)
         class_gemm_kernel<0, float><<<grid, GT, 0, s>>>(a, d_tiles);
     else if (epi == 1)
         class_gemm_kernel<1, double><<<grid, GT, 0, s>>>(a, d_tiles);
@@ -219,6 +221,10 @@ __global__ void coarse_kernel(KArgs a, int gate) {
     if (!gate_ok(a, r, gate)) return;
     const int i = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
     if (i >= a.d) return;
+    if (!a.K) {                       // no deflation (the outer flexible GMRES of the nested form)
+        if (lane == 0) a.c[(long long)r * a.d + i] = 0.0;
+        return;
+    }
     const double* K = a.K + (long long)a.op[r] * a.K_stride + (long long)i * a.d;
     const double* q = a.q + (long long)r * a.d;
     double s = 0.0;
@@ -768,6 +774,18 @@ __global__ void identity_kernel(double* X, int m) {
 void k_identity(double* X, int m, cudaStream_t s) {
     const long long tot = (long long)m * m;
     identity_kernel<<<(unsigned)((tot + 255) / 256), 256, 0, s>>>(X, m);
+    count_launches(1);
+}
+
+// done[r] = !active[r]: the inner solve of the nested mixed-precision form runs
+// only for the right-hand sides whose outer Arnoldi process is still active.
+__global__ void invert_flags_kernel(int* __restrict__ done, const int* __restrict__ active, int R) {
+    const int r = blockIdx.x * blockDim.x + threadIdx.x;
+    if (r < R) done[r] = active[r] ? 0 : 1;
+}
+
+void k_invert_flags(int* done, const int* active, int R, cudaStream_t s) {
+    invert_flags_kernel<<<(R + 127) / 128, 128, 0, s>>>(done, active, R);
     count_launches(1);
 }
 

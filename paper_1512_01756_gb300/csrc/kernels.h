@@ -32,7 +32,7 @@ struct KArgs {
     double* c;                     // [R][d]        coarse solution K q
     const double* rho;             // op o: rho + o*rho_stride, [cls][side][ng][2 fz]
     long long rho_stride;
-    const double* K;               // op o: K + o*K_stride, [d][d]
+    const double* K;               // op o: K + o*K_stride, [d][d]; null: no deflation (c = 0)
     long long K_stride;
     const int* op;                 // [R] operator set of each rhs
     const int* strip_cls;          // [mx]
@@ -99,6 +99,8 @@ void k_gauge(const GridArgs& g, int R, double* u, long long u_ld, const int* app
 void k_build_strip_op(double* A, const double* Ax, const double* Lz, double k2, int n, int fz,
                       cudaStream_t s);
 void k_identity(double* X, int m, cudaStream_t s);
+// done[r] = active[r] ? 0 : 1 for r < R
+void k_invert_flags(int* done, const int* active, int R, cudaStream_t s);
 // K <- K - (K u) u^T (row-major d x d, w: d scratch): the projected coarse division
 void k_project_coarse(double* K, double* w, const double* u, int d, cudaStream_t s);
 void k_build_W(double* W, const double* Ainv, const double* beta, int n, int fz, cudaStream_t s);

@@ -48,13 +48,14 @@ def _rel(a, b):
     return np.linalg.norm(a - b) / np.linalg.norm(b)
 
 
+@pytest.mark.parametrize("precision", [1, 2])
 @pytest.mark.parametrize("shape,k2", [((8, 2, 8, 4.0, 1.0, 1.0), 0.0), ((7, 3, 6, 2.0, 1.0, 1.2), 0.0),
-                                      ((6, 3, 5, 2.0, 1.0, 1.2), 25.0)])
-def test_mixed_small_matches_direct(smpm, shape, k2):
+                                      ((6, 3, 5, 2.0, 1.0, 1.2), 25.0), ((2, 3, 5, 1.0, 1.0, 1.0), 0.0)])
+def test_mixed_small_matches_direct(smpm, shape, k2, precision):
     g = Grid(*shape[:5], z_ratio=shape[5])
     f = np.random.default_rng(31).uniform(0, 1, g.r)
     u_ref, _ = direct_solve(g, f, None, k2)
-    u, st = _solve(smpm, shape, f, 1, k2)
+    u, st = _solve(smpm, shape, f, precision, k2)
     assert st.rel_resid_true <= 1e-10
     assert _rel(u, u_ref) < 1e-9
 
@@ -82,9 +83,10 @@ def test_mixed_stretched_order16_matches_oracle(smpm):
     f, _ = inputs.cos_modes(X, Z, 2.0, 1.0, inputs.cos_modes_spec(inputs.seed_for(3)))
     u_ref, _ = dbj.solve(g, f, method="dbj", tol=1e-13, coarse="rank1")
     u, st = _solve(smpm, shape, f, 1)
+    u2, st2 = _solve(smpm, shape, f, 2)
     u64, st64 = _solve(smpm, shape, f, 0)
-    assert st.rel_resid_true <= 1e-10 and st64.rel_resid_true <= 1e-10
-    assert _rel(u, u64) < 1e-9
+    assert st.rel_resid_true <= 1e-10 and st64.rel_resid_true <= 1e-10 and st2.rel_resid_true <= 1e-10
+    assert _rel(u, u64) < 1e-9 and _rel(u2, u64) < 1e-9
     assert _rel(u, u_ref) < 1e-7, _rel(u, u_ref)
     L = assemble_L(g).tocsr()
     uL = left_null_sparse(L)
@@ -108,9 +110,10 @@ def test_mixed_full_workload_matches_fp64(smpm):
     f, u_ex = inputs.cos_modes(x, z, 32.0, 1.0, inputs.cos_modes_spec(inputs.seed_for(3)))
     u64, st64 = _solve(smpm, shape, f, 0)
     u32, st32 = _solve(smpm, shape, f, 1)
-    print("fp64", st64.as_dict(), "mixed", st32.as_dict())
-    assert st64.rel_resid_true <= 1e-10 and st32.rel_resid_true <= 1e-10
-    assert _rel(u32, u64) < 1e-9
+    un, stn = _solve(smpm, shape, f, 2)
+    print("fp64", st64.as_dict(), "mixed", st32.as_dict(), "nested", stn.as_dict())
+    assert st64.rel_resid_true <= 1e-10 and st32.rel_resid_true <= 1e-10 and stn.rel_resid_true <= 1e-10
+    assert _rel(u32, u64) < 1e-9 and _rel(un, u64) < 1e-9
     # the analytic solution of the continuous problem, to spectral accuracy
     w = np.ones_like(u_ex)
     ue = u_ex - np.average(u_ex, weights=w)
