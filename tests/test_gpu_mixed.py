@@ -67,9 +67,10 @@ def test_mixed_stretched_order16_matches_oracle(smpm):
     4.8e-9 (and the oracle's rank-1 and least-squares coarse divisions give
     solutions 4.8e-9 apart), so two independently computed null vectors --
     the oracle's sparse inverse iteration on L, the library's Kronecker
-    product of 1-D null vectors -- put the solutions some 1e-8 apart.  The
+    product of 1-D null vectors -- may put the solutions ~1e-8 apart
+    (measured: 1.05e-9 against the oracle with refined strip solves).  The
     checks: mixed against plain FP64 on the GPU (same null vector) at 1e-9;
-    against the oracle at 1e-7, the bound that sensitivity allows; and the
+    against the oracle at 1e-8, the bound that sensitivity allows; and the
     backward error ||L u - b|| / (||L||_1 ||u|| + ||b||) of the GPU solution in
     the oracle's own assembled system, which a 1e-9 error in a generic
     direction would raise to ~1e-10 (the oracle's own solution: ~1e-13)."""
@@ -87,7 +88,7 @@ def test_mixed_stretched_order16_matches_oracle(smpm):
     u64, st64 = _solve(smpm, shape, f, 0)
     assert st.rel_resid_true <= 1e-10 and st64.rel_resid_true <= 1e-10 and st2.rel_resid_true <= 1e-10
     assert _rel(u, u64) < 1e-9 and _rel(u2, u64) < 1e-9
-    assert _rel(u, u_ref) < 1e-7, _rel(u, u_ref)
+    assert _rel(u, u_ref) < 1e-8, _rel(u, u_ref)
     L = assemble_L(g).tocsr()
     uL = left_null_sparse(L)
     b = f - uL * np.dot(uL, f)

@@ -7,8 +7,20 @@
   m_y = 128 -> 65 modes, k_j = j): a separable manufactured solution carried
   by the k = 3 mode is recovered to spectral accuracy, and for the paper's
   U[0,1] right-hand side every mode's GPU solution satisfies the oracle's own
-  assembled (L - k_j^2) system (a property that holds at any size; the oracle's
-  per-mode solves at this size take too long for a test).
+  assembled (L - k_j^2) system (a property that holds at any size), and
+  sampled modes equal the oracle's own DBJ solves at the 1e-9 bar (the GPU
+  solved to 1e-11 there, as a solution at residual 1e-10 is only accurate to
+  kappa * 1e-10 on this long domain).
+
+Mode 0 of U[0,1] data is incompatible (mean ~0.5): Eq. regularize_poisson
+removes its u_L component, which is most of the vector, so the projected data
+moves with u_L, and u_L is fixed by L only to ~eps / (sigma_2 / sigma_1) on a
+32-long domain.  The library's and the oracle's null vectors (both with
+|L^T u_L| ~ 1e-17) put the mode-0 solutions 2.5e-5 apart -- the problem's
+conditioning, not an error of either.  Mode 0 is therefore compared with the
+oracle on the same data made consistent with the oracle's u_L beforehand
+(the library's projection then moves it only to second order), and by
+residual in the oracle's system as given.
 """
 import numpy as np
 import pytest
@@ -110,3 +122,46 @@ def test_full_size_modes_satisfy_oracle_systems(smpm, full3d):
             assert np.linalg.norm(r) / np.linalg.norm(b) < 1e-8, (j, np.linalg.norm(r) / np.linalg.norm(b))
     # the zero mode is returned with zero quadrature mean
     assert abs(np.dot(g.quad_weights(), uh[:, 0].real)) < 1e-10 * np.abs(uh[:, 0].real).max()
+
+
+def test_full_size_sampled_modes_match_oracle(smpm, full3d):
+    from oracle import dbj
+    from oracle.schur import StripSchur
+    shape, s = full3d
+    g = Grid(*shape)
+    my = 128
+    f3 = np.random.default_rng(20151209).uniform(0, 1, (g.r, my))
+    fh = fourier.forward(f3)
+    Fh = torch.from_numpy(_stack(fh)).cuda()
+    Uh = torch.empty_like(Fh)
+    st = s.solve_3d(Fh, Uh, tol=1e-11)
+    torch.cuda.synchronize()
+    assert st.rel_resid_true <= 1e-11
+    uh = _unstack(Uh.cpu().numpy())
+    ks = fourier.wavenumbers(my, 2.0 * np.pi)
+    for j in (1, 64):
+        sch = StripSchur(g, ks[j] ** 2)
+        for part in (np.real, np.imag):
+            b = part(fh[:, j]).copy()
+            if not np.any(b):
+                continue
+            u_ref, _ = dbj.solve(g, b, k2=ks[j] ** 2, method="dbj", tol=1e-13, schur=sch, coarse="rank1")
+            u = part(uh[:, j])
+            rel = np.linalg.norm(u - u_ref) / np.linalg.norm(u_ref)
+            print(f"mode {j} {part.__name__}: rel {rel:.2e}")
+            assert rel < 1e-9, (j, part.__name__, rel)
+    # mode 0 made consistent first (its component along the oracle's u_L
+    # removed, Eq. regularize_poisson), through a 2-D handle of the grid
+    from oracle.schur import left_null_sparse
+    uL = left_null_sparse(assemble_L(g))
+    b0 = fh[:, 0].real.copy()
+    b0 -= uL * np.dot(uL, b0)
+    s2 = smpm.Solver(smpm.make_grid(*shape), 0.0)
+    u0 = np.zeros_like(b0)
+    st0 = s2.solve(b0, u0, tol=1e-11)
+    s2.close()
+    assert st0.rel_resid_true <= 1e-11
+    u_ref, _ = dbj.solve(g, b0, method="dbj", tol=1e-13, coarse="rank1")
+    rel = np.linalg.norm(u0 - u_ref) / np.linalg.norm(u_ref)
+    print(f"mode 0 (consistent): rel {rel:.2e}")
+    assert rel < 1e-9, rel
