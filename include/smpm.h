@@ -165,6 +165,11 @@ int smpm_last_residuals(smpm_handle h, int n, double* out);
  * the handle has no k^2 = 0 operator set. */
 int smpm_null_vectors(smpm_handle h, double* uL, double* uS);
 
+/* Move a handle's device work to another stream (a cudaStream_t or NULL);
+ * waits for the work queued on the old stream first.  Lets a handle built on
+ * one thread's stream be reused from another's. */
+int smpm_set_stream(smpm_handle h, void* stream);
+
 /* Device bytes held by the handle (operators + workspace). */
 long long smpm_device_bytes(smpm_handle h);
 

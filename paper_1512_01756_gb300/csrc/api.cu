@@ -1855,6 +1855,16 @@ int smpm_null_vectors(smpm_handle h, double* uL, double* uS) {
     });
 }
 
+int smpm_set_stream(smpm_handle h, void* stream) {
+    return guarded([&] {
+        if (!h) throw Err{SMPM_EINVAL, "null handle"};
+        Solver& S = *(Solver*)h;
+        if (S.stream) CK(cudaStreamSynchronize(S.stream));
+        S.stream = (cudaStream_t)stream;
+        return SMPM_OK;
+    });
+}
+
 long long smpm_device_bytes(smpm_handle h) { return h ? ((Solver*)h)->bytes : 0; }
 
 void smpm_release(smpm_handle h) {

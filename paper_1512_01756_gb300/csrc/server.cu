@@ -13,8 +13,15 @@
 // footprint (operators + Krylov bases + work vectors) fits the server's byte
 // budget next to the batches in flight.
 //
+// Operator cache: a batch of a single k^2 keeps its handle (operators, Krylov
+// basis, workspace) on the device after the solve, keyed by the grid options
+// and k^2; a later batch with the same key reuses it without setup.  Cached
+// handles are idle (bound to the legacy stream), least recently used first
+// out when their bytes exceed a quarter of the budget.
+//
 // The server is layered on the public entry points (smpm_setup_multi,
-// smpm_solve_multi, smpm_last_residuals); all solver arithmetic is theirs.
+// smpm_solve_multi, smpm_last_residuals, smpm_set_stream); all solver
+// arithmetic is theirs.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -76,10 +83,25 @@ long long footprint(const smpm_grid& g, int nop, int R) {
     return 8 * (nop * op + (long long)R * per_rhs) + (64LL << 20);
 }
 
+struct CacheEntry {
+    Request key;          // grid options, tol unused
+    smpm_handle h = nullptr;
+    long long bytes = 0;
+};
+
+bool same_operator(const Request& a, const Request& b) {
+    Request x = a, y = b;
+    x.tol = y.tol = 0.0;
+    return same_problem(x, y) && a.k2 == b.k2;
+}
+
 struct Server {
     int device = 0;
     int max_batch = 16;
     long long budget = 0, inflight = 0;
+    std::deque<CacheEntry> cache;          // front = most recently used
+    long long cache_bytes = 0;
+    long long cache_hits = 0;
     std::mutex mu;
     std::condition_variable cv;
     std::deque<Request*> pending;
@@ -118,7 +140,7 @@ struct Server {
                         std::sort(ks.begin(), ks.end());
                         const int nop = (int)(std::unique(ks.begin(), ks.end()) - ks.begin());
                         est = footprint(r0->grid, nop, (int)take.size());
-                        if (inflight == 0 || inflight + est <= budget) {   // admission by device footprint
+                        if (inflight == 0 || inflight + cache_bytes + est <= budget) {   // admission by device footprint
                             for (size_t q = take.size(); q-- > 0;) {
                                 batch.insert(batch.begin(), pending[take[q]]);
                                 pending.erase(pending.begin() + (long)take[q]);
@@ -141,7 +163,24 @@ struct Server {
             const int R = (int)batch.size();
             const smpm_grid grid = batch[0]->grid;
             smpm_handle h = nullptr;
-            int rc = smpm_setup_multi(&grid, (int)k2s.size(), k2s.data(), stream, &h);
+            bool hit = false;
+            if (k2s.size() == 1) {
+                std::lock_guard<std::mutex> lk(mu);
+                for (auto it = cache.begin(); it != cache.end(); ++it)
+                    if (same_operator(it->key, *batch[0])) {
+                        h = it->h;
+                        cache_bytes -= it->bytes;
+                        cache.erase(it);
+                        hit = true;
+                        ++cache_hits;
+                        break;
+                    }
+            }
+            int rc = SMPM_OK;
+            if (hit)
+                rc = smpm_set_stream(h, stream);
+            else
+                rc = smpm_setup_multi(&grid, (int)k2s.size(), k2s.data(), stream, &h);
             long long r = 0, nb = 0, kk = 0;
             smpm_stats st{};
             std::vector<double> res(R, 0.0);
@@ -194,8 +233,33 @@ struct Server {
                     }
                 }
             }
-            if (h) smpm_release(h);
             const std::string err = (rc == SMPM_OK || rc == SMPM_ENOCONV) ? std::string() : std::string(smpm_last_error());
+            if (h) {
+                // keep a single-k^2 handle for later batches (idle, on the legacy stream)
+                bool kept = false;
+                if (k2s.size() == 1 && (rc == SMPM_OK || rc == SMPM_ENOCONV) && smpm_set_stream(h, nullptr) == SMPM_OK) {
+                    CacheEntry e;
+                    e.key = *batch[0];
+                    e.h = h;
+                    e.bytes = smpm_device_bytes(h);
+                    std::vector<smpm_handle> evict;
+                    {
+                        std::lock_guard<std::mutex> lk(mu);
+                        if (e.bytes <= budget / 4) {
+                            cache.push_front(e);
+                            cache_bytes += e.bytes;
+                            kept = true;
+                            while (cache_bytes > budget / 4 && !cache.empty()) {
+                                cache_bytes -= cache.back().bytes;
+                                evict.push_back(cache.back().h);
+                                cache.pop_back();
+                            }
+                        }
+                    }
+                    for (smpm_handle x : evict) smpm_release(x);
+                }
+                if (!kept) smpm_release(h);
+            }
             const double t = now_ms();
             {
                 std::lock_guard<std::mutex> lk(mu);
@@ -203,6 +267,7 @@ struct Server {
                 for (int i = 0; i < R; ++i) {
                     Request* q = batch[i];
                     q->st = st;
+                    if (hit) q->st.setup_ms = 0.0;     // operators taken from the cache
                     q->st.status = rc;
                     q->st.rel_resid_true = res[i];
                     q->st.solve_ms = t - q->t_submit;      // latency: completion - submission
@@ -305,6 +370,7 @@ int smpm_server_destroy(smpm_server_t srv) {
     }
     s->cv.notify_all();
     for (auto& t : s->workers) t.join();
+    for (CacheEntry& e : s->cache) smpm_release(e.h);
     delete s;
     return SMPM_OK;
 }

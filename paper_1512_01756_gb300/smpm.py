@@ -18,7 +18,7 @@ SMPM_OK, SMPM_EINVAL, SMPM_ENOMEM, SMPM_ENOCONV, SMPM_EBREAKDOWN, SMPM_ECUDA, SM
 # every entry point include/smpm.h declares
 EXPORTS = ["smpm_setup", "smpm_solve", "smpm_solve_batch", "smpm_setup_multi", "smpm_solve_multi",
            "smpm_setup_3d", "smpm_solve_3d",
-           "smpm_sizes", "smpm_node_coords", "smpm_grid_coords", "smpm_null_vectors", "smpm_device_bytes", "smpm_release", "smpm_probe_fp64",
+           "smpm_sizes", "smpm_node_coords", "smpm_grid_coords", "smpm_null_vectors", "smpm_set_stream", "smpm_device_bytes", "smpm_release", "smpm_probe_fp64",
            "smpm_profile", "smpm_profile_read", "smpm_kernel_launches", "smpm_apply", "smpm_last_residuals", "smpm_apply_deflation_noalloc",
            "smpm_server_create", "smpm_submit", "smpm_poll", "smpm_server_destroy", "smpm_last_error"]
 
@@ -70,6 +70,7 @@ def load():
     lib.smpm_node_coords.argtypes = [H, P, P]
     lib.smpm_grid_coords.argtypes = [ctypes.POINTER(Grid), P, P]
     lib.smpm_null_vectors.argtypes = [H, P, P]
+    lib.smpm_set_stream.argtypes = [H, P]
     lib.smpm_device_bytes.argtypes = [H]
     lib.smpm_device_bytes.restype = ctypes.c_longlong
     lib.smpm_release.argtypes = [H]
@@ -161,6 +162,9 @@ class Solver:
 
     def device_bytes(self):
         return load().smpm_device_bytes(self._h)
+
+    def set_stream(self, stream):
+        _check(load().smpm_set_stream(self._h, _stream_ptr(stream)))
 
     def null_vectors(self):
         """(u_L, u_S) of the k^2 = 0 operator set, as numpy arrays."""

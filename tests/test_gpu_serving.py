@@ -124,3 +124,24 @@ def test_bad_requests(smpm):
         assert time.time() < deadline
         time.sleep(0.001)
     srv.close()
+
+
+def test_operator_cache_reuses_setup(smpm):
+    """A second request with the grid and k^2 of a finished one takes the cached
+    operators (no setup) and gives what a fresh handle gives."""
+    shape, k2 = (6, 2, 8, 3.0, 1.0), 3.7
+    srv = smpm.Server(nworkers=1, max_batch=1)
+    f1, f2 = _rhs(shape, 301), _rhs(shape, 302)
+    u1, u2 = np.zeros_like(f1), np.zeros_like(f2)
+    st1 = _wait(srv, [srv.submit(smpm.make_grid(*shape), k2, f1, u1)])[0]
+    st2 = _wait(srv, [srv.submit(smpm.make_grid(*shape), k2, f2, u2)])[0]
+    # a different k^2 on the same grid does not hit
+    u3 = np.zeros_like(f2)
+    st3 = _wait(srv, [srv.submit(smpm.make_grid(*shape), 4.0, f2, u3)])[0]
+    srv.close()
+    assert st1.setup_ms > 0.0 and st2.setup_ms == 0.0 and st3.setup_ms > 0.0
+    s = smpm.Solver(smpm.make_grid(*shape), k2)
+    u_fresh = np.zeros_like(f2)
+    s.solve(f2, u_fresh, tol=1e-10)
+    s.close()
+    assert st2.rel_resid_true <= 1e-10 and _rel(u2, u_fresh) < 1e-12
