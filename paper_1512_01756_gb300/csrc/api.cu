@@ -27,6 +27,7 @@
 #include <cstring>
 #include <map>
 #include <memory>
+#include <mutex>
 #include <string>
 #include <vector>
 
@@ -55,7 +56,13 @@ struct Err {
             throw Err{SMPM_ECUDA, std::string(#x) + ": cusolver status " + std::to_string((int)s_)}; \
     } while (0)
 
-static constexpr int kBN = 32;      // GEMM column tile (kernels.cu BN)
+// Tile lists of one GEMM site, built for both tile shapes (0: 16 x 32,
+// 1: 8 x 64; columns per tile gemm_tile_columns(shape)).
+struct TileSet {
+    Tile* t[2] = {nullptr, nullptr};
+    int n[2] = {0, 0};
+    size_t cap = 0;
+};
 static constexpr int kChunk = 1024; // vector-kernel chunk
 
 struct Solver {
@@ -111,9 +118,7 @@ struct Solver {
         const double** uLp = nullptr;
         const double** uSp = nullptr;
         const double** oneSp = nullptr;
-        Tile *tM = nullptr, *tG = nullptr, *tW = nullptr, *tA = nullptr, *tS1 = nullptr, *tS2 = nullptr;
-        int ntM = 0, ntG = 0, ntW = 0, ntA = 0, ntS1 = 0, ntS2 = 0;
-        size_t capS1 = 0, capS2 = 0;
+        TileSet tM, tG, tW, tA, tS1, tS2;
         double *fs1 = nullptr, *fs2 = nullptr, *fs3 = nullptr, *k2r = nullptr;
         double* Zb = nullptr;             // FGMRES preconditioned vectors [R][m][ld] (precision 1)
         std::vector<void*> allocs;
@@ -140,6 +145,7 @@ struct Solver {
     cudaStream_t cap_stream = nullptr;
     std::vector<cudaEvent_t>* cap_events = nullptr;   // set while capturing with profiling on
     bool graphs_ok = true;
+    bool capturing = false;                 // a group is being captured (no tuning, no syncs)
     void drop_graphs() {
         for (auto& kv : graphs) {
             if (kv.second.exec) cudaGraphExecDestroy(kv.second.exec);
@@ -208,14 +214,14 @@ static void invert_dense(Solver& S, double* src, double* dst, int m, double* wor
     if (h_info != 0) throw Err{SMPM_EBREAKDOWN, "singular strip or block-Jacobi matrix (getrf info " + std::to_string(h_info) + ")"};
 }
 
-static void run_gemm(Solver& S, GemmArgs a, const Tile* tiles, int ntiles, int epi);
+static void run_gemm(Solver& S, GemmArgs a, const TileSet& ts, int epi);
 
 // Fast strip solve out = A_c(k)^-1 (in - E x_S) on nstrips strips (classes in fa.cls)
 // for R right-hand sides: x-transform by Q^-1, the slot inverses of B_c (+) L_z - k^2
 // (class GEMMs over the size-1 and size-2 slots), x-transform by Q.
 static void fss_run(Solver& S, const FssArgs& fa, int R, const double* in, long long in_ld, double* out,
-                    long long out_ld, const double* xS, long long x_ld, double* t1, double* t2, const Tile* tS1,
-                    int nS1, const Tile* tS2, int nS2, bool accumulate = false) {
+                    long long out_ld, const double* xS, long long x_ld, double* t1, double* t2, const TileSet& tS1,
+                    const TileSet& tS2, bool accumulate = false) {
     const int fz = S.g.fz, n = S.g.n;
     const long long nfz = (long long)n * fz, ld = (long long)fa.nstrips * nfz;
     k_xform(fa, R, S.d_Qinv, in, in_ld, t1, ld, xS, x_ld, S.stream);
@@ -229,7 +235,7 @@ static void fss_run(Solver& S, const FssArgs& fa, int R, const double* in, long 
         a.row_hi = sz == 1 ? S.rh_S1 : S.rh_S2;
         a.in = t1; a.in_rs = ld; a.in_us = nfz; a.in_off = 0;
         a.out = t2; a.out_rs = ld; a.out_us = nfz; a.out_off0 = 0; a.out_off1 = 0; a.msplit = sz * fz;
-        run_gemm(S, a, sz == 1 ? tS1 : tS2, sz == 1 ? nS1 : nS2, 0);
+        run_gemm(S, a, sz == 1 ? tS1 : tS2, 0);
     }
     k_xform(fa, R, S.d_Q, t2, ld, out, out_ld, nullptr, 0, S.stream, accumulate ? out : nullptr, out_ld);
 }
@@ -241,21 +247,21 @@ static void fss_run(Solver& S, const FssArgs& fa, int R, const double* in, long 
 // ~1e-10 only; the refined result matches a dense LU solve (~1e-13).
 static void fss_refined(Solver& S, const FssArgs& fa, int R, const double* in, long long in_ld, double* out,
                         long long out_ld, const double* xS, long long x_ld, const double* k2r, double* t1, double* t2,
-                        double* t3, const Tile* tS1, int nS1, const Tile* tS2, int nS2) {
+                        double* t3, const TileSet& tS1, const TileSet& tS2) {
     const long long ld = (long long)fa.nstrips * S.g.n * S.g.fz;
-    fss_run(S, fa, R, in, in_ld, out, out_ld, xS, x_ld, t1, t2, tS1, nS1, tS2, nS2);
+    fss_run(S, fa, R, in, in_ld, out, out_ld, xS, x_ld, t1, t2, tS1, tS2);
     k_strip_residual(fa, R, S.d_Ax3, S.d_Lz, S.d_zlo, S.d_zhi, k2r, in, in_ld, xS, x_ld, out, out_ld, t3, ld, S.stream);
-    fss_run(S, fa, R, t3, ld, out, out_ld, nullptr, 0, t1, t2, tS1, nS1, tS2, nS2, true);
+    fss_run(S, fa, R, t3, ld, out, out_ld, nullptr, 0, t1, t2, tS1, tS2, true);
 }
 
 // Slot tiles of one class on a single strip for R right-hand sides of operator o.
-static std::vector<Tile> single_strip_slot_tiles(const Solver& S, int o, int c, int R, int sz) {
+static std::vector<Tile> single_strip_slot_tiles(const Solver& S, int o, int c, int R, int sz, int bn) {
     std::vector<Tile> out;
     const int ns = std::max(sz == 1 ? S.ns1 : S.ns2, 1);
     for (size_t t = 0; t < S.sl_size[c].size(); ++t) {
         if (S.sl_size[c][t] != sz) continue;
-        for (int rr = 0; rr < R; rr += kBN)
-            out.push_back(Tile{(o * 3 + S.slot_cls[c]) * ns + S.sl_idx[c][t], 0, 1, rr, std::min(kBN, R - rr),
+        for (int rr = 0; rr < R; rr += bn)
+            out.push_back(Tile{(o * 3 + S.slot_cls[c]) * ns + S.sl_idx[c][t], 0, 1, rr, std::min(bn, R - rr),
                                (long long)S.sl_start[c][t] * S.g.fz});
     }
     return out;
@@ -265,17 +271,22 @@ static std::vector<Tile> single_strip_slot_tiles(const Solver& S, int o, int c, 
 static void fss_single(Solver& S, int o, int c, int R, const double* in, double* out, double* t1, double* t2,
                        std::vector<void*>& tmp) {
     FssArgs fa{S.g.n, S.g.fz, 1, S.d_cls3 + c};
-    auto t1v = single_strip_slot_tiles(S, o, c, R, 1);
-    auto t2v = single_strip_slot_tiles(S, o, c, R, 2);
-    Tile* d1 = S.dalloc<Tile>(std::max<size_t>(t1v.size(), 1), tmp);
-    Tile* d2 = S.dalloc<Tile>(std::max<size_t>(t2v.size(), 1), tmp);
-    if (!t1v.empty()) CK(cudaMemcpyAsync(d1, t1v.data(), t1v.size() * sizeof(Tile), cudaMemcpyHostToDevice, S.stream));
-    if (!t2v.empty()) CK(cudaMemcpyAsync(d2, t2v.data(), t2v.size() * sizeof(Tile), cudaMemcpyHostToDevice, S.stream));
+    TileSet ts[2];
+    std::vector<Tile> tv[2][2];
+    for (int sz = 1; sz <= 2; ++sz)
+        for (int sh = 0; sh < 2; ++sh) {
+            tv[sz - 1][sh] = single_strip_slot_tiles(S, o, c, R, sz, gemm_tile_columns(sh));
+            const auto& v = tv[sz - 1][sh];
+            ts[sz - 1].t[sh] = S.dalloc<Tile>(std::max<size_t>(v.size(), 1), tmp);
+            ts[sz - 1].n[sh] = (int)v.size();
+            if (!v.empty())
+                CK(cudaMemcpyAsync(ts[sz - 1].t[sh], v.data(), v.size() * sizeof(Tile), cudaMemcpyHostToDevice, S.stream));
+        }
     const long long nfz = (long long)S.g.n * S.g.fz;
     double* k2r = S.dalloc<double>((size_t)R, tmp);
     k_fill(k2r, R, S.k2[o], S.stream);
     double* t3 = S.dalloc<double>((size_t)R * nfz, tmp);
-    fss_refined(S, fa, R, in, nfz, out, nfz, nullptr, 0, k2r, t1, t2, t3, d1, (int)t1v.size(), d2, (int)t2v.size());
+    fss_refined(S, fa, R, in, nfz, out, nfz, nullptr, 0, k2r, t1, t2, t3, ts[0], ts[1]);
     CK(cudaStreamSynchronize(S.stream));
 }
 
@@ -828,8 +839,7 @@ static void ensure_workspace(Solver& S, int R) {
     S.drop_graphs();
     S.bytes -= S.wk_bytes;
     S.free_list(S.wk.allocs);
-    S.wk.tS1 = S.wk.tS2 = nullptr;
-    S.wk.capS1 = S.wk.capS2 = 0;
+    S.wk.tG = S.wk.tW = S.wk.tA = S.wk.tM = S.wk.tS1 = S.wk.tS2 = TileSet();
     const long long bytes_before = S.bytes;
     auto& w = S.wk;
     auto& L = w.allocs;
@@ -912,19 +922,14 @@ static void ensure_workspace(Solver& S, int R) {
     w.uSp = (const double**)S.dalloc<double*>(R, L);
     w.oneSp = (const double**)S.dalloc<double*>(R, L);
     // tile lists sized for the worst case (every rhs its own op): units * R
-    const size_t tcap_strip = (size_t)(g.mx + 2) * R + 8;
-    const size_t tcap_pair = (size_t)(S.P + 2) * R + 8;
-    w.tG = S.dalloc<Tile>(tcap_strip, L);
-    w.tW = S.dalloc<Tile>(tcap_strip, L);
-    w.tA = S.dalloc<Tile>(tcap_strip, L);
-    w.tM = S.dalloc<Tile>(tcap_pair, L);
+    w.tG = w.tW = w.tA = w.tM = w.tS1 = w.tS2 = TileSet();   // built by prepare_ops
     CK(cudaStreamSynchronize(S.stream));
     S.wk_bytes = S.bytes - bytes_before;
     S.Rcap = R;
     S.cur_ops.clear();
 }
 
-static std::vector<Tile> make_tiles(const std::vector<int>& unit_cls, int ncls, const std::vector<int>& ops) {
+static std::vector<Tile> make_tiles(const std::vector<int>& unit_cls, int ncls, const std::vector<int>& ops, int bn) {
     std::vector<Tile> out;
     const int R = (int)ops.size(), nu = (int)unit_cls.size();
     int rb = 0;
@@ -936,8 +941,8 @@ static std::vector<Tile> make_tiles(const std::vector<int>& unit_cls, int ncls, 
             int ue = ub;
             while (ue < nu && unit_cls[ue] == unit_cls[ub]) ++ue;
             for (int rr = rb; rr < re;) {
-                const int nr = std::min(kBN, re - rr);
-                const int upt = std::max(1, kBN / nr);
+                const int nr = std::min(bn, re - rr);
+                const int upt = std::max(1, bn / nr);
                 for (int u = ub; u < ue; u += upt)
                     out.push_back(Tile{ops[rb] * ncls + unit_cls[ub], u, std::min(upt, ue - u), rr, nr});
                 rr += nr;
@@ -949,7 +954,7 @@ static std::vector<Tile> make_tiles(const std::vector<int>& unit_cls, int ncls, 
     return out;
 }
 
-static std::vector<Tile> make_slot_tiles(const Solver& S, const std::vector<int>& ops, int sz) {
+static std::vector<Tile> make_slot_tiles(const Solver& S, const std::vector<int>& ops, int sz, int bn) {
     std::vector<Tile> out;
     const int R = (int)ops.size(), nu = (int)S.strip_cls.size();
     const int ns = std::max(sz == 1 ? S.ns1 : S.ns2, 1);
@@ -967,8 +972,8 @@ static std::vector<Tile> make_slot_tiles(const Solver& S, const std::vector<int>
                 const int mat = (ops[rb] * 3 + S.slot_cls[c]) * ns + S.sl_idx[c][t];
                 const long long off = (long long)S.sl_start[c][t] * S.g.fz;
                 for (int rr = rb; rr < re;) {
-                    const int nr = std::min(kBN, re - rr);
-                    const int upt = std::max(1, kBN / nr);
+                    const int nr = std::min(bn, re - rr);
+                    const int upt = std::max(1, bn / nr);
                     for (int u = ub; u < ue; u += upt) out.push_back(Tile{mat, u, std::min(upt, ue - u), rr, nr, off});
                     rr += nr;
                 }
@@ -980,34 +985,44 @@ static std::vector<Tile> make_slot_tiles(const Solver& S, const std::vector<int>
     return out;
 }
 
+// Upload a tile list of shape sh into ts (grown in the workspace as needed; a
+// replaced list stays allocated until the workspace is freed).  The host
+// vector must live until the stream has consumed the copy.
+static void upload_tiles(Solver& S, TileSet& ts, int sh, const std::vector<Tile>& v) {
+    if (v.size() > ts.cap || ts.t[sh] == nullptr) {
+        const size_t cap = std::max<size_t>(v.size(), 1) * 2;
+        for (int k = 0; k < 2; ++k) {   // both shapes share one capacity (shape 1 never has more tiles)
+            Tile* fresh = S.dalloc<Tile>(cap, S.wk.allocs);
+            if (ts.t[k] && k != sh && ts.n[k] > 0)
+                CK(cudaMemcpyAsync(fresh, ts.t[k], ts.n[k] * sizeof(Tile), cudaMemcpyDeviceToDevice, S.stream));
+            ts.t[k] = fresh;
+        }
+        ts.cap = cap;
+    }
+    if (!v.empty()) CK(cudaMemcpyAsync(ts.t[sh], v.data(), v.size() * sizeof(Tile), cudaMemcpyHostToDevice, S.stream));
+    ts.n[sh] = (int)v.size();
+}
+
 static void prepare_ops(Solver& S, const std::vector<int>& ops) {
     if (ops == S.cur_ops) return;
     S.drop_graphs();
     auto& w = S.wk;
-    if (S.fss) {
-        for (int sz = 1; sz <= 2; ++sz) {
-            auto tv = make_slot_tiles(S, ops, sz);
-            Tile*& dt = sz == 1 ? w.tS1 : w.tS2;
-            int& nt = sz == 1 ? w.ntS1 : w.ntS2;
-            size_t& cap = sz == 1 ? w.capS1 : w.capS2;
-            if (tv.size() > cap || dt == nullptr) {   // grow (the old list stays in the workspace until it is freed)
-                cap = std::max<size_t>(tv.size(), 1) * 2;
-                dt = S.dalloc<Tile>(cap, w.allocs);
+    std::vector<std::vector<Tile>> keep;   // host lists alive until the sync below
+    for (int sh = 0; sh < 2; ++sh) {
+        const int bn = gemm_tile_columns(sh);
+        if (S.fss)
+            for (int sz = 1; sz <= 2; ++sz) {
+                keep.push_back(make_slot_tiles(S, ops, sz, bn));
+                upload_tiles(S, sz == 1 ? w.tS1 : w.tS2, sh, keep.back());
             }
-            if (!tv.empty())
-                CK(cudaMemcpyAsync(dt, tv.data(), tv.size() * sizeof(Tile), cudaMemcpyHostToDevice, S.stream));
-            nt = (int)tv.size();
-        }
+        keep.push_back(make_tiles(S.strip_cls, 3, ops, bn));
+        upload_tiles(S, w.tG, sh, keep.back());
+        upload_tiles(S, w.tW, sh, keep.back());
+        upload_tiles(S, w.tA, sh, keep.back());
+        keep.push_back(make_tiles(S.pair_mc, S.nmc, ops, bn));
+        upload_tiles(S, w.tM, sh, keep.back());
     }
     const int R = (int)ops.size();
-    auto tS = make_tiles(S.strip_cls, 3, ops);
-    auto tM = make_tiles(S.pair_mc, S.nmc, ops);
-    CK(cudaMemcpyAsync(w.tG, tS.data(), tS.size() * sizeof(Tile), cudaMemcpyHostToDevice, S.stream));
-    CK(cudaMemcpyAsync(w.tW, tS.data(), tS.size() * sizeof(Tile), cudaMemcpyHostToDevice, S.stream));
-    CK(cudaMemcpyAsync(w.tA, tS.data(), tS.size() * sizeof(Tile), cudaMemcpyHostToDevice, S.stream));
-    CK(cudaMemcpyAsync(w.tM, tM.data(), tM.size() * sizeof(Tile), cudaMemcpyHostToDevice, S.stream));
-    w.ntG = w.ntW = w.ntA = (int)tS.size();
-    w.ntM = (int)tM.size();
     std::vector<const double*> uLp(R, nullptr), uSp(R, nullptr), oneSp(R, nullptr);
     std::vector<int> gauge(R, 0);
     for (int r = 0; r < R; ++r)
@@ -1056,7 +1071,60 @@ static GemmArgs gemm_base(const Solver& S) {
 
 static constexpr int kEventPairs = 8192;
 
-static void run_gemm(Solver& S, GemmArgs a, const Tile* tiles, int ntiles, int epi) {
+// Tile-shape autotuner.  The first time a GEMM of a given kind (epilogue,
+// precision, M, K, size class of the column count) runs outside a graph
+// capture and outside profiling, both tile shapes are launched twice each on
+// the real operands (every launch writes the complete output, so the result
+// stands), timed with CUDA events, and the faster shape is kept for that key
+// for the rest of the process (all handles, all threads).
+static std::mutex g_tune_mu;
+static std::map<std::array<int, 6>, int> g_tune;
+
+static int tune_shape(Solver& S, GemmArgs& a, const TileSet& ts, int epi, bool& launched) {
+    launched = false;
+    if (ts.n[1] <= 0 || epi == 3) return 0;
+    int dev = 0;
+    cudaGetDevice(&dev);
+    int bucket = 0;
+    while ((1 << (bucket + 1)) <= ts.n[0]) ++bucket;
+    const std::array<int, 6> key{dev, epi, a.fp32, a.M, a.K, bucket};
+    {
+        std::lock_guard<std::mutex> lk(g_tune_mu);
+        auto it = g_tune.find(key);
+        if (it != g_tune.end()) return it->second;
+    }
+    if (S.capturing || S.prof) return 0;
+    cudaEvent_t e[5];
+    for (auto& x : e) CK(cudaEventCreate(&x));
+    CK(cudaEventRecord(e[0], S.stream));
+    for (int rep = 0; rep < 2; ++rep)
+        for (int sh = 0; sh < 2; ++sh) {
+            a.shape = sh;
+            launch_class_gemm(a, ts.t[sh], ts.n[sh], epi, S.stream);
+            CK(cudaEventRecord(e[1 + rep * 2 + sh], S.stream));
+        }
+    CK(cudaEventSynchronize(e[4]));
+    float t[4];
+    CK(cudaEventElapsedTime(&t[0], e[0], e[1]));
+    for (int k = 1; k < 4; ++k) CK(cudaEventElapsedTime(&t[k], e[k], e[k + 1]));
+    for (auto& x : e) cudaEventDestroy(x);
+    const int best = std::min(t[1], t[3]) < std::min(t[0], t[2]) ? 1 : 0;
+    {
+        std::lock_guard<std::mutex> lk(g_tune_mu);
+        g_tune.emplace(key, best);
+    }
+    launched = true;
+    return best;
+}
+
+static void run_gemm(Solver& S, GemmArgs a, const TileSet& ts, int epi) {
+    bool launched = false;
+    const int sh = std::getenv("SMPM_TILE_SHAPE") ? std::atoi(std::getenv("SMPM_TILE_SHAPE")) & 1
+                                                  : tune_shape(S, a, ts, epi, launched);
+    if (launched) return;                // the tuning launches computed the output
+    a.shape = sh;
+    const Tile* tiles = ts.t[sh];
+    const int ntiles = ts.n[sh];
     if (S.prof && S.cap_events) {   // inside a graph capture: the graph owns its events
         a.flops = S.d_flops;
         cudaEvent_t e0, e1;
@@ -1137,8 +1205,7 @@ static int solve_impl(Solver& S, const std::vector<int>& ops, const double* f, c
     k_project(R, g.r, w.b, g.r, w.uLp, w.rpart, rch, kChunk, st_);
     const FssArgs fa{n, fz, g.mx, S.d_strip_cls};
     if (S.fss) {  // b_S = B (A^-1 b): fast strip solves, then the face fluxes
-        fss_refined(S, fa, R, w.b, g.r, w.t2, g.r, nullptr, 0, w.k2r, w.fs1, w.fs2, w.fs3, w.tS1, w.ntS1, w.tS2,
-                    w.ntS2);
+        fss_refined(S, fa, R, w.b, g.r, w.t2, g.r, nullptr, 0, w.k2r, w.fs1, w.fs2, w.fs3, w.tS1, w.tS2);
         k_face_flux(fa, R, S.d_beta, w.t2, g.r, w.bS, ld, S.kp, st_);
     } else {
         GemmArgs aW = gemm_base(S);
@@ -1146,7 +1213,7 @@ static int solve_impl(Solver& S, const std::vector<int>& ops, const double* f, c
         aW.row_lo = S.rl_GW; aW.row_hi = S.rh_GW;
         aW.in = w.b; aW.in_rs = g.r; aW.in_us = nfz; aW.in_off = 0;
         aW.out = w.bS; aW.out_rs = ld; aW.out_us = f2; aW.out_off0 = -fz; aW.out_off1 = f2; aW.msplit = fz;
-        run_gemm(S, aW, w.tW, w.ntW, 0);
+        run_gemm(S, aW, w.tW, 0);
     }
     // SMPM_TRACE_SOLVE=1: per-cycle true residual and iterate norms on stderr
     const bool trace = std::getenv("SMPM_TRACE_SOLVE") != nullptr;
@@ -1215,7 +1282,7 @@ static int solve_impl(Solver& S, const std::vector<int>& ops, const double* f, c
         a.in = in; a.in_rs = in_rs; a.in_us = f4; a.in_off = in_off + fz;
         a.out = out; a.out_rs = out_rs; a.out_us = f4; a.out_off0 = out_off + fz; a.out_off1 = 0; a.msplit = f4;
         a.active = active;
-        run_gemm(S, a, w.tM, w.ntM, 0);
+        run_gemm(S, a, w.tM, 0);
     };
     // Schur product: out = in + sum_i scatter_i G_i gather_i in
     auto schur = [&](const double* in, long long in_rs, long long in_off, double* out, const int* active) {
@@ -1226,7 +1293,7 @@ static int solve_impl(Solver& S, const std::vector<int>& ops, const double* f, c
         a.out = out; a.out_rs = ld; a.out_us = f2; a.out_off0 = -fz; a.out_off1 = f2; a.msplit = fz;
         a.add = in;  // identity term, same layout when in_rs == ld and in_off == 0
         a.active = active;
-        run_gemm(S, a, w.tG, w.ntG, 1);
+        run_gemm(S, a, w.tG, 1);
     };
     // FP32 Schur product of the inner solve (FP32 blocks and accumulation)
     auto schur32 = [&](const double* in, double* out, const int* active) {
@@ -1238,7 +1305,7 @@ static int solve_impl(Solver& S, const std::vector<int>& ops, const double* f, c
         a.out = out; a.out_rs = ld; a.out_us = f2; a.out_off0 = -fz; a.out_off1 = f2; a.msplit = fz;
         a.add = in;
         a.active = active;
-        run_gemm(S, a, w.tG, w.ntG, 1);
+        run_gemm(S, a, w.tG, 1);
     };
     // z = inner solve of S z = V_j for the active right-hand sides (one
     // deflated right-preconditioned GMRES cycle from z = 0, Alg. seq steps
@@ -1276,7 +1343,7 @@ static int solve_impl(Solver& S, const std::vector<int>& ops, const double* f, c
         a.out = out; a.out_rs = ld; a.out_us = f2; a.out_off0 = -fz; a.out_off1 = f2; a.msplit = fz;
         a.add = in;
         a.out_lo = out_lo;
-        run_gemm(S, a, w.tG, w.ntG, 3);
+        run_gemm(S, a, w.tG, 3);
     };
 
     CK(cudaMemsetAsync(w.done, 0, R * sizeof(int), st_));
@@ -1435,6 +1502,7 @@ static int solve_impl(Solver& S, const std::vector<int>& ops, const double* f, c
                     cudaGraph_t graph = nullptr;
                     cudaError_t e1 = cudaStreamBeginCapture(S.cap_stream, cudaStreamCaptureModeThreadLocal);
                     if (e1 == cudaSuccess) {
+                        S.capturing = true;
                         try {
                             for (int jj = j; jj < j + cnt; ++jj) step(jj);
                         } catch (...) {
@@ -1442,8 +1510,10 @@ static int solve_impl(Solver& S, const std::vector<int>& ops, const double* f, c
                             if (graph) cudaGraphDestroy(graph);
                             S.stream = st_ = keep;
                             S.cap_events = nullptr;
+                            S.capturing = false;
                             throw;
                         }
+                        S.capturing = false;
                         e1 = cudaStreamEndCapture(S.cap_stream, &graph);
                     }
                     S.stream = st_ = keep;
@@ -1508,7 +1578,7 @@ static int solve_impl(Solver& S, const std::vector<int>& ops, const double* f, c
     }
     // recovery: u = A^-1 (b - E x_S)  (Alg. seq step 9)
     if (S.fss) {
-        fss_refined(S, fa, R, w.b, g.r, u_d, g.r, w.xS, ld, w.k2r, w.fs1, w.fs2, w.fs3, w.tS1, w.ntS1, w.tS2, w.ntS2);
+        fss_refined(S, fa, R, w.b, g.r, u_d, g.r, w.xS, ld, w.k2r, w.fs1, w.fs2, w.fs3, w.tS1, w.tS2);
     } else {
         k_recovery_rhs(ga, R, w.b, g.r, w.xS, ld, w.t2, st_);
         GemmArgs a = gemm_base(S);
@@ -1516,7 +1586,7 @@ static int solve_impl(Solver& S, const std::vector<int>& ops, const double* f, c
         a.row_lo = S.rl_A; a.row_hi = S.rh_A;
         a.in = w.t2; a.in_rs = g.r; a.in_us = nfz; a.in_off = 0;
         a.out = u_d; a.out_rs = g.r; a.out_us = nfz; a.out_off0 = 0; a.out_off1 = 0; a.msplit = nfz;
-        run_gemm(S, a, w.tA, w.ntA, 0);
+        run_gemm(S, a, w.tA, 0);
     }
     k_gauge(ga, R, u_d, g.r, w.gauge, w.rpart, rch, kChunk, st_);
     if (!u_dev) CK(cudaMemcpyAsync(u, u_d, sizeof(double) * g.r * R, cudaMemcpyDeviceToHost, st_));
@@ -1580,12 +1650,12 @@ static int apply_impl(Solver& S, int kind, int R, const double* in, double* out)
         a.mats = S.G; a.mat_stride = S.sG; a.M = f2; a.K = f2; a.row_lo = S.rl_GW; a.row_hi = S.rh_GW;
         a.in = w.z; a.in_rs = ld; a.in_us = f2; a.in_off = 0;
         a.out = w.w; a.out_rs = ld; a.out_us = f2; a.out_off0 = -fz; a.out_off1 = f2; a.msplit = fz; a.add = w.z;
-        run_gemm(S, a, w.tG, w.ntG, 1);
+        run_gemm(S, a, w.tG, 1);
     } else if (kind == 1) {
         a.mats = S.Minv; a.mat_stride = S.sM; a.M = f4; a.K = f4; a.row_lo = S.rl_M; a.row_hi = S.rh_M;
         a.in = w.z; a.in_rs = ld; a.in_us = f4; a.in_off = fz;
         a.out = w.w; a.out_rs = ld; a.out_us = f4; a.out_off0 = fz; a.msplit = f4;
-        run_gemm(S, a, w.tM, w.ntM, 0);
+        run_gemm(S, a, w.tM, 0);
     } else if (kind == 2) {
         KArgs ka;
         std::memset(&ka, 0, sizeof(ka));
@@ -1604,22 +1674,22 @@ static int apply_impl(Solver& S, int kind, int R, const double* in, double* out)
         k_cgs(ka, -1, 0, st_);  // w -= S Z c, no dot products
     } else if (kind == 3 && S.fss) {
         const FssArgs fa{g.n, fz, g.mx, S.d_strip_cls};
-        fss_refined(S, fa, R, w.t2, r, w.b, r, nullptr, 0, w.k2r, w.fs1, w.fs2, w.fs3, w.tS1, w.ntS1, w.tS2, w.ntS2);
+        fss_refined(S, fa, R, w.t2, r, w.b, r, nullptr, 0, w.k2r, w.fs1, w.fs2, w.fs3, w.tS1, w.tS2);
         k_face_flux(fa, R, S.d_beta, w.b, r, w.w, ld, S.kp, st_);
     } else if (kind == 4 && S.fss) {
         const FssArgs fa{g.n, fz, g.mx, S.d_strip_cls};
-        fss_refined(S, fa, R, w.t2, r, w.b, r, nullptr, 0, w.k2r, w.fs1, w.fs2, w.fs3, w.tS1, w.ntS1, w.tS2, w.ntS2);
+        fss_refined(S, fa, R, w.t2, r, w.b, r, nullptr, 0, w.k2r, w.fs1, w.fs2, w.fs3, w.tS1, w.tS2);
         res = w.b;
     } else if (kind == 3) {
         a.mats = S.W; a.mat_stride = S.sW; a.M = f2; a.K = nfz; a.row_lo = S.rl_GW; a.row_hi = S.rh_GW;
         a.in = w.t2; a.in_rs = r; a.in_us = nfz; a.in_off = 0;
         a.out = w.w; a.out_rs = ld; a.out_us = f2; a.out_off0 = -fz; a.out_off1 = f2; a.msplit = fz;
-        run_gemm(S, a, w.tW, w.ntW, 0);
+        run_gemm(S, a, w.tW, 0);
     } else {
         a.mats = S.Ainv; a.mat_stride = S.sA; a.M = nfz; a.K = nfz; a.row_lo = S.rl_A; a.row_hi = S.rh_A;
         a.in = w.t2; a.in_rs = r; a.in_us = nfz; a.in_off = 0;
         a.out = w.b; a.out_rs = r; a.out_us = nfz; a.msplit = nfz;
-        run_gemm(S, a, w.tA, w.ntA, 0);
+        run_gemm(S, a, w.tA, 0);
         res = w.b;
     }
     if (face_out)

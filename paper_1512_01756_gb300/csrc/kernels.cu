@@ -46,20 +46,24 @@ __device__ __forceinline__ double block_sum(double v, double* sh) {
 
 // ---------------------------------------------------------------------------
 // Class GEMM: out[:, col] = Mat_{tile} * in[:, col] (+ add) over tiles of columns
-// sharing one class matrix.  A CTA owns a 16-row x 32-column output tile; each
-// of its 128 threads one row and four columns.  The short row tile keeps the
-// padding waste of M = 2 f_z, 4 f_z, n f_z small, and the many small tiles
-// spread the FP64 work evenly over the SMs.
+// sharing one class matrix.  A CTA of 128 threads owns a BMT-row x BNT-column
+// output tile, each thread one row and four columns: 16 x 32 (the default) or
+// 8 x 64 (less row padding for small M such as the f_z-row slot matrices).
+// The short row tiles keep the padding waste of M = f_z, 2 f_z, 4 f_z small,
+// and the many small tiles spread the FP64 work evenly over the SMs.  K runs
+// in 16-wide slabs; the last slab stops at K (no FMAs on padding).
 // ---------------------------------------------------------------------------
 // TM: element type of the class matrices and of the arithmetic (double, or
 // float for the FP32 block-Jacobi of the mixed-precision solve: FP64 vectors are
 // rounded to FP32 on load, products accumulate in FP32, results are stored in FP64).
-template <int EPI, typename TM>
+template <int EPI, typename TM, int BMT = BM>
 __global__ void __launch_bounds__(GT) class_gemm_kernel(GemmArgs a, const Tile* __restrict__ tiles) {
+    constexpr int BNT = 4 * GT / BMT;          // columns per tile (4 per thread)
+    constexpr int CG = GT / BMT;               // column groups of four
     const Tile t = tiles[blockIdx.x];
-    const int row0 = blockIdx.y * BM;
+    const int row0 = blockIdx.y * BMT;
     const int lo = a.row_lo[t.mat], hi = a.row_hi[t.mat];
-    if (row0 >= hi || row0 + BM <= lo) return;
+    if (row0 >= hi || row0 + BMT <= lo) return;
     if (a.active) {
         int any = 0;
         for (int c = 0; c < t.nr; ++c) any |= a.active[t.r0 + c];
@@ -69,21 +73,21 @@ __global__ void __launch_bounds__(GT) class_gemm_kernel(GemmArgs a, const Tile* 
     if (a.flops && threadIdx.x == 0) {
         int cols = 0;
         for (int c = 0; c < ncol; ++c) cols += (a.active == nullptr || a.active[t.r0 + c % t.nr]) ? 1 : 0;
-        const int r_lo = max(lo, row0), r_hi = min(min(hi, row0 + BM), a.M);
+        const int r_lo = max(lo, row0), r_hi = min(min(hi, row0 + BMT), a.M);
         atomicAdd(a.flops, 2ULL * (unsigned long long)max(0, r_hi - r_lo) * (unsigned long long)a.K *
                                (unsigned long long)cols);
     }
-    __shared__ TM As[BK][BM + 1];
-    __shared__ __align__(16) TM Bs[BK][BN + 4];
+    __shared__ TM As[BK][BMT + 1];
+    __shared__ __align__(16) TM Bs[BK][BNT + 4];
     const TM* __restrict__ A = reinterpret_cast<const TM*>(a.mats) + (long long)t.mat * a.mat_stride;
     const int tid = threadIdx.x;
-    const int tr = tid >> 3, tc = tid & 7;     // row 0..15, column group 0..7
+    const int tr = tid / CG, tc = tid % CG;    // row 0..BMT-1, column group 0..CG-1
     TM acc[4] = {TM(0), TM(0), TM(0), TM(0)};
     double acc_lo[4] = {0.0, 0.0, 0.0, 0.0};   // EPI 3: running error of acc
 
-    const double* colp[(BN * BK) / GT];
+    const double* colp[(BNT * BK) / GT];
 #pragma unroll
-    for (int l = 0; l < (BN * BK) / GT; ++l) {
+    for (int l = 0; l < (BNT * BK) / GT; ++l) {
         const int e = tid + l * GT, c = e >> 4;
         colp[l] = nullptr;
         if (c < ncol) {
@@ -92,14 +96,13 @@ __global__ void __launch_bounds__(GT) class_gemm_kernel(GemmArgs a, const Tile* 
         }
     }
     for (int k0 = 0; k0 < a.K; k0 += BK) {
-#pragma unroll
-        for (int l = 0; l < (BM * BK) / GT; ++l) {
-            const int e = tid + l * GT, i = e >> 4, kk = e & 15;
+        for (int e = tid; e < BMT * BK; e += GT) {
+            const int i = e >> 4, kk = e & 15;
             const int row = row0 + i, k = k0 + kk;
             As[kk][i] = (row < a.M && k < a.K) ? A[(long long)row * a.K + k] : TM(0);
         }
 #pragma unroll
-        for (int l = 0; l < (BN * BK) / GT; ++l) {
+        for (int l = 0; l < (BNT * BK) / GT; ++l) {
             const int e = tid + l * GT, c = e >> 4, kk = e & 15;
             const int k = k0 + kk;
             Bs[kk][c] = (colp[l] != nullptr && k < a.K) ? TM(colp[l][k]) : TM(0);
@@ -127,9 +130,16 @@ __global__ void __launch_bounds__(GT) class_gemm_kernel(GemmArgs a, const Tile* 
                     acc_lo[j] += pe + se;
                 }
             }
-        } else {
+        } else if (k0 + BK <= a.K) {
 #pragma unroll
             for (int kk = 0; kk < BK; ++kk) {
+                const TM av = As[kk][tr];
+#pragma unroll
+                for (int j = 0; j < 4; ++j) acc[j] = fma(av, Bs[kk][tc * 4 + j], acc[j]);
+            }
+        } else {   // last, partial slab
+            const int kn = a.K - k0;
+            for (int kk = 0; kk < kn; ++kk) {
                 const TM av = As[kk][tr];
 #pragma unroll
                 for (int j = 0; j < 4; ++j) acc[j] = fma(av, Bs[kk][tc * 4 + j], acc[j]);
@@ -162,20 +172,30 @@ __global__ void __launch_bounds__(GT) class_gemm_kernel(GemmArgs a, const Tile* 
     }
 }
 
+template <int BMT>
+static void launch_shape(const GemmArgs& a, const Tile* d_tiles, int ntiles, int epi, cudaStream_t s) {
+    dim3 grid(ntiles, (a.M + BMT - 1) / BMT);
+    if (a.fp32 && epi == 1)
+        class_gemm_kernel<1, float, BMT><<<grid, GT, 0, s>>>(a, d_tiles);
+    else if (a.fp32)
+        class_gemm_kernel<0, float, BMT><<<grid, GT, 0, s>>>(a, d_tiles);
+    else if (epi == 1)
+        class_gemm_kernel<1, double, BMT><<<grid, GT, 0, s>>>(a, d_tiles);
+    else if (epi == 3)
+        class_gemm_kernel<3, double, BMT><<<grid, GT, 0, s>>>(a, d_tiles);
+    else
+        class_gemm_kernel<0, double, BMT><<<grid, GT, 0, s>>>(a, d_tiles);
+}
+
+int gemm_tile_columns(int shape) { return shape == 1 ? 64 : 32; }
+
 void launch_class_gemm(const GemmArgs& a, const Tile* d_tiles, int ntiles, int epi, void* stream) {
     if (ntiles <= 0) return;
-    dim3 grid(ntiles, (a.M + BM - 1) / BM);
     cudaStream_t s = (cudaStream_t)stream;
-    if (a.fp32 && epi == 1)
-        class_gemm_kernel<1, float><<<grid, GT, 0, s>>>(a, d_tiles);
-    else if (a.fp32)
-        class_gemm_kernel<0, float><<<grid, GT, 0, s>>>(a, d_tiles);
-    else if (epi == 1)
-        class_gemm_kernel<1, double><<<grid, GT, 0, s>>>(a, d_tiles);
-    else if (epi == 3)
-        class_gemm_kernel<3, double><<<grid, GT, 0, s>>>(a, d_tiles);
+    if (a.shape == 1)
+        launch_shape<8>(a, d_tiles, ntiles, epi, s);
     else
-        class_gemm_kernel<0, double><<<grid, GT, 0, s>>>(a, d_tiles);
+        launch_shape<16>(a, d_tiles, ntiles, epi, s);
     count_launches(1);
 }
 

@@ -109,6 +109,7 @@ struct GemmArgs {
     unsigned long long* flops;  // if set: each working CTA adds 2 * rows * K * active columns
     int fp32;                 // 1: mats are float, arithmetic in FP32 (EPI 0 only)
     double* out_lo;           // EPI 3: low parts of the compensated out = add + acc
+    int shape;                // tile shape: 0 = 16 rows x 32 columns, 1 = 8 rows x 64 columns
 };
 
 // Number of kernels libsmpm has launched in this process.
@@ -116,6 +117,8 @@ long long launch_count();
 void count_launches(int n);
 
 void launch_class_gemm(const GemmArgs& a, const Tile* d_tiles, int ntiles, int epi, void* stream);
+// columns per tile of a tile shape (the tile lists of a launch are built for it)
+int gemm_tile_columns(int shape);
 
 // Describes the vector batch layout shared by the small kernels.
 struct VecLayout {
