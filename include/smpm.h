@@ -31,6 +31,12 @@
  *   No C++ exception crosses this boundary.
  * Gauge: for k^2 = 0 the solution is returned with zero GLL-quadrature mean
  *   (the Neumann problem fixes u only up to a constant, Sec. 2.4).
+ * Environment switches (none changes a result beyond rounding):
+ *   SMPM_TRACE_SETUP / SMPM_TRACE_SOLVE print setup phases and per-cycle
+ *   residuals on stderr; SMPM_NO_GRAPHS disables CUDA-graph replay of the
+ *   Arnoldi steps; SMPM_TILE_SHAPE=0|1 forces a GEMM tile shape instead of
+ *   the autotuned one; SMPM_REFINE_EXTENDED forces extra-precise refinement;
+ *   SMPM_INNER_STEPS sets the inner steps of precision 2.
  */
 #ifndef SMPM_H
 #define SMPM_H
