@@ -677,10 +677,17 @@ static void setup_solver(Solver& S) {
         const double k2 = S.k2[o];
         double* G = S.G + (size_t)o * 3 * S.sG;
         if (S.fss) {
-            // from fast solves of the 2 fz unit face vectors of one strip
+            // from fast solves of the 2 fz unit face vectors of one strip; the
+            // east boundary class of a mirror-symmetric grid is the west one
+            // with its two faces swapped
             for (int c = 0; c < 3; ++c) {
                 if (c == 1 && mx < 3) {
                     k_fill(G + c * S.sG, S.sG, 0.0, st);
+                    continue;
+                }
+                if (S.slot_cls[c] != c) {
+                    k_mirror_blocks(G + c * S.sG, G + S.slot_cls[c] * S.sG, fz, 2, st);
+                    k_build_rho(S.rho + (size_t)o * S.sRho + (size_t)c * 2 * ng * f2, G + c * S.sG, fz, ng, st);
                     continue;
                 }
                 k_unit_faces(U, n, fz, st);
@@ -708,11 +715,21 @@ static void setup_solver(Solver& S) {
     }
     phase("G");
 
-    // phase 3: block-Jacobi pair blocks and their inverses (Sec. 3.2)
+    // phase 3: block-Jacobi pair blocks and their inverses (Sec. 3.2).  On a
+    // mirror-symmetric grid the last pair (strips of classes 1, 1, 2) is the
+    // mirror image of the first (0, 1, 1): its inverse is the first one's
+    // with the four face blocks reversed.
+    int mc_first = -1, mc_last = -1;
+    for (int mc = 0; mc < S.nmc; ++mc) {
+        if (sig[mc] == std::array<int, 3>{0, 1, 1}) mc_first = mc;
+        if (sig[mc] == std::array<int, 3>{1, 1, 2}) mc_last = mc;
+    }
+    const bool mirror_m = S.slot_cls[2] == 0 && mc_first >= 0 && mc_last >= 0;
     fork();
     for (int o = 0; o < nop; ++o) {
         const double* G = S.G + (size_t)o * 3 * S.sG;
         for (int mc = 0; mc < S.nmc; ++mc) {
+            if (mirror_m && mc == mc_last) continue;   // after the join
             const int l = next_lane++ % L;
             cudaStream_t ls = lanes[l].s;
             const double* gA = G + sig[mc][0] * S.sG;
@@ -736,6 +753,10 @@ static void setup_solver(Solver& S) {
         }
     }
     join();
+    if (mirror_m)
+        for (int o = 0; o < nop; ++o)
+            k_mirror_blocks(S.Minv + ((size_t)o * S.nmc + mc_last) * S.sM, S.Minv + ((size_t)o * S.nmc + mc_first) * S.sM,
+                            fz, 4, st);
     phase("M_inverses");
 
     // phase 4: coarse matrix C = Z^T S Z from the row sums (host), then its

@@ -1137,6 +1137,24 @@ __global__ void g_from_solves_kernel(double* __restrict__ G, const double* __res
     G[idx] = v;
 }
 
+// dst = P src P for an (nb fz) x (nb fz) row-major matrix, P reversing the
+// order of its nb face blocks (z order inside a block kept): the operator of
+// the mirror-image strip or strip pair (x -> -x swaps east and west faces).
+__global__ void mirror_blocks_kernel(double* __restrict__ dst, const double* __restrict__ src, int fz, int nb) {
+    const long long m = (long long)nb * fz;
+    const long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx >= m * m) return;
+    const long long i = idx / m, j = idx - i * m;
+    const long long pi = (nb - 1 - i / fz) * fz + i % fz, pj = (nb - 1 - j / fz) * fz + j % fz;
+    dst[idx] = src[pi * m + pj];
+}
+
+void k_mirror_blocks(double* dst, const double* src, int fz, int nb, cudaStream_t s) {
+    const long long tot = (long long)nb * fz * nb * fz;
+    mirror_blocks_kernel<<<(unsigned)((tot + 255) / 256), 256, 0, s>>>(dst, src, fz, nb);
+    count_launches(1);
+}
+
 void k_g_from_solves(double* G, const double* Y, const double* beta, int n, int fz, int cls, cudaStream_t s) {
     const int tot = 4 * fz * fz;
     g_from_solves_kernel<<<(tot + 255) / 256, 256, 0, s>>>(G, Y, beta, n, fz, cls);

@@ -99,6 +99,8 @@ void k_gauge(const GridArgs& g, int R, double* u, long long u_ld, const int* app
 void k_build_strip_op(double* A, const double* Ax, const double* Lz, double k2, int n, int fz,
                       cudaStream_t s);
 void k_identity(double* X, int m, cudaStream_t s);
+// dst = P src P, P reversing the nb face blocks of an (nb fz)^2 matrix (mirror image)
+void k_mirror_blocks(double* dst, const double* src, int fz, int nb, cudaStream_t s);
 // done[r] = active[r] ? 0 : 1 for r < R
 void k_invert_flags(int* done, const int* active, int R, cudaStream_t s);
 // K <- K - (K u) u^T (row-major d x d, w: d scratch): the projected coarse division
