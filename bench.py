@@ -5,8 +5,9 @@ Workload: the 2-D Poisson-Neumann long-domain problem, 256 x 4 elements of
 order 12 on [0, 64] x [0, 1] (r = 173,056 nodes, k = 26,520 Schur unknowns),
 f = a seeded sum of 32 random low-wavenumber cos-cos modes, g = 0, plain FP64
 path (Alg. seq: block-Jacobi + deflation, CGS2 GMRES) to a relative Schur
-residual of 1e-10.  A step solves one batch of --rhs independent right-hand
-sides (each with its own Krylov space) through the C ABI; value = solved
+residual of 1e-10.  A step solves one batch of --rhs (default 128)
+independent right-hand sides (each with its own Krylov space) through the C
+ABI; value = solved
 right-hand sides per second over all ranks (each rank its own batch: weak
 scaling, no collective on the data path).
 
@@ -41,7 +42,7 @@ def parse():
     p.add_argument("--gpus", type=int, default=1)
     p.add_argument("--steps", type=int, default=5)
     p.add_argument("--warmup", type=int, default=3)
-    p.add_argument("--rhs", type=int, default=16)
+    p.add_argument("--rhs", type=int, default=128, help="right-hand sides per step (one batched solve)")
     p.add_argument("--impl", default="ours", choices=["ours", "reference"])
     p.add_argument("--cpu-sample", type=int, default=2, help="oracle right-hand sides in the cpu_baseline leg")
     p.add_argument("--no-cpu-baseline", action="store_true")
