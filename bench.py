@@ -51,6 +51,7 @@ def parse():
                         "mixed-precision and serving configurations, measured separately (not the driver's "
                         "bench line)")
     p.add_argument("--requests", type=int, default=200, help="serve: requests in the stream")
+    p.add_argument("--mixed-rhs", type=int, default=16, help="mixed: right-hand sides per step")
     p.add_argument("--workers", type=int, default=4, help="serve: server worker threads (one stream each)")
     p.add_argument("--max-batch", type=int, default=16, help="serve: requests per batch at most")
     return p.parse_args()
@@ -400,7 +401,7 @@ def run_other(args):
         s.close()
     else:
         shape = dict(mx=512, mz=16, order=16, lx=32.0, lz=1.0, z_ratio=1.2)
-        R = 4
+        R = args.mixed_rhs
         for prec in (0, 1, 2):
             s = smpm.Solver(smpm.make_grid(**shape, precision=prec), 0.0, stream)
             x, z = s.coords()
@@ -414,7 +415,7 @@ def run_other(args):
             roof = gemm_roofline(s, ms * args.steps, None if prec else FP64_NOMINAL_TFLOPS,
                                  "FP64 and FP32 launches" if prec else "FP64")
             lines.append({"roofline": roof, "workload": "2-D Poisson-Neumann 512x16 elements, order 16, domain 32x1, z stretched "
-                                      "geometrically (ratio 1.2), cos-cos modes, 4 right-hand sides per step",
+                                      "geometrically (ratio 1.2), cos-cos modes, %d right-hand sides per step" % R,
                           "precision": ["FP64", "mixed: FP64 FGMRES, FP32 block-Jacobi",
                                         "nested mixed: FP64 FGMRES, inner DBJ-GMRES with FP32 Schur "
                                         "and block-Jacobi blocks"][prec],

@@ -1,6 +1,6 @@
 """Full-size parity in the launch configuration bench.py times: the 256 x 4,
 order-12 long-domain workload (r = 173,056 nodes, k = 26,520 Schur unknowns),
-16 right-hand sides in one batched FP64 solve, at the bench's 1e-10 and
+128 right-hand sides in one batched FP64 solve, at the bench's 1e-10 and
 again at 1e-11.  Every right-hand side must meet its residual, carry the
 zero-mean gauge and match the analytic solution of the continuous problem to
 1e-9 (the discretisation error here is ~1e-11); sampled right-hand sides are
@@ -20,7 +20,7 @@ from oracle.schur import StripSchur  # noqa: E402
 from oracle import dbj  # noqa: E402
 
 SHAPE = (256, 4, 12, 64.0, 1.0)
-R = 16
+R = 128
 
 
 @pytest.fixture(scope="module")
