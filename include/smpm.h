@@ -152,6 +152,16 @@ int smpm_setup_3d(const smpm_grid* grid, int my, double ly, void* stream, smpm_h
 int smpm_solve_3d(smpm_handle h, const double* fhat, const double* ghat, double tol,
                   double* uhat, smpm_stats* st);
 
+/* The same 3-D problem in physical space (Alg. 3d with the y-transforms on the
+ * GPU): f3, u3: [my][r] doubles, plane t holding the samples at
+ * y_t = t ly / my in node order; g3: [my][nb] Neumann data per plane, or NULL.
+ * The real DFT along y (u_j = (1/my) sum_t u(y_t) e^{-2 pi i j t/my}), the
+ * batched mode solve of smpm_solve_3d and the inverse DFT run on the handle's
+ * stream; pointers host or device.  Only for handles from smpm_setup_3d
+ * (SMPM_EINVAL otherwise).  st->solve_ms covers the whole call. */
+int smpm_solve_3d_physical(smpm_handle h, const double* f3, const double* g3, double tol,
+                           double* u3, smpm_stats* st);
+
 /* Number of nodes r, Neumann values nb and Schur unknowns k of a handle. */
 int smpm_sizes(smpm_handle h, long long* r, long long* nb, long long* k);
 

@@ -92,6 +92,11 @@ struct Solver {
     float* Minv32 = nullptr;              // FP32 block-Jacobi inverses (precision 1 and 2)
     float* G32 = nullptr;                 // FP32 Schur blocks (precision 2: the inner solve)
     int inner_m = 10;                     // inner Arnoldi steps per outer step (precision 2)
+    // physical-space 3-D solve (handles from smpm_setup_3d)
+    int my = 0;
+    double* d_cs = nullptr;               // [cos; sin](2 pi idx / my)
+    double *f3hat = nullptr, *g3hat = nullptr, *u3hat = nullptr, *f3stage = nullptr;
+    long long cap3 = 0, capg3 = 0;
     int precision = 0;
     double *uL = nullptr, *uS = nullptr;
     double* oneS = nullptr;                 // right null vector of S(0): 1 on the interface faces, unit norm
@@ -1918,8 +1923,72 @@ int smpm_setup_3d(const smpm_grid* grid, int my, double ly, void* stream, smpm_h
             const double kj = 2.0 * pi * j / ly;
             k2[j] = kj * kj;
         }
-        *out = (smpm_handle)make_solver(grid, nm, k2.data(), stream);
+        Solver* S = make_solver(grid, nm, k2.data(), stream);
+        S->my = my;
+        *out = (smpm_handle)S;
         return SMPM_OK;
+    });
+}
+
+int smpm_solve_3d_physical(smpm_handle h, const double* f3, const double* g3, double tol, double* u3,
+                           smpm_stats* st) {
+    return guarded([&] {
+        if (!h || !f3 || !u3) throw Err{SMPM_EINVAL, "null argument"};
+        Solver& S = *(Solver*)h;
+        if (S.my <= 0) throw Err{SMPM_EINVAL, "the handle was not built by smpm_setup_3d"};
+        const auto t0 = std::chrono::steady_clock::now();
+        const int my = S.my, nm = my / 2 + 1;
+        const long long r = S.g.r, nb = 2LL * S.g.fz + 2LL * S.g.nx;
+        cudaStream_t st_ = S.stream;
+        if (!S.d_cs) {
+            // exact zeros and ones at the quarter points keep mode 0 and the
+            // Nyquist mode real
+            std::vector<double> cs(2 * (size_t)my);
+            const long double pi = 3.141592653589793238462643383279502884L;
+            for (int i = 0; i < my; ++i) {
+                const long double a = 2.0L * pi * i / my;
+                cs[i] = (4 * i == my || 4 * i == 3 * my) ? 0.0 : (double)std::cos(a);
+                cs[my + i] = (i == 0 || 2 * i == my) ? 0.0 : (double)std::sin(a);
+            }
+            S.d_cs = S.dalloc<double>(cs.size(), S.allocs);
+            upload(S.d_cs, cs, st_);
+        }
+        if (S.cap3 < r) {
+            S.f3hat = S.dalloc<double>((size_t)nm * 2 * r, S.allocs);
+            S.u3hat = S.dalloc<double>((size_t)nm * 2 * r, S.allocs);
+            S.f3stage = S.dalloc<double>((size_t)my * r, S.allocs);
+            S.cap3 = r;
+        }
+        if (g3 && S.capg3 < nb) {
+            S.g3hat = S.dalloc<double>((size_t)nm * 2 * nb + (size_t)my * nb, S.allocs);
+            S.capg3 = nb;
+        }
+        const double* f_d = f3;
+        if (!is_device_ptr(f3)) {
+            CK(cudaMemcpyAsync(S.f3stage, f3, sizeof(double) * my * r, cudaMemcpyHostToDevice, st_));
+            f_d = S.f3stage;
+        }
+        k_dft_forward(f_d, S.f3hat, S.d_cs, r, my, st_);
+        double* gh = nullptr;
+        if (g3) {
+            gh = S.g3hat;
+            const double* g_d = g3;
+            if (!is_device_ptr(g3)) {
+                double* gstage = S.g3hat + (size_t)nm * 2 * nb;
+                CK(cudaMemcpyAsync(gstage, g3, sizeof(double) * my * nb, cudaMemcpyHostToDevice, st_));
+                g_d = gstage;
+            }
+            k_dft_forward(g_d, gh, S.d_cs, nb, my, st_);
+        }
+        std::vector<int> ops(2 * S.nop);
+        for (int j = 0; j < S.nop; ++j) ops[2 * j] = ops[2 * j + 1] = j;
+        const int rc = solve_impl(S, ops, S.f3hat, gh, tol, S.u3hat, st);
+        double* u_d = is_device_ptr(u3) ? u3 : S.f3stage;
+        k_dft_inverse(S.u3hat, u_d, S.d_cs, r, my, st_);
+        if (u_d != u3) CK(cudaMemcpyAsync(u3, u_d, sizeof(double) * my * r, cudaMemcpyDeviceToHost, st_));
+        CK(cudaStreamSynchronize(st_));
+        if (st) st->solve_ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+        return rc;
     });
 }
 

@@ -1137,6 +1137,105 @@ __global__ void g_from_solves_kernel(double* __restrict__ G, const double* __res
     G[idx] = v;
 }
 
+// Real DFT along y (Sec. 5, Eq. fourier_poisson) for the physical-space 3-D
+// solve.  in: [my][n] samples at y_t = t l_y / my; out: [my/2+1][2][n] with
+// u(y) = sum_j u_j e^{i k_j y}: u_j = (1/my) sum_t u(y_t) e^{-2 pi i j t / my}.
+// cs: [2][my] table of cos and sin of 2 pi idx / my.
+static constexpr int DFT_W = 4;   // modes (forward) or planes (inverse) per thread: each load serves four
+
+__global__ void __launch_bounds__(VB) dft_forward_kernel(const double* __restrict__ in, double* __restrict__ out,
+                                                        const double* __restrict__ cs, long long n, int my) {
+    extern __shared__ double tab[];
+    for (int i = threadIdx.x; i < 2 * my; i += VB) tab[i] = cs[i];
+    __syncthreads();
+    const int h = my / 2;
+    const int j0 = blockIdx.y * DFT_W;
+    const long long i = (long long)blockIdx.x * VB + threadIdx.x;
+    if (i >= n) return;
+    // samples t and my - t share cos(2 pi j t / my) and carry opposite sines:
+    // re_j = v_0 + (-1)^j v_{my/2} + sum_{0<t<my/2} (v_t + v_{my-t}) cos,
+    // im_j = -sum_{0<t<my/2} (v_t - v_{my-t}) sin
+    const double v0 = in[i], vh = in[(long long)h * n + i];
+    double re[DFT_W], im[DFT_W];
+    int idx[DFT_W];                                // (j t) mod my, stepped
+#pragma unroll
+    for (int w = 0; w < DFT_W; ++w) {
+        re[w] = v0 + (((j0 + w) & 1) ? -vh : vh);
+        im[w] = 0.0;
+        idx[w] = (j0 + w) % my;
+    }
+    for (int t = 1; t < h; ++t) {
+        const double a = in[(long long)t * n + i], b = in[(long long)(my - t) * n + i];
+        const double sp = a + b, sm = b - a;
+#pragma unroll
+        for (int w = 0; w < DFT_W; ++w) {
+            re[w] = fma(sp, tab[idx[w]], re[w]);
+            im[w] = fma(sm, tab[my + idx[w]], im[w]);
+            idx[w] += j0 + w;
+            if (idx[w] >= my) idx[w] -= my;
+        }
+    }
+    const double inv = 1.0 / my;
+#pragma unroll
+    for (int w = 0; w < DFT_W; ++w) {
+        const int j = j0 + w;
+        if (j > h) break;
+        out[(long long)(2 * j) * n + i] = re[w] * inv;
+        out[(long long)(2 * j + 1) * n + i] = (j == 0 || j == h) ? 0.0 : im[w] * inv;
+    }
+}
+
+// Inverse: u(y_t) = Re u_0 + Re u_{my/2} (-1)^t + 2 sum_{0<j<my/2} Re(u_j e^{2 pi i j t / my});
+// outputs t and my - t together (same cosines, opposite sines), t in [0, my/2]
+__global__ void __launch_bounds__(VB) dft_inverse_kernel(const double* __restrict__ in, double* __restrict__ out,
+                                                        const double* __restrict__ cs, long long n, int my) {
+    extern __shared__ double tab[];
+    for (int i = threadIdx.x; i < 2 * my; i += VB) tab[i] = cs[i];
+    __syncthreads();
+    const int h = my / 2;
+    const int t0 = blockIdx.y * DFT_W;
+    const long long i = (long long)blockIdx.x * VB + threadIdx.x;
+    if (i >= n) return;
+    const double u0 = in[i], uh = in[(long long)(2 * h) * n + i];
+    double A[DFT_W], B[DFT_W];
+    int idx[DFT_W];                                // (j t) mod my, stepped
+#pragma unroll
+    for (int w = 0; w < DFT_W; ++w) {
+        A[w] = u0 + (((t0 + w) & 1) ? -uh : uh);
+        B[w] = 0.0;
+        idx[w] = (t0 + w) % my;
+    }
+    for (int j = 1; j < h; ++j) {
+        const double re = 2.0 * in[(long long)(2 * j) * n + i], im = 2.0 * in[(long long)(2 * j + 1) * n + i];
+#pragma unroll
+        for (int w = 0; w < DFT_W; ++w) {
+            A[w] = fma(re, tab[idx[w]], A[w]);
+            B[w] = fma(im, tab[my + idx[w]], B[w]);
+            idx[w] += t0 + w;
+            if (idx[w] >= my) idx[w] -= my;
+        }
+    }
+#pragma unroll
+    for (int w = 0; w < DFT_W; ++w) {
+        const int t = t0 + w;
+        if (t > h) break;
+        out[(long long)t * n + i] = A[w] - B[w];
+        if (t != 0 && t != h) out[(long long)(my - t) * n + i] = A[w] + B[w];
+    }
+}
+
+void k_dft_forward(const double* in, double* out, const double* cs, long long n, int my, cudaStream_t s) {
+    dim3 grid((unsigned)((n + VB - 1) / VB), (my / 2 + 1 + DFT_W - 1) / DFT_W);
+    dft_forward_kernel<<<grid, VB, (size_t)2 * my * sizeof(double), s>>>(in, out, cs, n, my);
+    count_launches(1);
+}
+
+void k_dft_inverse(const double* in, double* out, const double* cs, long long n, int my, cudaStream_t s) {
+    dim3 grid((unsigned)((n + VB - 1) / VB), (my / 2 + 1 + DFT_W - 1) / DFT_W);
+    dft_inverse_kernel<<<grid, VB, (size_t)2 * my * sizeof(double), s>>>(in, out, cs, n, my);
+    count_launches(1);
+}
+
 // dst = P src P for an (nb fz) x (nb fz) row-major matrix, P reversing the
 // order of its nb face blocks (z order inside a block kept): the operator of
 // the mirror-image strip or strip pair (x -> -x swaps east and west faces).

@@ -17,7 +17,7 @@ SMPM_OK, SMPM_EINVAL, SMPM_ENOMEM, SMPM_ENOCONV, SMPM_EBREAKDOWN, SMPM_ECUDA, SM
 
 # every entry point include/smpm.h declares
 EXPORTS = ["smpm_setup", "smpm_solve", "smpm_solve_batch", "smpm_setup_multi", "smpm_solve_multi",
-           "smpm_setup_3d", "smpm_solve_3d",
+           "smpm_setup_3d", "smpm_solve_3d", "smpm_solve_3d_physical",
            "smpm_sizes", "smpm_node_coords", "smpm_grid_coords", "smpm_null_vectors", "smpm_set_stream", "smpm_device_bytes", "smpm_release", "smpm_probe_fp64",
            "smpm_profile", "smpm_profile_read", "smpm_kernel_launches", "smpm_apply", "smpm_last_residuals", "smpm_apply_deflation_noalloc",
            "smpm_server_create", "smpm_submit", "smpm_poll", "smpm_server_destroy", "smpm_last_error"]
@@ -65,6 +65,7 @@ def load():
     lib.smpm_solve_multi.argtypes = [H, ctypes.c_int, P, P, P, ctypes.c_double, P, ctypes.POINTER(Stats)]
     lib.smpm_setup_3d.argtypes = [ctypes.POINTER(Grid), ctypes.c_int, ctypes.c_double, P, ctypes.POINTER(H)]
     lib.smpm_solve_3d.argtypes = [H, P, P, ctypes.c_double, P, ctypes.POINTER(Stats)]
+    lib.smpm_solve_3d_physical.argtypes = [H, P, P, ctypes.c_double, P, ctypes.POINTER(Stats)]
     lib.smpm_sizes.argtypes = [H, ctypes.POINTER(ctypes.c_longlong), ctypes.POINTER(ctypes.c_longlong),
                                ctypes.POINTER(ctypes.c_longlong)]
     lib.smpm_node_coords.argtypes = [H, P, P]
@@ -246,6 +247,12 @@ class Solver3D(Solver):
         """fhat, uhat: [n_modes, 2, r] float64 (real and imaginary parts)."""
         st = Stats()
         _check(load().smpm_solve_3d(self._h, _ptr(fhat), _ptr(ghat), float(tol), _ptr(uhat), ctypes.byref(st)))
+        return st
+
+    def solve_3d_physical(self, f3, u3, g3=None, tol=1e-10):
+        """f3, u3: [my, r] float64 planes (y_t = t ly / my); g3: [my, nb] or None."""
+        st = Stats()
+        _check(load().smpm_solve_3d_physical(self._h, _ptr(f3), _ptr(g3), float(tol), _ptr(u3), ctypes.byref(st)))
         return st
 
 
