@@ -54,6 +54,8 @@ def parse():
     p.add_argument("--mixed-rhs", type=int, default=16, help="mixed: right-hand sides per step")
     p.add_argument("--workers", type=int, default=4, help="serve: server worker threads (one stream each)")
     p.add_argument("--max-batch", type=int, default=16, help="serve: requests per batch at most")
+    p.add_argument("--served-precision", type=int, default=2, choices=[0, 1, 2],
+                   help="serve: precision of the served solves (the plain baseline is always FP64)")
     return p.parse_args()
 
 
@@ -490,6 +492,9 @@ def run_serve(args):
     reqs = serve_stream(args.requests, inputs.seed_for(5))
     for q in reqs:
         q["grid"] = smpm.make_grid(q["mx"], q["mz"], q["order"], q["mx"] / q["mz"], 1.0)
+        # the served form may run the mixed-precision solve (same FP64 true residual)
+        q["grid_served"] = smpm.make_grid(q["mx"], q["mz"], q["order"], q["mx"] / q["mz"], 1.0,
+                                          precision=args.served_precision)
         q["f"] = torch.from_numpy(serve_rhs(smpm, q["grid"], q["mx"] / q["mz"], q["seed"])).to(dev)
         q["u_plain"] = torch.zeros_like(q["f"])
         q["u_served"] = torch.zeros_like(q["f"])
@@ -510,9 +515,10 @@ def run_serve(args):
             continue
         seen.add(key)
         for k2w in (1.0, 0.0):
-            s = smpm.Solver(q["grid"], k2w, stream)
-            s.solve(q["f"], q["u_plain"], tol=TOL)
-            s.close()
+            for gw in {id(q["grid"]): q["grid"], id(q["grid_served"]): q["grid_served"]}.values():
+                s = smpm.Solver(gw, k2w, stream)
+                s.solve(q["f"], q["u_plain"], tol=TOL)
+                s.close()
     torch.cuda.synchronize()
     srv = smpm.Server(nworkers=args.workers, max_batch=args.max_batch)
     t = srv.submit(wg, 2.0, wf, wu, tol=TOL)
@@ -552,7 +558,7 @@ def run_serve(args):
         now = time.perf_counter() - t0
         while nxt < len(reqs) and arrivals[nxt] - arrivals[0] <= now:
             q = reqs[nxt]
-            tickets[srv.submit(q["grid"], q["k2"], q["f"], q["u_served"], tol=TOL)] = nxt
+            tickets[srv.submit(q["grid_served"], q["k2"], q["f"], q["u_served"], tol=TOL)] = nxt
             nxt += 1
         for tk, i in list(tickets.items()):
             st = srv.poll(tk)
@@ -576,7 +582,7 @@ def run_serve(args):
     for q in reqs:
         q["u_burst"] = torch.zeros_like(q["f"])
     t0 = time.perf_counter()
-    burst = [srv.submit(q["grid"], q["k2"], q["f"], q["u_burst"], tol=TOL) for q in reqs]
+    burst = [srv.submit(q["grid_served"], q["k2"], q["f"], q["u_burst"], tol=TOL) for q in reqs]
     pend = set(burst)
     res_burst = []
     while pend:
@@ -613,7 +619,9 @@ def run_serve(args):
             "metric": "solves/s at 1e-10 rel. residual, p50/p99 latency: served vs plain FP64",
             "unit": "solves/s", "value": len(reqs) / burst_span, "dtype": "f64", "data": "synthetic",
             "value_is": "served capacity: the stream submitted at once",
-            "served": {"capacity_solves_per_s": len(reqs) / burst_span,
+            "served": {"precision": ["FP64", "mixed: FP64 FGMRES, FP32 block-Jacobi",
+                                     "nested mixed"][args.served_precision],
+                       "capacity_solves_per_s": len(reqs) / burst_span,
                        "solves_per_s_at_arrival_rate": len(reqs) / served_span, "p50_ms": pct(lat_served, 50),
                        "p99_ms": pct(lat_served, 99), "workers": args.workers, "max_batch": args.max_batch,
                        "mean_batch": float(np.mean(batch_sizes)),

@@ -91,6 +91,8 @@ struct Solver {
     double *Ainv = nullptr, *W = nullptr, *G = nullptr, *Minv = nullptr, *rho = nullptr, *K = nullptr;
     float* Minv32 = nullptr;              // FP32 block-Jacobi inverses (precision 1 and 2)
     float* G32 = nullptr;                 // FP32 Schur blocks (precision 2: the inner solve)
+    double fp32_err = 0.0;                // measured relative error of the FP32 block-Jacobi apply
+    bool bj32_ok = true;                  // FP32 blocks adequate (precision 1 uses them)
     int inner_m = 10;                     // inner Arnoldi steps per outer step (precision 2)
     // physical-space 3-D solve (handles from smpm_setup_3d)
     int my = 0;
@@ -146,8 +148,8 @@ struct Solver {
         long long launches = 0;              // library kernels in the graph
         std::vector<cudaEvent_t> ev;         // GEMM event pairs (profiling)
     };
-    std::map<std::array<int, 3>, GroupGraph> graphs;
-    std::map<std::array<int, 3>, int> group_seen;
+    std::map<std::array<int, 4>, GroupGraph> graphs;
+    std::map<std::array<int, 4>, int> group_seen;
     cudaStream_t cap_stream = nullptr;
     std::vector<cudaEvent_t>* cap_events = nullptr;   // set while capturing with profiling on
     bool graphs_ok = true;
@@ -898,6 +900,19 @@ static void setup_solver(Solver& S) {
     if (S.precision >= 1) {
         S.Minv32 = S.dalloc<float>((size_t)nop * S.nmc * S.sM, S.allocs);
         k_to_fp32(S.Minv32, S.Minv, (long long)nop * S.nmc * S.sM, st);
+        // An FP32 copy of an ill-conditioned block inverse (large k^2 on fine
+        // grids) turns the preconditioner into noise: measure the FP32 apply's
+        // relative error on a sign vector for every block, and keep the FP64
+        // blocks for precision 1 when it exceeds 1e-3.
+        double* q = S.dalloc<double>((size_t)nop * S.nmc, tmp);
+        k_fp32_quality(S.Minv, S.Minv32, f4, S.sM, nop * S.nmc, q, st);
+        std::vector<double> qh((size_t)nop * S.nmc);
+        CK(cudaMemcpyAsync(qh.data(), q, sizeof(double) * qh.size(), cudaMemcpyDeviceToHost, st));
+        CK(cudaStreamSynchronize(st));
+        S.fp32_err = 0.0;
+        for (double v : qh) S.fp32_err = std::max(S.fp32_err, v);
+        S.bj32_ok = S.fp32_err <= 1e-3;
+        if (trace) fprintf(stderr, "smpm setup: FP32 block-Jacobi relative apply error %.2e\n", S.fp32_err);
     }
     if (S.precision == 2) {
         S.G32 = S.dalloc<float>((size_t)nop * 3 * S.sG, S.allocs);
@@ -1458,6 +1473,13 @@ static int solve_impl(Solver& S, const std::vector<int>& ops, const double* f, c
     // the cycle-start residual b_S - S (x_S + x_lo) is formed with the
     // compensated Schur product; the GMRES cycles themselves stay FP64
     // (iterative refinement with an extra-precise residual).
+    // precision 1 applies the block-Jacobi blocks in FP32; when a refinement
+    // cycle reduces the true residual by less than 10x (FP32 blocks too coarse
+    // for an ill-conditioned M, e.g. large k^2), the remaining cycles of this
+    // solve use the FP64 blocks (the flexible GMRES allows the switch)
+    bool bj_fp32 = S.precision == 1 && S.bj32_ok;
+    bool group_fp32 = bj_fp32;
+    double prev_cycle_rel = -1.0;
     bool ext = false;
     if (std::getenv("SMPM_REFINE_EXTENDED") != nullptr) {   // from the first refinement step on
         ext = true;
@@ -1497,6 +1519,15 @@ static int solve_impl(Solver& S, const std::vector<int>& ops, const double* f, c
             for (int r = 0; r < R; ++r) fprintf(stderr, " rel[%d] %.3e", r, h_bn[r] > 0 ? h_rn[r] / h_bn[r] : 0.0);
             host_norms(w.xS, "xS");
             fprintf(stderr, "\n");
+        }
+        if (bj_fp32 && !first) {
+            double worst_rel = 0.0;
+            for (int r = 0; r < R; ++r)
+                if (!h_done[r] && h_bn[r] > 0.0) worst_rel = std::max(worst_rel, h_rn[r] / h_bn[r]);
+            if (worst_rel > 0.0 && prev_cycle_rel > 0.0 && worst_rel > 0.1 * prev_cycle_rel) bj_fp32 = false;
+            prev_cycle_rel = worst_rel;
+        } else if (bj_fp32) {
+            prev_cycle_rel = 1.0;
         }
         bool switch_ext = false;
         for (int r = 0; r < R; ++r) {
@@ -1541,7 +1572,8 @@ static int solve_impl(Solver& S, const std::vector<int>& ops, const double* f, c
         const int last_allowed = std::min(m, S.max_iter - total_it);
         int j = 0;
         const bool mixed = S.precision >= 1;      // flexible: the preconditioned vectors are kept
-        const bool use_graphs = S.graphs_ok && !graphs_off;
+        // (the nested form's steps carry whole inner solves; they run uncaptured)
+        const bool use_graphs = S.graphs_ok && !graphs_off && !nested;
         // one Arnoldi step j of every active right-hand side
         auto step = [&](int jj) {
             // z_j = M^-1 v_j (FP32 block-Jacobi in the mixed form, the inner
@@ -1552,7 +1584,7 @@ static int solve_impl(Solver& S, const std::vector<int>& ops, const double* f, c
                 inner_solve(jj);
                 zj = w.xi;
             } else {
-                bj(w.V, (long long)(m + 1) * ld, (long long)jj * ld, w.z, ld, 0, w.active, mixed);
+                bj(w.V, (long long)(m + 1) * ld, (long long)jj * ld, w.z, ld, 0, w.active, group_fp32);
             }
             if (mixed)
                 CK(cudaMemcpy2DAsync(w.Zb + (long long)jj * ld, (size_t)m * ld * 8, zj, (size_t)ld * 8,
@@ -1567,7 +1599,12 @@ static int solve_impl(Solver& S, const std::vector<int>& ops, const double* f, c
         };
         while (j < last_allowed) {
             const int cnt = std::min(check_every - j % check_every, last_allowed - j);
-            const std::array<int, 3> key{j, cnt, last_allowed};
+            // precision 1: the first step group of the first cycle applies the
+            // FP64 blocks (easy problems -- large k^2 -- converge right there,
+            // where FP32 copies of their ill-conditioned blocks would stall the
+            // flexible GMRES near 1e-8); FP32 from the next group on
+            group_fp32 = bj_fp32 && !(cycles == 0 && j < check_every);
+            const std::array<int, 4> key{j, cnt, last_allowed, group_fp32 ? 1 : 0};
             Solver::GroupGraph* gg = nullptr;
             if (use_graphs) {
                 auto it = S.graphs.find(key);

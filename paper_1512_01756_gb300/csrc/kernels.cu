@@ -1137,6 +1137,39 @@ __global__ void g_from_solves_kernel(double* __restrict__ G, const double* __res
     G[idx] = v;
 }
 
+// Quality of the FP32 block-Jacobi copies: for each m x m block (row-major,
+// FP64 inverse A and its FP32 copy B), the relative difference
+// |A v - B v| / |A v| of the FP64 product and the FP32 product (FP32 inputs and
+// accumulation, as the mixed apply does) for a fixed sign vector v.  One block
+// of VB threads per matrix; out[i] receives the ratio.
+__global__ void __launch_bounds__(VB) fp32_quality_kernel(const double* __restrict__ A, const float* __restrict__ B,
+                                                         int m, long long stride, double* __restrict__ out) {
+    __shared__ double red[32];
+    const double* a = A + (long long)blockIdx.x * stride;
+    const float* b = B + (long long)blockIdx.x * stride;
+    double num = 0.0, den = 0.0;
+    for (int i = threadIdx.x; i < m; i += VB) {
+        double y64 = 0.0;
+        float y32 = 0.0f;
+        for (int j = 0; j < m; ++j) {
+            const unsigned hsh = (unsigned)j * 2654435761u;
+            const double v = (hsh & 0x10000u) ? 1.0 : -1.0;
+            y64 = fma(a[(long long)i * m + j], v, y64);
+            y32 = fmaf(b[(long long)i * m + j], (float)v, y32);
+        }
+        num = fma(y64 - (double)y32, y64 - (double)y32, num);
+        den = fma(y64, y64, den);
+    }
+    num = block_sum(num, red);
+    den = block_sum(den, red);
+    if (threadIdx.x == 0) out[blockIdx.x] = den > 0.0 ? sqrt(num / den) : 0.0;
+}
+
+void k_fp32_quality(const double* A, const float* B, int m, long long stride, int nmat, double* out, cudaStream_t s) {
+    fp32_quality_kernel<<<nmat, VB, 0, s>>>(A, B, m, stride, out);
+    count_launches(1);
+}
+
 // Real DFT along y (Sec. 5, Eq. fourier_poisson) for the physical-space 3-D
 // solve.  in: [my][n] samples at y_t = t l_y / my; out: [my/2+1][2][n] with
 // u(y) = sum_j u_j e^{i k_j y}: u_j = (1/my) sum_t u(y_t) e^{-2 pi i j t / my}.

@@ -99,6 +99,8 @@ void k_gauge(const GridArgs& g, int R, double* u, long long u_ld, const int* app
 void k_build_strip_op(double* A, const double* Ax, const double* Lz, double k2, int n, int fz,
                       cudaStream_t s);
 void k_identity(double* X, int m, cudaStream_t s);
+// per matrix: |A v - fl32(B) v| / |A v| for a fixed sign vector (FP32 copy adequacy)
+void k_fp32_quality(const double* A, const float* B, int m, long long stride, int nmat, double* out, cudaStream_t s);
 // real DFT along y: [my][n] -> [my/2+1][2][n] (scaled by 1/my) and back; cs = [cos; sin](2 pi idx / my)
 void k_dft_forward(const double* in, double* out, const double* cs, long long n, int my, cudaStream_t s);
 void k_dft_inverse(const double* in, double* out, const double* cs, long long n, int my, cudaStream_t s);

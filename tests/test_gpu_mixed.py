@@ -120,3 +120,40 @@ def test_mixed_full_workload_matches_fp64(smpm):
     ue = u_ex - np.average(u_ex, weights=w)
     err = np.abs((u32 - u32.mean()) - ue).max() / np.abs(ue).max()
     assert err < 1e-6, err
+
+
+def test_mixed_falls_back_to_fp64_blocks_for_large_k2(smpm):
+    """256 x 8 order 12 at k^2 = 3416 (a request of the serving stream): the
+    FP64 solve converges in 3 iterations, while flexible GMRES with the FP32
+    block-Jacobi copies (apply error only 2.7e-7) stalled near 1e-8, each
+    64-step cycle gaining ~3x.  Precision 1 now takes its first step group
+    with the FP64 blocks, where such easy problems converge; the solve must
+    reach its residual and the FP64 solution, and so must the nested form."""
+    from paper_1512_01756_gb300 import inputs
+    shape, k2, seed = (256, 8, 12, 32.0, 1.0), 3415.846389920769, 20151365
+    grid = smpm.make_grid(*shape)
+    x, z = smpm.grid_coords(grid)
+    f, _ = inputs.cos_modes(x, z, 32.0, 1.0, inputs.cos_modes_spec(seed))
+    out = {}
+    for prec in (0, 1, 2):
+        s = smpm.Solver(smpm.make_grid(*shape, precision=prec), k2)
+        u = np.zeros_like(f)
+        st = s.solve(f, u, tol=1e-11)      # the 1e-9 bar needs ~kappa * tol below it
+        s.close()
+        assert st.status == 0 and st.rel_resid_true <= 1e-11, (prec, st.as_dict())
+        out[prec] = u
+    assert _rel(out[1], out[0]) < 1e-9 and _rel(out[2], out[0]) < 1e-9
+
+
+def test_nested_multi_cycle(smpm):
+    """The nested form over several outer restart cycles (restart 2)."""
+    shape = (12, 4, 7, 3.0, 1.0, 1.0)
+    g = Grid(*shape[:5])
+    f = np.random.default_rng(71).uniform(0, 1, g.r)
+    s = smpm.Solver(smpm.make_grid(*shape[:5], precision=2, restart=2), 0.0)
+    u = np.zeros_like(f)
+    st = s.solve(f, u, tol=1e-11)
+    s.close()
+    assert st.status == 0 and st.rel_resid_true <= 1e-11 and st.restarts >= 1, st.as_dict()
+    u_ref, _ = direct_solve(g, f)
+    assert _rel(u, u_ref) < 1e-9
