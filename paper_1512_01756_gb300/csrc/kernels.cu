@@ -23,7 +23,7 @@ void count_launches(int n) { g_launches.fetch_add(n); }
 
 #define CUDA_LAUNCH_CHECK() (void)0
 
-static constexpr int BM = 16, BN = 32, BK = 16, GT = 128;
+static constexpr int BM = 16, BK = 16, GT = 128;   // default tile rows, K slab, threads per GEMM CTA
 static constexpr int VB = 256;  // threads of the vector kernels
 
 __device__ __forceinline__ double warp_sum(double v) {
