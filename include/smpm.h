@@ -110,6 +110,16 @@ int smpm_solve(smpm_handle h, const double* f, const double* g, double tol,
 int smpm_solve_batch(smpm_handle h, int nrhs, const double* f, const double* g,
                      double tol, double* u, smpm_stats* st);
 
+/* smpm_solve_batch from an initial guess u0 (nrhs consecutive r-vectors, host
+ * or device; NULL = zero): the first refinement cycle starts from
+ * x_S0 = B u0, the interface unknowns of the guess (the exact solution has
+ * x_S = B u, Sec. 2.3), so a guess close to the solution (the previous time
+ * step's field) leaves only its error for GMRES.  The convergence test is the
+ * same (||S x_S - b_S|| <= tol ||b_S||).  The guess is ignored on the
+ * dense-inverse fallback path. */
+int smpm_solve_guess(smpm_handle h, int nrhs, const double* f, const double* g, const double* u0,
+                     double tol, double* u, smpm_stats* st);
+
 /* One handle holding the operators of several k^2 values (the Fourier modes
  * of the 3-D problem, Sec. 5, Alg. 3d): nop >= 1 values k2[0..nop-1], at most
  * one of them zero.  Each operator set is built as by smpm_setup. */

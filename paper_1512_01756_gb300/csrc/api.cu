@@ -1263,7 +1263,7 @@ static void harvest_profile(Solver& S) {
 }
 
 static int solve_impl(Solver& S, const std::vector<int>& ops, const double* f, const double* gb, double tol,
-                      double* u, smpm_stats* st) {
+                      double* u, smpm_stats* st, const double* u0 = nullptr) {
     auto t0 = std::chrono::steady_clock::now();
     const int R = (int)ops.size();
     if (R <= 0) throw Err{SMPM_EINVAL, "nrhs must be positive"};
@@ -1448,6 +1448,17 @@ static int solve_impl(Solver& S, const std::vector<int>& ops, const double* f, c
     CK(cudaMemsetAsync(w.flags, 0, R * sizeof(int), st_));
     CK(cudaMemsetAsync(w.nit, 0, R * sizeof(int), st_));
     k_fill(w.xS, (long long)R * ld, 0.0, st_);
+    // warm start: x_S0 = B u0 (the interface unknowns of a guess, Sec. 2.3:
+    // the exact solution has x_S = B u)
+    const bool warm = u0 != nullptr && S.fss;
+    if (warm) {
+        const double* u0_d = u0;
+        if (!is_device_ptr(u0)) {
+            CK(cudaMemcpyAsync(w.ustage, u0, sizeof(double) * g.r * R, cudaMemcpyHostToDevice, st_));
+            u0_d = w.ustage;
+        }
+        k_face_flux(fa, R, S.d_beta, u0_d, g.r, w.xS, ld, S.kp, st_);
+    }
 
     // Restart cycles as iterative refinement on x_S: every cycle starts from the
     // true residual d = b_S - S x_S, runs deflated right-preconditioned GMRES on
@@ -1488,8 +1499,8 @@ static int solve_impl(Solver& S, const std::vector<int>& ops, const double* f, c
         ka.s_lo = w.slo;
         ka.s_xlo = w.sxlo;
     }
-    auto cycle_residual = [&](bool at_start) {
-        if (!at_start) {
+    auto cycle_residual = [&](bool zero_x, bool stamp) {
+        if (!zero_x) {
             if (ext) {
                 schur_ext(w.xS, w.s, w.slo);
                 schur(w.xSlo, ld, 0, w.sxlo, nullptr);
@@ -1505,11 +1516,11 @@ static int solve_impl(Solver& S, const std::vector<int>& ops, const double* f, c
             k_dot_partial(R, S.kp, w.s, ld, w.uSp, w.rpart, nch, kChunk, st_);
             k_project(R, S.kp, w.s, ld, w.uSp, w.rpart, nch, kChunk, st_);
         }
-        k_residual(ka, w.bS, at_start ? nullptr : w.s, st_);
-        k_cycle_start(ka, w.c0, at_start ? 1 : 0, tol, st_);
+        k_residual(ka, w.bS, zero_x ? nullptr : w.s, st_);
+        k_cycle_start(ka, w.c0, stamp ? 1 : 0, tol, st_);
     };
     while (true) {
-        cycle_residual(first);
+        cycle_residual(first && !warm, first);
         CK(cudaMemcpyAsync(h_done.data(), w.done, R * sizeof(int), cudaMemcpyDeviceToHost, st_));
         CK(cudaMemcpyAsync(h_rn.data(), w.rnorm, R * sizeof(double), cudaMemcpyDeviceToHost, st_));
         CK(cudaMemcpyAsync(h_bn.data(), w.bnorm, R * sizeof(double), cudaMemcpyDeviceToHost, st_));
@@ -1544,7 +1555,7 @@ static int solve_impl(Solver& S, const std::vector<int>& ops, const double* f, c
             ka.s_lo = w.slo;
             ka.s_xlo = w.sxlo;
             std::fill(stall.begin(), stall.end(), 0);
-            cycle_residual(false);   // this cycle starts from the extra-precise residual
+            cycle_residual(false, false);   // this cycle starts from the extra-precise residual
             CK(cudaMemcpyAsync(h_done.data(), w.done, R * sizeof(int), cudaMemcpyDeviceToHost, st_));
             CK(cudaMemcpyAsync(h_rn.data(), w.rnorm, R * sizeof(double), cudaMemcpyDeviceToHost, st_));
             CK(cudaStreamSynchronize(st_));
@@ -1897,6 +1908,17 @@ int smpm_setup(const smpm_grid* grid, double k2, void* stream, smpm_handle* out)
         if (!out) throw Err{SMPM_EINVAL, "out is null"};
         *out = (smpm_handle)make_solver(grid, 1, &k2, stream);
         return SMPM_OK;
+    });
+}
+
+int smpm_solve_guess(smpm_handle h, int nrhs, const double* f, const double* g, const double* u0, double tol,
+                     double* u, smpm_stats* st) {
+    return guarded([&] {
+        if (!h) throw Err{SMPM_EINVAL, "null handle"};
+        if (nrhs <= 0) throw Err{SMPM_EINVAL, "nrhs must be positive"};
+        Solver& S = *(Solver*)h;
+        std::vector<int> ops((size_t)nrhs, 0);
+        return solve_impl(S, ops, f, g, tol, u, st, u0);
     });
 }
 

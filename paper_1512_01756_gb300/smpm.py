@@ -16,7 +16,7 @@ LIB_PATH = os.path.join(_PKG, "libsmpm.so")
 SMPM_OK, SMPM_EINVAL, SMPM_ENOMEM, SMPM_ENOCONV, SMPM_EBREAKDOWN, SMPM_ECUDA, SMPM_EBUSY = 0, -1, -2, -3, -4, -5, -6
 
 # every entry point include/smpm.h declares
-EXPORTS = ["smpm_setup", "smpm_solve", "smpm_solve_batch", "smpm_setup_multi", "smpm_solve_multi",
+EXPORTS = ["smpm_setup", "smpm_solve", "smpm_solve_batch", "smpm_solve_guess", "smpm_setup_multi", "smpm_solve_multi",
            "smpm_setup_3d", "smpm_solve_3d", "smpm_solve_3d_physical",
            "smpm_sizes", "smpm_node_coords", "smpm_grid_coords", "smpm_null_vectors", "smpm_set_stream", "smpm_device_bytes", "smpm_release", "smpm_probe_fp64",
            "smpm_profile", "smpm_profile_read", "smpm_kernel_launches", "smpm_apply", "smpm_last_residuals", "smpm_apply_deflation_noalloc",
@@ -62,6 +62,7 @@ def load():
     lib.smpm_setup_multi.argtypes = [ctypes.POINTER(Grid), ctypes.c_int, P, P, ctypes.POINTER(H)]
     lib.smpm_solve.argtypes = [H, P, P, ctypes.c_double, P, ctypes.POINTER(Stats)]
     lib.smpm_solve_batch.argtypes = [H, ctypes.c_int, P, P, ctypes.c_double, P, ctypes.POINTER(Stats)]
+    lib.smpm_solve_guess.argtypes = [H, ctypes.c_int, P, P, P, ctypes.c_double, P, ctypes.POINTER(Stats)]
     lib.smpm_solve_multi.argtypes = [H, ctypes.c_int, P, P, P, ctypes.c_double, P, ctypes.POINTER(Stats)]
     lib.smpm_setup_3d.argtypes = [ctypes.POINTER(Grid), ctypes.c_int, ctypes.c_double, P, ctypes.POINTER(H)]
     lib.smpm_solve_3d.argtypes = [H, P, P, ctypes.c_double, P, ctypes.POINTER(Stats)]
@@ -174,11 +175,15 @@ class Solver:
         _check(load().smpm_null_vectors(self._h, _ptr(uL), _ptr(uS)))
         return uL, uS
 
-    def solve(self, f, u, g=None, tol=1e-10):
-        """f, u: one r-vector or [nrhs, r]; g: [nrhs, nb] or None.  Returns Stats."""
+    def solve(self, f, u, g=None, tol=1e-10, u0=None):
+        """f, u: one r-vector or [nrhs, r]; g: [nrhs, nb] or None; u0: an initial
+        guess shaped like u, or None.  Returns Stats."""
         st = Stats()
         nrhs = 1 if len(f.shape) == 1 else int(f.shape[0])
-        if nrhs == 1:
+        if u0 is not None:
+            code = load().smpm_solve_guess(self._h, nrhs, _ptr(f), _ptr(g), _ptr(u0), float(tol), _ptr(u),
+                                           ctypes.byref(st))
+        elif nrhs == 1:
             code = load().smpm_solve(self._h, _ptr(f), _ptr(g), float(tol), _ptr(u), ctypes.byref(st))
         else:
             code = load().smpm_solve_batch(self._h, nrhs, _ptr(f), _ptr(g), float(tol), _ptr(u), ctypes.byref(st))

@@ -125,3 +125,34 @@ def test_profiling_counts_replayed_gemms(smpm):
     for p in per:
         assert p["ms"] > 0.0
         assert p["launches"] == per[0]["launches"] and p["flops"] == per[0]["flops"], per
+
+
+@pytest.mark.parametrize("k2", [0.0, 5.0])
+def test_warm_start_from_a_guess(smpm, k2):
+    """smpm_solve_guess: from the converged solution the solve stops at once
+    with the same answer; from a perturbed guess it needs fewer iterations
+    than from zero and meets the same residual and the direct solve."""
+    from oracle.smpm import Grid, direct_solve
+    shape = (12, 4, 7, 3.0, 1.0)
+    g = Grid(*shape)
+    rng = np.random.default_rng(90)
+    f = rng.uniform(0, 1, g.r)
+    s = smpm.Solver(smpm.make_grid(*shape), k2)
+    u_cold = np.zeros_like(f)
+    st_cold = s.solve(f, u_cold, tol=1e-10)
+    u_same = np.zeros_like(f)
+    st_same = s.solve(f, u_same, tol=1e-10, u0=u_cold)
+    X, Z = g.coords()
+    guess = u_cold + 1e-4 * np.abs(u_cold).max() * np.cos(np.pi * X / 3.0) * np.cos(2 * np.pi * Z)
+    u_warm = np.zeros_like(f)
+    st_warm = s.solve(f, u_warm, tol=1e-10, u0=guess)
+    u_zero = np.zeros_like(f)
+    st_zero = s.solve(f, u_zero, tol=1e-10, u0=np.zeros_like(f))
+    s.close()
+    u_ref, _ = direct_solve(g, f, None, k2)
+    assert st_cold.status == 0 and st_same.status == 0 and st_warm.status == 0
+    assert st_same.iters <= 1 and np.linalg.norm(u_same - u_cold) < 1e-9 * np.linalg.norm(u_cold)
+    assert st_warm.iters < st_cold.iters, (st_warm.iters, st_cold.iters)
+    assert st_warm.rel_resid_true <= 1e-10
+    assert np.linalg.norm(u_warm - u_ref) < 1e-9 * np.linalg.norm(u_ref)
+    assert st_zero.iters == st_cold.iters and np.array_equal(u_zero, u_cold)
