@@ -76,7 +76,8 @@ typedef struct {
                                strip solves in FP64) preconditioned by an inner
                                deflated block-Jacobi GMRES whose Schur products
                                and block-Jacobi applies use FP32 blocks with FP32
-                               accumulation (10 inner steps or 1e-4 relative;
+                               accumulation (its block-Jacobi inverses are
+                               factorised in FP32 too; 10 inner steps or 1e-4 relative;
                                SMPM_INNER_STEPS overrides the step count)      */
 } smpm_grid;
 

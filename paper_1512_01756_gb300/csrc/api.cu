@@ -619,13 +619,24 @@ static void setup_solver(Solver& S) {
     guard.lanes = &lanes;
     const int L = (int)lanes.size();
     const int mlane = std::max(f4, S.fss ? f2 : 0);
-    struct LaneBuf { double *a, *b, *work; int* ipiv; };
+    // precision 2 uses only FP32 block-Jacobi inverses: they are factorised
+    // and inverted in FP32 (cuSOLVER S-getrf/getrs) from the FP64 blocks
+    const bool m_fp32 = S.precision == 2;
+    int lwork_f = 0;
+    if (m_fp32) CS(cusolverDnSgetrf_bufferSize(S.sol, f4, f4, nullptr, f4, &lwork_f));
+    struct LaneBuf { double *a, *b, *work; int* ipiv; float *af, *cf, *workf; };
     std::vector<LaneBuf> lb(L);
     for (int l = 0; l < L; ++l) {
         lb[l].a = S.dalloc<double>((size_t)mlane * mlane, tmp);
         lb[l].b = S.dalloc<double>((size_t)f2 * f2, tmp);
         lb[l].work = S.dalloc<double>((size_t)std::max(lwork, 1), tmp);
         lb[l].ipiv = S.dalloc<int>((size_t)mlane, tmp);
+        lb[l].af = lb[l].cf = lb[l].workf = nullptr;
+        if (m_fp32) {
+            lb[l].af = S.dalloc<float>((size_t)f4 * f4, tmp);
+            lb[l].cf = S.dalloc<float>((size_t)f4 * f4, tmp);
+            lb[l].workf = S.dalloc<float>((size_t)std::max(lwork_f, 1), tmp);
+        }
     }
     int n_inv = 0;
     for (int c = 0; c < 3 && S.fss; ++c) n_inv += (int)S.sl_size[c].size();
@@ -787,7 +798,10 @@ static void setup_solver(Solver& S) {
         if (sig[mc] == std::array<int, 3>{0, 1, 1}) mc_first = mc;
         if (sig[mc] == std::array<int, 3>{1, 1, 2}) mc_last = mc;
     }
-    const bool mirror_m = S.slot_cls[2] == 0 && mc_first >= 0 && mc_last >= 0;
+    const bool mirror_m = S.slot_cls[2] == 0 && mc_first >= 0 && mc_last >= 0 && !m_fp32;
+    if (m_fp32) {   // the FP32 inverses go straight into Minv32
+        S.Minv32 = S.dalloc<float>((size_t)nop * S.nmc * S.sM, S.allocs);
+    }
     fork();
     for (int o = 0; o < nop; ++o) {
         const double* G = S.G + (size_t)o * 3 * S.sG;
@@ -800,6 +814,23 @@ static void setup_solver(Solver& S) {
             const double* gC = sig[mc][2] >= 0 ? G + sig[mc][2] * S.sG : nullptr;
             const int m = gC ? f4 : f2;
             double* dst = S.Minv + ((size_t)o * S.nmc + mc) * S.sM;
+            if (m_fp32) {
+                float* dst32 = S.Minv32 + ((size_t)o * S.nmc + mc) * S.sM;
+                if (S.P == 1 && S.k2[o] == 0.0) {
+                    k_identity_f(lb[l].cf, m, ls);
+                } else {
+                    k_build_M(lb[l].a, gA, gB, gC, fz, ls);
+                    k_to_fp32(lb[l].af, lb[l].a, (long long)m * m, ls);
+                    const int slot = inv_used++;
+                    if (slot >= n_inv) throw Err{SMPM_ECUDA, "setup: inversion count exceeded"};
+                    int* info = d_infos + 2 * slot;
+                    k_identity_f(lb[l].cf, m, ls);
+                    CS(cusolverDnSgetrf(lanes[l].h, m, m, lb[l].af, m, lb[l].workf, lb[l].ipiv, info));
+                    CS(cusolverDnSgetrs(lanes[l].h, CUBLAS_OP_N, m, m, lb[l].af, m, lb[l].ipiv, lb[l].cf, m, info + 1));
+                }
+                k_pad_block_f(dst32, lb[l].cf, m, f4, ls);
+                continue;
+            }
             if (S.P == 1 && S.k2[o] == 0.0) {
                 // m_x <= 3: the one block is all of the singular S; use M = I
                 k_identity(lb[l].a, m, ls);
@@ -897,7 +928,7 @@ static void setup_solver(Solver& S) {
     for (int v : infos)
         if (v != 0) throw Err{SMPM_EBREAKDOWN, "singular strip slot, block-Jacobi or coarse matrix (getrf info " + std::to_string(v) + ")"};
     phase("coarse");
-    if (S.precision >= 1) {
+    if (S.precision == 1) {
         S.Minv32 = S.dalloc<float>((size_t)nop * S.nmc * S.sM, S.allocs);
         k_to_fp32(S.Minv32, S.Minv, (long long)nop * S.nmc * S.sM, st);
         // An FP32 copy of an ill-conditioned block inverse (large k^2 on fine
@@ -1782,7 +1813,14 @@ static int apply_impl(Solver& S, int kind, int R, const double* in, double* out)
         a.out = w.w; a.out_rs = ld; a.out_us = f2; a.out_off0 = -fz; a.out_off1 = f2; a.msplit = fz; a.add = w.z;
         run_gemm(S, a, w.tG, 1);
     } else if (kind == 1) {
-        a.mats = S.Minv; a.mat_stride = S.sM; a.M = f4; a.K = f4; a.row_lo = S.rl_M; a.row_hi = S.rh_M;
+        // precision 2 keeps only the FP32 block inverses
+        if (S.precision == 2) {
+            a.mats = reinterpret_cast<const double*>(S.Minv32);
+            a.fp32 = 1;
+        } else {
+            a.mats = S.Minv;
+        }
+        a.mat_stride = S.sM; a.M = f4; a.K = f4; a.row_lo = S.rl_M; a.row_hi = S.rh_M;
         a.in = w.z; a.in_rs = ld; a.in_us = f4; a.in_off = fz;
         a.out = w.w; a.out_rs = ld; a.out_us = f4; a.out_off0 = fz; a.msplit = f4;
         run_gemm(S, a, w.tM, 0);

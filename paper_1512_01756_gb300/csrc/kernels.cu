@@ -952,6 +952,31 @@ __global__ void to_fp32_kernel(float* dst, const double* src, long long n) {
     if (i < n) dst[i] = (float)src[i];
 }
 
+__global__ void identity_f_kernel(float* X, int m) {
+    const long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx >= (long long)m * m) return;
+    const long long i = idx / m, j = idx - i * m;
+    X[idx] = (i == j) ? 1.0f : 0.0f;
+}
+
+void k_identity_f(float* X, int m, cudaStream_t s) {
+    const long long tot = (long long)m * m;
+    identity_f_kernel<<<(unsigned)((tot + 255) / 256), 256, 0, s>>>(X, m);
+    count_launches(1);
+}
+
+__global__ void pad_block_f_kernel(float* __restrict__ dst, const float* __restrict__ src, int ms, int md) {
+    const int idx = blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx >= md * md) return;
+    const int i = idx / md, j = idx - i * md;
+    dst[idx] = (i < ms && j < ms) ? src[i * ms + j] : 0.0f;
+}
+
+void k_pad_block_f(float* dst, const float* src, int m_src, int m_dst, cudaStream_t s) {
+    pad_block_f_kernel<<<(m_dst * m_dst + 255) / 256, 256, 0, s>>>(dst, src, m_src, m_dst);
+    count_launches(1);
+}
+
 void k_to_fp32(float* dst, const double* src, long long n, cudaStream_t s) {
     if (n <= 0) return;
     to_fp32_kernel<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(dst, src, n);

@@ -120,6 +120,8 @@ void k_pad_block(double* dst, const double* src, int m_src, int m_dst, cudaStrea
 void k_build_rho(double* rho, const double* G, int fz, int ng, cudaStream_t s);
 void k_fill(double* x, long long n, double v, cudaStream_t s);
 void k_to_fp32(float* dst, const double* src, long long n, cudaStream_t s);
+void k_identity_f(float* X, int m, cudaStream_t s);
+void k_pad_block_f(float* dst, const float* src, int m_src, int m_dst, cudaStream_t s);
 
 // Fast strip solver pieces.
 struct FssArgs {
