@@ -36,7 +36,9 @@
  *   residuals on stderr; SMPM_NO_GRAPHS disables CUDA-graph replay of the
  *   Arnoldi steps; SMPM_TILE_SHAPE=0|1 forces a GEMM tile shape instead of
  *   the autotuned one; SMPM_REFINE_EXTENDED forces extra-precise refinement;
- *   SMPM_INNER_STEPS sets the inner steps of precision 2.
+ *   SMPM_INNER_STEPS sets the inner steps of precision 2; SMPM_NO_MIRROR
+ *   (read at setup) keeps the full-size products of the interior strips and
+ *   block-Jacobi pairs instead of their mirror-symmetric half-size form.
  */
 #ifndef SMPM_H
 #define SMPM_H

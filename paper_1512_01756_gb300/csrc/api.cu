@@ -127,6 +127,7 @@ struct Solver {
         const double** uSp = nullptr;
         const double** oneSp = nullptr;
         TileSet tM, tG, tW, tA, tS1, tS2;
+        TileSet tGb, tGm, tMb, tMm;       // boundary-class / mirror-form tiles
         double *fs1 = nullptr, *fs2 = nullptr, *fs3 = nullptr, *k2r = nullptr;
         double* Zb = nullptr;             // FGMRES preconditioned vectors [R][m][ld] (precision 1)
         std::vector<void*> allocs;
@@ -138,6 +139,12 @@ struct Solver {
     double setup_ms = 0.0;
     cusolverDnHandle_t sol = nullptr;
     int slot_cls[3] = {0, 1, 2};            // class whose slot inverses a class uses (mirror sharing)
+    // Mirror form of the interior Schur blocks and block-Jacobi pairs (uniform
+    // h_x): halves [Hp; Hm] per operator, FP64 and FP32 copies
+    bool mirG = false, mirM = false;
+    int mc_int = -1;                        // block class of the interior pairs
+    double *Gh = nullptr, *Mh = nullptr;
+    float *Gh32 = nullptr, *Mh32 = nullptr;
     // optional profiling of the class-GEMM launches (events + device flop counter)
     // CUDA graphs of the Arnoldi step groups (between two convergence checks),
     // keyed by (first step, steps, steps allowed in the cycle); valid for the
@@ -761,13 +768,11 @@ static void setup_solver(Solver& S) {
                 }
                 if (S.slot_cls[c] != c) {
                     k_mirror_blocks(G + c * S.sG, G + S.slot_cls[c] * S.sG, fz, 2, st);
-                    k_build_rho(S.rho + (size_t)o * S.sRho + (size_t)c * 2 * ng * f2, G + c * S.sG, fz, ng, st);
                     continue;
                 }
                 k_unit_faces(U, n, fz, st);
                 fss_single(S, o, c, f2, U, Y, T1, T2, tmp);
                 k_g_from_solves(G + c * S.sG, Y, S.d_beta + (size_t)c * 2 * n, n, fz, c, st);
-                k_build_rho(S.rho + (size_t)o * S.sRho + (size_t)c * 2 * ng * f2, G + c * S.sG, fz, ng, st);
             }
             continue;
         }
@@ -784,9 +789,44 @@ static void setup_solver(Solver& S) {
             invert_dense(S, dtmp, Ainv + c * S.sA, nfz, dwork, lwork, dipiv, dinfo);
             k_build_W(W + c * S.sW, Ainv + c * S.sA, dbeta + (size_t)c * 2 * n, n, fz, st);
             k_build_G(G + c * S.sG, W + c * S.sW, n, fz, c, st);
-            k_build_rho(S.rho + (size_t)o * S.sRho + (size_t)c * 2 * ng * f2, G + c * S.sG, fz, ng, st);
         }
     }
+    // Interior strips of a uniform-h_x grid are symmetric under the reflection
+    // of x about the strip centre, so G_1 = J G_1 J (J: the two faces swapped)
+    // up to the rounding of its solves.  Where the computed G_1 has that
+    // symmetry to 1e-11 relative (every operator), it is made exactly
+    // symmetric and the Schur product of the interior strips runs in the
+    // mirror form (half the FLOPs, kernels.cu); the boundary strips keep the
+    // full product.  The coarse row sums and the block-Jacobi pairs are built
+    // from the symmetric G_1, so every part of the method uses one operator.
+    S.mirG = S.mirM = false;
+    if (mx >= 3 && std::getenv("SMPM_NO_MIRROR") == nullptr) {
+        double* dres = S.dalloc<double>((size_t)2 * nop, tmp);
+        for (int o = 0; o < nop; ++o) k_mirror_asym(S.G + ((size_t)o * 3 + 1) * S.sG, fz, 2, dres + 2 * o, st);
+        std::vector<double> res((size_t)2 * nop);
+        CK(cudaMemcpyAsync(res.data(), dres, sizeof(double) * res.size(), cudaMemcpyDeviceToHost, st));
+        CK(cudaStreamSynchronize(st));
+        bool ok = true;
+        for (int o = 0; o < nop; ++o) ok = ok && res[2 * o] <= 1e-11 * res[2 * o + 1];
+        if (trace)
+            for (int o = 0; o < nop; ++o)
+                fprintf(stderr, "smpm setup: interior Schur block mirror asymmetry %.2e (op %d)\n",
+                        res[2 * o] / std::max(res[2 * o + 1], 1e-300), o);
+        if (ok) {
+            S.mirG = true;
+            const long long sh = (long long)fz * fz;
+            S.Gh = S.dalloc<double>((size_t)nop * 2 * sh, S.allocs);
+            for (int o = 0; o < nop; ++o) {
+                double* G1 = S.G + ((size_t)o * 3 + 1) * S.sG;
+                k_mirror_symmetrize(G1, fz, 2, st);
+                k_mirror_halves(S.Gh + (size_t)o * 2 * sh, G1, fz, 2, st);
+            }
+        }
+    }
+    for (int o = 0; o < nop; ++o)
+        for (int c = 0; c < 3; ++c)
+            k_build_rho(S.rho + (size_t)o * S.sRho + (size_t)c * 2 * ng * f2, S.G + ((size_t)o * 3 + c) * S.sG, fz, ng,
+                        st);
     phase("G");
 
     // phase 3: block-Jacobi pair blocks and their inverses (Sec. 3.2).  On a
@@ -851,6 +891,30 @@ static void setup_solver(Solver& S) {
         for (int o = 0; o < nop; ++o)
             k_mirror_blocks(S.Minv + ((size_t)o * S.nmc + mc_last) * S.sM, S.Minv + ((size_t)o * S.nmc + mc_first) * S.sM,
                             fz, 4, st);
+    // The interior pairs (strip classes 1, 1, 1) are built from the symmetric
+    // G_1, so their block is symmetric under the reversal of its four faces,
+    // and so is its inverse up to rounding: symmetrised, it runs in the
+    // mirror form too (FP32 copies for the mixed forms below).
+    S.mc_int = -1;
+    for (int mc = 0; mc < S.nmc; ++mc)
+        if (sig[mc] == std::array<int, 3>{1, 1, 1}) S.mc_int = mc;
+    if (S.mirG && S.mc_int >= 0 && !(S.P == 1)) {
+        const long long sh = 4LL * fz * fz;
+        if (m_fp32) {
+            S.Mh32 = S.dalloc<float>((size_t)nop * 2 * sh, S.allocs);
+            for (int o = 0; o < nop; ++o)
+                k_mirror_halves_f(S.Mh32 + (size_t)o * 2 * sh, S.Minv32 + ((size_t)o * S.nmc + S.mc_int) * S.sM, fz, 4,
+                                  st);
+        } else {
+            S.Mh = S.dalloc<double>((size_t)nop * 2 * sh, S.allocs);
+            for (int o = 0; o < nop; ++o) {
+                double* Mi = S.Minv + ((size_t)o * S.nmc + S.mc_int) * S.sM;
+                k_mirror_symmetrize(Mi, fz, 4, st);
+                k_mirror_halves(S.Mh + (size_t)o * 2 * sh, Mi, fz, 4, st);
+            }
+        }
+        S.mirM = true;
+    }
     phase("M_inverses");
 
     // phase 4: coarse matrix C = Z^T S Z from the row sums (host), then its
@@ -931,6 +995,10 @@ static void setup_solver(Solver& S) {
     if (S.precision == 1) {
         S.Minv32 = S.dalloc<float>((size_t)nop * S.nmc * S.sM, S.allocs);
         k_to_fp32(S.Minv32, S.Minv, (long long)nop * S.nmc * S.sM, st);
+        if (S.mirM) {
+            S.Mh32 = S.dalloc<float>((size_t)nop * 2 * 4 * fz * fz, S.allocs);
+            k_to_fp32(S.Mh32, S.Mh, (long long)nop * 2 * 4 * fz * fz, st);
+        }
         // An FP32 copy of an ill-conditioned block inverse (large k^2 on fine
         // grids) turns the preconditioner into noise: measure the FP32 apply's
         // relative error on a sign vector for every block, and keep the FP64
@@ -948,6 +1016,10 @@ static void setup_solver(Solver& S) {
     if (S.precision == 2) {
         S.G32 = S.dalloc<float>((size_t)nop * 3 * S.sG, S.allocs);
         k_to_fp32(S.G32, S.G, (long long)nop * 3 * S.sG, st);
+        if (S.mirG) {
+            S.Gh32 = S.dalloc<float>((size_t)nop * 2 * fz * fz, S.allocs);
+            k_to_fp32(S.Gh32, S.Gh, (long long)nop * 2 * fz * fz, st);
+        }
     }
     CK(cudaStreamSynchronize(st));
     S.free_list(tmp);
@@ -968,6 +1040,7 @@ static void ensure_workspace(Solver& S, int R) {
     S.bytes -= S.wk_bytes;
     S.free_list(S.wk.allocs);
     S.wk.tG = S.wk.tW = S.wk.tA = S.wk.tM = S.wk.tS1 = S.wk.tS2 = TileSet();
+    S.wk.tGb = S.wk.tGm = S.wk.tMb = S.wk.tMm = TileSet();
     const long long bytes_before = S.bytes;
     auto& w = S.wk;
     auto& L = w.allocs;
@@ -1051,6 +1124,7 @@ static void ensure_workspace(Solver& S, int R) {
     w.oneSp = (const double**)S.dalloc<double*>(R, L);
     // tile lists sized for the worst case (every rhs its own op): units * R
     w.tG = w.tW = w.tA = w.tM = w.tS1 = w.tS2 = TileSet();   // built by prepare_ops
+    w.tGb = w.tGm = w.tMb = w.tMm = TileSet();
     CK(cudaStreamSynchronize(S.stream));
     S.wk_bytes = S.bytes - bytes_before;
     S.Rcap = R;
@@ -1068,7 +1142,7 @@ static std::vector<Tile> make_tiles(const std::vector<int>& unit_cls, int ncls, 
         while (ub < nu) {
             int ue = ub;
             while (ue < nu && unit_cls[ue] == unit_cls[ub]) ++ue;
-            for (int rr = rb; rr < re;) {
+            for (int rr = rb; rr < re && unit_cls[ub] >= 0;) {   // class -1: units left out
                 const int nr = std::min(bn, re - rr);
                 const int upt = std::max(1, bn / nr);
                 for (int u = ub; u < ue; u += upt)
@@ -1149,6 +1223,21 @@ static void prepare_ops(Solver& S, const std::vector<int>& ops) {
         upload_tiles(S, w.tA, sh, keep.back());
         keep.push_back(make_tiles(S.pair_mc, S.nmc, ops, bn));
         upload_tiles(S, w.tM, sh, keep.back());
+        // mirror form: interior units in one list (matrix index = operator),
+        // the other classes in another
+        auto split = [&](const std::vector<int>& cls, int ncls, int mc, TileSet& tb, TileSet& tm) {
+            std::vector<int> cb(cls), cm(cls);
+            for (size_t u = 0; u < cls.size(); ++u) {
+                cb[u] = cls[u] == mc ? -1 : cls[u];
+                cm[u] = cls[u] == mc ? 0 : -1;
+            }
+            keep.push_back(make_tiles(cb, ncls, ops, bn));
+            upload_tiles(S, tb, sh, keep.back());
+            keep.push_back(make_tiles(cm, 1, ops, bn));
+            upload_tiles(S, tm, sh, keep.back());
+        };
+        if (S.mirG) split(S.strip_cls, 3, 1, w.tGb, w.tGm);
+        if (S.mirM) split(S.pair_mc, S.nmc, S.mc_int, w.tMb, w.tMm);
     }
     const int R = (int)ops.size();
     std::vector<const double*> uLp(R, nullptr), uSp(R, nullptr), oneSp(R, nullptr);
@@ -1206,7 +1295,7 @@ static constexpr int kEventPairs = 8192;
 // stands), timed with CUDA events, and the faster shape is kept for that key
 // for the rest of the process (all handles, all threads).
 static std::mutex g_tune_mu;
-static std::map<std::array<int, 6>, int> g_tune;
+static std::map<std::array<int, 7>, int> g_tune;
 
 static int tune_shape(Solver& S, GemmArgs& a, const TileSet& ts, int epi, bool& launched) {
     launched = false;
@@ -1215,7 +1304,7 @@ static int tune_shape(Solver& S, GemmArgs& a, const TileSet& ts, int epi, bool& 
     cudaGetDevice(&dev);
     int bucket = 0;
     while ((1 << (bucket + 1)) <= ts.n[0]) ++bucket;
-    const std::array<int, 6> key{dev, epi, a.fp32, a.M, a.K, bucket};
+    const std::array<int, 7> key{dev, epi, a.fp32, a.M, a.K, bucket, a.mirror_nb};
     {
         std::lock_guard<std::mutex> lk(g_tune_mu);
         auto it = g_tune.find(key);
@@ -1291,6 +1380,55 @@ static void harvest_profile(Solver& S) {
     CK(cudaMemcpy(&fl, S.d_flops, sizeof(fl), cudaMemcpyDeviceToHost));
     S.prof_flops += (double)fl;
     CK(cudaMemset(S.d_flops, 0, sizeof(fl)));
+}
+
+// Schur product out = add + sum_i scatter_i G_i gather_i in (Sec. 3.1,
+// assembled blocks) with the FP64 blocks or their FP32 copies; the interior
+// strips go through the mirror form when the handle has it.
+static void schur_product(Solver& S, const double* in, long long in_rs, long long in_off, double* out,
+                          const double* add, const int* active, bool fp32) {
+    const int fz = S.g.fz, f2 = 2 * fz;
+    GemmArgs a = gemm_base(S);
+    a.mats = fp32 ? reinterpret_cast<const double*>(S.G32) : S.G;
+    a.fp32 = fp32 ? 1 : 0;
+    a.mat_stride = S.sG; a.M = f2; a.K = f2;
+    a.row_lo = S.rl_GW; a.row_hi = S.rh_GW;
+    a.in = in; a.in_rs = in_rs; a.in_us = f2; a.in_off = in_off;
+    a.out = out; a.out_rs = S.ld; a.out_us = f2; a.out_off0 = -fz; a.out_off1 = f2; a.msplit = fz;
+    a.add = add;
+    a.active = active;
+    const double* h = fp32 ? reinterpret_cast<const double*>(S.Gh32) : S.Gh;
+    if (!S.mirG || h == nullptr) {
+        run_gemm(S, a, S.wk.tG, 1);
+        return;
+    }
+    run_gemm(S, a, S.wk.tGb, 1);
+    a.mats = h; a.mat_stride = 2LL * fz * fz; a.M = a.K = fz; a.mirror_nb = 2; a.face = fz;
+    run_gemm(S, a, S.wk.tGm, 1);
+}
+
+// Block-Jacobi apply out = M_p^-1 in over the pairs p (faces [(4p+1) fz,
+// (4p+5) fz), Sec. 3.2); the interior pairs through the mirror form when the
+// handle has it.
+static void bj_apply(Solver& S, const double* in, long long in_rs, long long in_off, double* out, long long out_rs,
+                     long long out_off, const int* active, bool fp32) {
+    const int fz = S.g.fz, f4 = 4 * fz;
+    GemmArgs a = gemm_base(S);
+    a.mats = fp32 ? reinterpret_cast<const double*>(S.Minv32) : S.Minv;
+    a.fp32 = fp32 ? 1 : 0;
+    a.mat_stride = S.sM; a.M = f4; a.K = f4;
+    a.row_lo = S.rl_M; a.row_hi = S.rh_M;
+    a.in = in; a.in_rs = in_rs; a.in_us = f4; a.in_off = in_off + fz;
+    a.out = out; a.out_rs = out_rs; a.out_us = f4; a.out_off0 = out_off + fz; a.out_off1 = 0; a.msplit = f4;
+    a.active = active;
+    const double* h = fp32 ? reinterpret_cast<const double*>(S.Mh32) : S.Mh;
+    if (!S.mirM || h == nullptr) {
+        run_gemm(S, a, S.wk.tM, 0);
+        return;
+    }
+    run_gemm(S, a, S.wk.tMb, 0);
+    a.mats = h; a.mat_stride = 8LL * fz * fz; a.M = a.K = 2 * fz; a.mirror_nb = 4; a.face = fz;
+    run_gemm(S, a, S.wk.tMm, 0);
 }
 
 static int solve_impl(Solver& S, const std::vector<int>& ops, const double* f, const double* gb, double tol,
@@ -1402,38 +1540,16 @@ static int solve_impl(Solver& S, const std::vector<int>& ops, const double* f, c
     // block-Jacobi apply: out = Minv_p in over pairs p (faces [(4p+1) fz, (4p+5) fz))
     auto bj = [&](const double* in, long long in_rs, long long in_off, double* out, long long out_rs,
                   long long out_off, const int* active, bool fp32 = false) {
-        GemmArgs a = gemm_base(S);
-        a.mats = fp32 ? reinterpret_cast<const double*>(S.Minv32) : S.Minv;
-        a.fp32 = fp32 ? 1 : 0;
-        a.mat_stride = S.sM; a.M = f4; a.K = f4;
-        a.row_lo = S.rl_M; a.row_hi = S.rh_M;
-        a.in = in; a.in_rs = in_rs; a.in_us = f4; a.in_off = in_off + fz;
-        a.out = out; a.out_rs = out_rs; a.out_us = f4; a.out_off0 = out_off + fz; a.out_off1 = 0; a.msplit = f4;
-        a.active = active;
-        run_gemm(S, a, w.tM, 0);
+        bj_apply(S, in, in_rs, in_off, out, out_rs, out_off, active, fp32);
     };
     // Schur product: out = in + sum_i scatter_i G_i gather_i in
+    // (identity term from the same layout when in_rs == ld and in_off == 0)
     auto schur = [&](const double* in, long long in_rs, long long in_off, double* out, const int* active) {
-        GemmArgs a = gemm_base(S);
-        a.mats = S.G; a.mat_stride = S.sG; a.M = f2; a.K = f2;
-        a.row_lo = S.rl_GW; a.row_hi = S.rh_GW;
-        a.in = in; a.in_rs = in_rs; a.in_us = f2; a.in_off = in_off;
-        a.out = out; a.out_rs = ld; a.out_us = f2; a.out_off0 = -fz; a.out_off1 = f2; a.msplit = fz;
-        a.add = in;  // identity term, same layout when in_rs == ld and in_off == 0
-        a.active = active;
-        run_gemm(S, a, w.tG, 1);
+        schur_product(S, in, in_rs, in_off, out, in, active, false);
     };
     // FP32 Schur product of the inner solve (FP32 blocks and accumulation)
     auto schur32 = [&](const double* in, double* out, const int* active) {
-        GemmArgs a = gemm_base(S);
-        a.mats = reinterpret_cast<const double*>(S.G32); a.fp32 = 1;
-        a.mat_stride = S.sG; a.M = f2; a.K = f2;
-        a.row_lo = S.rl_GW; a.row_hi = S.rh_GW;
-        a.in = in; a.in_rs = ld; a.in_us = f2; a.in_off = 0;
-        a.out = out; a.out_rs = ld; a.out_us = f2; a.out_off0 = -fz; a.out_off1 = f2; a.msplit = fz;
-        a.add = in;
-        a.active = active;
-        run_gemm(S, a, w.tG, 1);
+        schur_product(S, in, ld, 0, out, in, active, true);
     };
     // z = inner solve of S z = V_j for the active right-hand sides (one
     // deflated right-preconditioned GMRES cycle from z = 0, Alg. seq steps
@@ -1808,22 +1924,10 @@ static int apply_impl(Solver& S, int kind, int R, const double* in, double* out)
     GemmArgs a;
     std::memset(&a, 0, sizeof(a));
     if (kind == 0) {
-        a.mats = S.G; a.mat_stride = S.sG; a.M = f2; a.K = f2; a.row_lo = S.rl_GW; a.row_hi = S.rh_GW;
-        a.in = w.z; a.in_rs = ld; a.in_us = f2; a.in_off = 0;
-        a.out = w.w; a.out_rs = ld; a.out_us = f2; a.out_off0 = -fz; a.out_off1 = f2; a.msplit = fz; a.add = w.z;
-        run_gemm(S, a, w.tG, 1);
+        schur_product(S, w.z, ld, 0, w.w, w.z, nullptr, false);
     } else if (kind == 1) {
         // precision 2 keeps only the FP32 block inverses
-        if (S.precision == 2) {
-            a.mats = reinterpret_cast<const double*>(S.Minv32);
-            a.fp32 = 1;
-        } else {
-            a.mats = S.Minv;
-        }
-        a.mat_stride = S.sM; a.M = f4; a.K = f4; a.row_lo = S.rl_M; a.row_hi = S.rh_M;
-        a.in = w.z; a.in_rs = ld; a.in_us = f4; a.in_off = fz;
-        a.out = w.w; a.out_rs = ld; a.out_us = f4; a.out_off0 = fz; a.msplit = f4;
-        run_gemm(S, a, w.tM, 0);
+        bj_apply(S, w.z, ld, 0, w.w, ld, 0, nullptr, S.precision == 2);
     } else if (kind == 2) {
         KArgs ka;
         std::memset(&ka, 0, sizeof(ka));

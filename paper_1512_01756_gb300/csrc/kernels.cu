@@ -172,9 +172,147 @@ __global__ void __launch_bounds__(GT) class_gemm_kernel(GemmArgs a, const Tile* 
     }
 }
 
+// ---------------------------------------------------------------------------
+// Mirror form of the class GEMM.  With uniform h_x an interior strip, and an
+// interior block-Jacobi pair, is symmetric under the reflection of x about its
+// centre: with J the reversal of the order of the nb faces of a column (each
+// face of fz values keeps its z order), the class matrix has J Mat J = Mat.
+// Let h = nb fz / 2, v1 the first half of a column and v2' = (J v)[0:h] the
+// reflected second half, X = Mat[0:h, 0:h] and N[i][j] = Mat[i][mirror(j)].
+// Then (Mat v)[0:h] = X v1 + N v2' and (Mat v)[mirror(i)] = (N v1 + X v2')[i],
+// so with s = v1 + v2', d = v1 - v2' and Hp, Hm = (X +- N) / 2:
+//     out[i] = (Hp s + Hm d)[i],   out[mirror(i)] = (Hp s - Hm d)[i],
+// two h x h products instead of one 2h x 2h product: half the FLOPs.  mats
+// holds [Hp; Hm] per matrix, M = K = h, nb = 2 (Schur blocks G, one face per
+// half) or 4 (block-Jacobi pairs).  The output addressing (msplit, out_off0/1)
+// and the epilogues (EPI 0 store, EPI 1 add) are those of class_gemm_kernel.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ int mirror_index(int i, int fz, int rev) {
+    return rev + i - (i >= fz ? 2 * fz : 0);   // (nb - 1 - i / fz) fz + i % fz for i < 2 fz
+}
+
+template <int EPI, typename TM, int BMT>
+__global__ void __launch_bounds__(GT) mirror_gemm_kernel(GemmArgs a, const Tile* __restrict__ tiles) {
+    constexpr int BNT = 4 * GT / BMT;
+    constexpr int CG = GT / BMT;
+    const Tile t = tiles[blockIdx.x];
+    const int row0 = blockIdx.y * BMT;
+    const int h = a.M;
+    if (row0 >= h) return;
+    if (a.active) {
+        int any = 0;
+        for (int c = 0; c < t.nr; ++c) any |= a.active[t.r0 + c];
+        if (!any) return;
+    }
+    const int ncol = t.nu * t.nr;
+    if (a.flops && threadIdx.x == 0) {
+        int cols = 0;
+        for (int c = 0; c < ncol; ++c) cols += (a.active == nullptr || a.active[t.r0 + c % t.nr]) ? 1 : 0;
+        const int rows = min(h, row0 + BMT) - row0;
+        atomicAdd(a.flops, 4ULL * (unsigned long long)rows * (unsigned long long)h * (unsigned long long)cols);
+    }
+    __shared__ TM Ap[BK][BMT + 1], Am[BK][BMT + 1];
+    __shared__ __align__(16) TM Bp[BK][BNT + 4], Bm[BK][BNT + 4];
+    const TM* __restrict__ Hp = reinterpret_cast<const TM*>(a.mats) + (long long)t.mat * a.mat_stride;
+    const TM* __restrict__ Hm = Hp + (long long)h * h;
+    const int fz = a.face, rev = (a.mirror_nb - 1) * a.face;
+    const int tid = threadIdx.x;
+    const int tr = tid / CG, tc = tid % CG;
+    TM accp[4] = {TM(0), TM(0), TM(0), TM(0)};
+    TM accm[4] = {TM(0), TM(0), TM(0), TM(0)};
+
+    const double* colp[(BNT * BK) / GT];
+#pragma unroll
+    for (int l = 0; l < (BNT * BK) / GT; ++l) {
+        const int e = tid + l * GT, c = e >> 4;
+        colp[l] = nullptr;
+        if (c < ncol) {
+            const int u = t.u0 + c / t.nr, r = t.r0 + c % t.nr;
+            colp[l] = a.in + (long long)r * a.in_rs + (long long)u * a.in_us + a.in_off + t.off;
+        }
+    }
+    for (int k0 = 0; k0 < h; k0 += BK) {
+        for (int e = tid; e < BMT * BK; e += GT) {
+            const int i = e >> 4, kk = e & 15;
+            const int row = row0 + i, k = k0 + kk;
+            const bool ok = row < h && k < h;
+            Ap[kk][i] = ok ? Hp[(long long)row * h + k] : TM(0);
+            Am[kk][i] = ok ? Hm[(long long)row * h + k] : TM(0);
+        }
+#pragma unroll
+        for (int l = 0; l < (BNT * BK) / GT; ++l) {
+            const int e = tid + l * GT, c = e >> 4, kk = e & 15;
+            const int k = k0 + kk;
+            TM sp = TM(0), sm = TM(0);
+            if (colp[l] != nullptr && k < h) {
+                const double v1 = colp[l][k], v2 = colp[l][mirror_index(k, fz, rev)];
+                sp = TM(v1 + v2);
+                sm = TM(v1 - v2);
+            }
+            Bp[kk][c] = sp;
+            Bm[kk][c] = sm;
+        }
+        __syncthreads();
+        if (k0 + BK <= h) {
+#pragma unroll
+            for (int kk = 0; kk < BK; ++kk) {
+                const TM ap = Ap[kk][tr], am = Am[kk][tr];
+#pragma unroll
+                for (int j = 0; j < 4; ++j) {
+                    accp[j] = fma(ap, Bp[kk][tc * 4 + j], accp[j]);
+                    accm[j] = fma(am, Bm[kk][tc * 4 + j], accm[j]);
+                }
+            }
+        } else {   // last, partial slab
+            const int kn = h - k0;
+            for (int kk = 0; kk < kn; ++kk) {
+                const TM ap = Ap[kk][tr], am = Am[kk][tr];
+#pragma unroll
+                for (int j = 0; j < 4; ++j) {
+                    accp[j] = fma(ap, Bp[kk][tc * 4 + j], accp[j]);
+                    accm[j] = fma(am, Bm[kk][tc * 4 + j], accm[j]);
+                }
+            }
+        }
+        __syncthreads();
+    }
+    const int row = row0 + tr;
+    if (row >= h) return;
+    const int mrow = mirror_index(row, fz, rev);
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+        const int c = tc * 4 + j;
+        if (c >= ncol) continue;
+        const int u = t.u0 + c / t.nr, r = t.r0 + c % t.nr;
+        if (a.active && !a.active[r]) continue;
+        const long long base = (long long)r * a.out_rs + (long long)u * a.out_us + t.off;
+        const long long a1 = base + (row < a.msplit ? a.out_off0 + row : a.out_off1 + (row - a.msplit));
+        const long long a2 = base + (mrow < a.msplit ? a.out_off0 + mrow : a.out_off1 + (mrow - a.msplit));
+        double y1 = (double)accp[j] + (double)accm[j];
+        double y2 = (double)accp[j] - (double)accm[j];
+        if (EPI == 1) {
+            y1 += a.add[a1];
+            y2 += a.add[a2];
+        }
+        a.out[a1] = y1;
+        a.out[a2] = y2;
+    }
+}
+
 template <int BMT>
 static void launch_shape(const GemmArgs& a, const Tile* d_tiles, int ntiles, int epi, cudaStream_t s) {
     dim3 grid(ntiles, (a.M + BMT - 1) / BMT);
+    if (a.mirror_nb > 0) {
+        if (a.fp32 && epi == 1)
+            mirror_gemm_kernel<1, float, BMT><<<grid, GT, 0, s>>>(a, d_tiles);
+        else if (a.fp32)
+            mirror_gemm_kernel<0, float, BMT><<<grid, GT, 0, s>>>(a, d_tiles);
+        else if (epi == 1)
+            mirror_gemm_kernel<1, double, BMT><<<grid, GT, 0, s>>>(a, d_tiles);
+        else
+            mirror_gemm_kernel<0, double, BMT><<<grid, GT, 0, s>>>(a, d_tiles);
+        return;
+    }
     if (a.fp32 && epi == 1)
         class_gemm_kernel<1, float, BMT><<<grid, GT, 0, s>>>(a, d_tiles);
     else if (a.fp32)
@@ -1309,6 +1447,90 @@ __global__ void mirror_blocks_kernel(double* __restrict__ dst, const double* __r
 void k_mirror_blocks(double* dst, const double* src, int fz, int nb, cudaStream_t s) {
     const long long tot = (long long)nb * fz * nb * fz;
     mirror_blocks_kernel<<<(unsigned)((tot + 255) / 256), 256, 0, s>>>(dst, src, fz, nb);
+    count_launches(1);
+}
+
+// mirror(i) over the full column of nb faces
+__device__ __forceinline__ long long mirror_full(long long i, int fz, int nb) {
+    return (nb - 1 - i / fz) * fz + i % fz;
+}
+
+__global__ void mirror_asym_kernel(const double* __restrict__ Mat, int fz, int nb, double* res) {
+    __shared__ double sh[2][32];
+    const long long m = (long long)nb * fz;
+    double dmax = 0.0, amax = 0.0;
+    for (long long idx = threadIdx.x; idx < m * m; idx += blockDim.x) {
+        const long long i = idx / m, j = idx - i * m;
+        const double v = Mat[idx];
+        dmax = fmax(dmax, fabs(v - Mat[mirror_full(i, fz, nb) * m + mirror_full(j, fz, nb)]));
+        amax = fmax(amax, fabs(v));
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        dmax = fmax(dmax, __shfl_xor_sync(0xffffffffu, dmax, o));
+        amax = fmax(amax, __shfl_xor_sync(0xffffffffu, amax, o));
+    }
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    if (lane == 0) {
+        sh[0][wid] = dmax;
+        sh[1][wid] = amax;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        for (int w = 1; w < (int)(blockDim.x >> 5); ++w) {
+            dmax = fmax(dmax, sh[0][w]);
+            amax = fmax(amax, sh[1][w]);
+        }
+        res[0] = dmax;
+        res[1] = amax;
+    }
+}
+
+void k_mirror_asym(const double* Mat, int fz, int nb, double* res, cudaStream_t s) {
+    mirror_asym_kernel<<<1, 1024, 0, s>>>(Mat, fz, nb, res);
+    count_launches(1);
+}
+
+// Each element pair (idx, mirror of idx) is averaged by the thread of the
+// smaller index (the two never coincide for even nb).
+__global__ void mirror_symmetrize_kernel(double* __restrict__ Mat, int fz, int nb) {
+    const long long m = (long long)nb * fz;
+    const long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx >= m * m) return;
+    const long long i = idx / m, j = idx - i * m;
+    const long long p = mirror_full(i, fz, nb) * m + mirror_full(j, fz, nb);
+    if (p <= idx) return;
+    const double v = 0.5 * (Mat[idx] + Mat[p]);
+    Mat[idx] = v;
+    Mat[p] = v;
+}
+
+void k_mirror_symmetrize(double* Mat, int fz, int nb, cudaStream_t s) {
+    const long long tot = (long long)nb * fz * nb * fz;
+    mirror_symmetrize_kernel<<<(unsigned)((tot + 255) / 256), 256, 0, s>>>(Mat, fz, nb);
+    count_launches(1);
+}
+
+template <typename T>
+__global__ void mirror_halves_kernel(T* __restrict__ H, const T* __restrict__ Mat, int fz, int nb) {
+    const long long m = (long long)nb * fz, h = m / 2;
+    const long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx >= h * h) return;
+    const long long i = idx / h, j = idx - i * h;
+    const T x = Mat[i * m + j], y = Mat[i * m + mirror_full(j, fz, nb)];
+    H[idx] = T(0.5) * (x + y);
+    H[h * h + idx] = T(0.5) * (x - y);
+}
+
+void k_mirror_halves(double* H, const double* Mat, int fz, int nb, cudaStream_t s) {
+    const long long h = (long long)nb * fz / 2;
+    mirror_halves_kernel<double><<<(unsigned)((h * h + 255) / 256), 256, 0, s>>>(H, Mat, fz, nb);
+    count_launches(1);
+}
+
+void k_mirror_halves_f(float* H, const float* Mat, int fz, int nb, cudaStream_t s) {
+    const long long h = (long long)nb * fz / 2;
+    mirror_halves_kernel<float><<<(unsigned)((h * h + 255) / 256), 256, 0, s>>>(H, Mat, fz, nb);
     count_launches(1);
 }
 

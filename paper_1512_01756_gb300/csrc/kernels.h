@@ -106,6 +106,15 @@ void k_dft_forward(const double* in, double* out, const double* cs, long long n,
 void k_dft_inverse(const double* in, double* out, const double* cs, long long n, int my, cudaStream_t s);
 // dst = P src P, P reversing the nb face blocks of an (nb fz)^2 matrix (mirror image)
 void k_mirror_blocks(double* dst, const double* src, int fz, int nb, cudaStream_t s);
+// Mirror symmetry of a class matrix (nb = 2 or 4 faces of fz values, J the
+// reversal of the face order): res[0] = max |Mat - J Mat J|, res[1] = max |Mat|.
+void k_mirror_asym(const double* Mat, int fz, int nb, double* res, cudaStream_t s);
+// Mat <- (Mat + J Mat J) / 2 in place.
+void k_mirror_symmetrize(double* Mat, int fz, int nb, cudaStream_t s);
+// The two h x h halves of the mirror form, H = [Hp; Hm] (h = nb fz / 2):
+// Hp, Hm = (Mat[i][j] +- Mat[i][mirror(j)]) / 2 for i, j < h.
+void k_mirror_halves(double* H, const double* Mat, int fz, int nb, cudaStream_t s);
+void k_mirror_halves_f(float* H, const float* Mat, int fz, int nb, cudaStream_t s);
 // done[r] = active[r] ? 0 : 1 for r < R
 void k_invert_flags(int* done, const int* active, int R, cudaStream_t s);
 // K <- K - (K u) u^T (row-major d x d, w: d scratch): the projected coarse division

@@ -97,3 +97,29 @@ def test_strip_assembled_S_matches_dense():
     fz2 = 2 * g.fz
     Sc = sch.S.tocoo()
     assert np.all(np.abs(Sc.row // fz2 - Sc.col // fz2) <= 1)
+
+
+@pytest.mark.parametrize("shape,k2", [((6, 2, 5, 3.0, 1.0, 1.0), 2.5), ((5, 3, 4, 1.0, 1.0, 1.2), 0.0)])
+def test_schur_commutes_with_x_reflection(shape, k2):
+    """With uniform h_x the domain is symmetric under x -> l_x - x, which maps
+    interface j to m_x - 2 - j and swaps the two sides of every interface
+    (each side keeps its z order); the assembled S commutes with that
+    permutation.  This is the symmetry the library's mirror-form products of
+    the interior strips and block-Jacobi pairs rest on (Sec. 3.1, Sec. 3.2)."""
+    mx, mz, order, lx, lz, zr = shape
+    g = Grid(mx, mz, order, lx, lz, z_ratio=zr)
+    S = schur_dense(g, assemble_L(g, k2))[0]
+    fz = g.fz
+
+    def mirror(i):
+        j, rem = divmod(i, 2 * fz)
+        s, z = divmod(rem, fz)
+        return (g.mx - 2 - j) * 2 * fz + (1 - s) * fz + z
+
+    P = np.array([mirror(i) for i in range(g.k)])
+    assert sorted(P) == list(range(g.k))
+    assert np.abs(S[np.ix_(P, P)] - S).max() < 1e-12 * np.abs(S).max()
+    # and it is not a symmetry of the stretched z direction's reversal
+    if zr != 1.0:
+        Q = np.array([(i // fz) * fz + (fz - 1 - i % fz) for i in range(g.k)])
+        assert np.abs(S[np.ix_(Q, Q)] - S).max() > 1e-3 * np.abs(S).max()
