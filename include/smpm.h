@@ -36,9 +36,10 @@
  *   residuals on stderr; SMPM_NO_GRAPHS disables CUDA-graph replay of the
  *   Arnoldi steps; SMPM_TILE_SHAPE=0|1 forces a GEMM tile shape instead of
  *   the autotuned one; SMPM_REFINE_EXTENDED forces extra-precise refinement;
- *   SMPM_INNER_STEPS sets the inner steps of precision 2; SMPM_NO_MIRROR
- *   (read at setup) keeps the full-size products of the interior strips and
- *   block-Jacobi pairs instead of their mirror-symmetric half-size form.
+ *   SMPM_INNER_STEPS sets the inner steps of precision 2; SMPM_MIRROR=0|1
+ *   (read at setup) turns the mirror-symmetric half-size products of the
+ *   interior strips, block-Jacobi pairs and slot inverses off, or on at every
+ *   batch size (by default S and M^-1 use them where they save enough work).
  */
 #ifndef SMPM_H
 #define SMPM_H

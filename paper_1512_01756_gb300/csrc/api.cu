@@ -83,6 +83,8 @@ struct Solver {
     std::vector<int> sl_start[3], sl_size[3], sl_idx[3];             // per class: slot start, size, index in its size list
     int ns1 = 0, ns2 = 0;                                            // max size-1 / size-2 slots over the classes
     double *S1 = nullptr, *S2 = nullptr;                             // slot inverses [nop][3][ns][m*m]
+    bool zmir = false;                                               // slots in the z-mirror form
+    double *S1h = nullptr, *S2h = nullptr;                           // their halves [nop][3][ns][2][(m/2)^2]
     int *rl_S1 = nullptr, *rh_S1 = nullptr, *rl_S2 = nullptr, *rh_S2 = nullptr;
     int* d_cls3 = nullptr;                                           // {0, 1, 2}
     double *d_Ax3 = nullptr, *d_Lz = nullptr;                        // x-factors [3][n][n], z-operator [fz][fz]
@@ -141,7 +143,9 @@ struct Solver {
     int slot_cls[3] = {0, 1, 2};            // class whose slot inverses a class uses (mirror sharing)
     // Mirror form of the interior Schur blocks and block-Jacobi pairs (uniform
     // h_x): halves [Hp; Hm] per operator, FP64 and FP32 copies
-    bool mirG = false, mirM = false;
+    bool mirG = false, mirM = false;        // halves built
+    bool useG = false, useM = false;        // used by the current batch (prepare_ops)
+    int mirror_mode = 2;                    // SMPM_MIRROR at setup: 0 off, 1 always, 2 by size
     int mc_int = -1;                        // block class of the interior pairs
     double *Gh = nullptr, *Mh = nullptr;
     float *Gh32 = nullptr, *Mh32 = nullptr;
@@ -250,6 +254,14 @@ static void fss_run(Solver& S, const FssArgs& fa, int R, const double* in, long 
         a.row_hi = sz == 1 ? S.rh_S1 : S.rh_S2;
         a.in = t1; a.in_rs = ld; a.in_us = nfz; a.in_off = 0;
         a.out = t2; a.out_rs = ld; a.out_us = nfz; a.out_off0 = 0; a.out_off1 = 0; a.msplit = sz * fz;
+        if (S.zmir) {   // z-mirror form of the slot products
+            const int h = sz * fz / 2;
+            a.mats = sz == 1 ? S.S1h : S.S2h;
+            a.mat_stride = 2LL * h * h;
+            a.M = a.K = h;
+            a.mirror_nb = -sz;
+            a.face = fz;
+        }
         run_gemm(S, a, sz == 1 ? tS1 : tS2, 0);
     }
     k_xform(fa, R, S.d_Q, t2, ld, out, out_ld, nullptr, 0, S.stream, accumulate ? out : nullptr, out_ld);
@@ -367,6 +379,7 @@ static void setup_solver(Solver& S) {
     auto t0 = std::chrono::steady_clock::now();
     // SMPM_TRACE_SETUP=1: per-phase wall times of the setup on stderr
     const bool trace = std::getenv("SMPM_TRACE_SETUP") != nullptr;
+    if (const char* e = std::getenv("SMPM_MIRROR")) S.mirror_mode = std::atoi(e) == 0 ? 0 : 1;
     auto tp = t0;
     std::string trace_line;
     auto phase = [&](const char* name) {
@@ -743,6 +756,30 @@ static void setup_solver(Solver& S) {
                 }
             }
         join();
+        // With uniform h_z (and the same Neumann condition at the bottom and
+        // the top) L_z commutes with the reversal of the z-nodes, and so does
+        // every slot inverse (L_z + s I)^-1 and its 2 x 2 block form: the slot
+        // products run in the mirror form (half the FLOPs).  The halves are
+        // taken from the computed inverses; the refinement step of every fast
+        // solve uses the exact operator, so their rounding-level asymmetry
+        // does not reach a result.
+        S.zmir = false;
+        if (fz % 2 == 0 && S.mirror_mode != 0) {
+            double diff = 0.0, amax = 0.0;
+            for (int i = 0; i < fz; ++i)
+                for (int j = 0; j < fz; ++j) {
+                    amax = std::max(amax, std::fabs(Lz[(size_t)i * fz + j]));
+                    diff = std::max(diff, std::fabs(Lz[(size_t)(fz - 1 - i) * fz + (fz - 1 - j)] - Lz[(size_t)i * fz + j]));
+                }
+            S.zmir = diff <= 1e-13 * amax;
+        }
+        if (S.zmir) {
+            const long long c1 = (long long)nop * 3 * std::max(S.ns1, 1), c2 = (long long)nop * 3 * std::max(S.ns2, 1);
+            S.S1h = S.dalloc<double>((size_t)c1 * fz * fz / 2, S.allocs);
+            S.S2h = S.dalloc<double>((size_t)c2 * 2 * fz * fz, S.allocs);
+            k_mirror_halves_nodes(S.S1h, S.S1, c1, fz, 1, st);
+            k_mirror_halves_nodes(S.S2h, S.S2, c2, fz, 2, st);
+        }
         phase("slot_inverses");
     }
 
@@ -800,7 +837,7 @@ static void setup_solver(Solver& S) {
     // full product.  The coarse row sums and the block-Jacobi pairs are built
     // from the symmetric G_1, so every part of the method uses one operator.
     S.mirG = S.mirM = false;
-    if (mx >= 3 && std::getenv("SMPM_NO_MIRROR") == nullptr) {
+    if (mx >= 3 && S.mirror_mode != 0) {
         double* dres = S.dalloc<double>((size_t)2 * nop, tmp);
         for (int o = 0; o < nop; ++o) k_mirror_asym(S.G + ((size_t)o * 3 + 1) * S.sG, fz, 2, dres + 2 * o, st);
         std::vector<double> res((size_t)2 * nop);
@@ -1239,6 +1276,19 @@ static void prepare_ops(Solver& S, const std::vector<int>& ops) {
         if (S.mirG) split(S.strip_cls, 3, 1, w.tGb, w.tGm);
         if (S.mirM) split(S.pair_mc, S.nmc, S.mc_int, w.tMb, w.tMm);
     }
+    // The mirror form of S and M^-1 adds a launch for the boundary classes
+    // (~10 us); it pays where it saves more than ~25 MFLOP per product
+    // (256x4 order 12: 0.43 vs 0.59 ms for S x at 128 right-hand sides; an
+    // 8x2 order-8 single solve: 1.06 vs 0.86 ms).
+    {
+        const double fz2 = (double)S.g.fz * S.g.fz, R = (double)ops.size();
+        const double saveG = (double)(S.g.mx - 2) * R * 4.0 * fz2;
+        int npi = 0;
+        for (int mc : S.pair_mc) npi += mc == S.mc_int ? 1 : 0;
+        const double saveM = (double)npi * R * 16.0 * fz2;
+        S.useG = S.mirG && (S.mirror_mode == 1 || saveG >= 2.5e7);
+        S.useM = S.mirM && (S.mirror_mode == 1 || saveM >= 2.5e7);
+    }
     const int R = (int)ops.size();
     std::vector<const double*> uLp(R, nullptr), uSp(R, nullptr), oneSp(R, nullptr);
     std::vector<int> gauge(R, 0);
@@ -1398,7 +1448,7 @@ static void schur_product(Solver& S, const double* in, long long in_rs, long lon
     a.add = add;
     a.active = active;
     const double* h = fp32 ? reinterpret_cast<const double*>(S.Gh32) : S.Gh;
-    if (!S.mirG || h == nullptr) {
+    if (!S.useG || h == nullptr) {
         run_gemm(S, a, S.wk.tG, 1);
         return;
     }
@@ -1422,7 +1472,7 @@ static void bj_apply(Solver& S, const double* in, long long in_rs, long long in_
     a.out = out; a.out_rs = out_rs; a.out_us = f4; a.out_off0 = out_off + fz; a.out_off1 = 0; a.msplit = f4;
     a.active = active;
     const double* h = fp32 ? reinterpret_cast<const double*>(S.Mh32) : S.Mh;
-    if (!S.mirM || h == nullptr) {
+    if (!S.useM || h == nullptr) {
         run_gemm(S, a, S.wk.tM, 0);
         return;
     }

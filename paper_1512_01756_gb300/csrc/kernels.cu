@@ -184,11 +184,31 @@ __global__ void __launch_bounds__(GT) class_gemm_kernel(GemmArgs a, const Tile* 
 //     out[i] = (Hp s + Hm d)[i],   out[mirror(i)] = (Hp s - Hm d)[i],
 // two h x h products instead of one 2h x 2h product: half the FLOPs.  mats
 // holds [Hp; Hm] per matrix, M = K = h, nb = 2 (Schur blocks G, one face per
-// half) or 4 (block-Jacobi pairs).  The output addressing (msplit, out_off0/1)
+// half) or 4 (block-Jacobi pairs).  The same split holds for any involution
+// of the index set that commutes with Mat (first-half positions p(k), their
+// images q(k)): nb = -1 or -2 is the z-reversal inside each block of f_z
+// values, a symmetry of every slot inverse (L_z + s I)^-1 of the fast strip
+// solver when h_z is uniform.  The output addressing (msplit, out_off0/1)
 // and the epilogues (EPI 0 store, EPI 1 add) are those of class_gemm_kernel.
 // ---------------------------------------------------------------------------
 __device__ __forceinline__ int mirror_index(int i, int fz, int rev) {
     return rev + i - (i >= fz ? 2 * fz : 0);   // (nb - 1 - i / fz) fz + i % fz for i < 2 fz
+}
+
+// The index pair (p, q) of half-index k: mirror_nb > 0 reverses the order of
+// the faces (p = k, q = the mirrored face position); mirror_nb < 0 reverses the
+// nodes inside each of -mirror_nb blocks of `face` values (the z-reversal of a
+// slot matrix of the fast strip solver: p runs over the first half of every
+// block, q is its reflection in the block).
+__device__ __forceinline__ void mirror_pq(int k, int nb, int face, int rev, int& p, int& q) {
+    if (nb > 0) {
+        p = k;
+        q = mirror_index(k, face, rev);
+    } else {
+        const int hb = face >> 1, b = k / hb, z = k - b * hb;
+        p = b * face + z;
+        q = b * face + face - 1 - z;
+    }
 }
 
 template <int EPI, typename TM, int BMT>
@@ -215,7 +235,7 @@ __global__ void __launch_bounds__(GT) mirror_gemm_kernel(GemmArgs a, const Tile*
     __shared__ __align__(16) TM Bp[BK][BNT + 4], Bm[BK][BNT + 4];
     const TM* __restrict__ Hp = reinterpret_cast<const TM*>(a.mats) + (long long)t.mat * a.mat_stride;
     const TM* __restrict__ Hm = Hp + (long long)h * h;
-    const int fz = a.face, rev = (a.mirror_nb - 1) * a.face;
+    const int nbm = a.mirror_nb, fz = a.face, rev = (a.mirror_nb - 1) * a.face;
     const int tid = threadIdx.x;
     const int tr = tid / CG, tc = tid % CG;
     TM accp[4] = {TM(0), TM(0), TM(0), TM(0)};
@@ -245,7 +265,9 @@ __global__ void __launch_bounds__(GT) mirror_gemm_kernel(GemmArgs a, const Tile*
             const int k = k0 + kk;
             TM sp = TM(0), sm = TM(0);
             if (colp[l] != nullptr && k < h) {
-                const double v1 = colp[l][k], v2 = colp[l][mirror_index(k, fz, rev)];
+                int pk, qk;
+                mirror_pq(k, nbm, fz, rev, pk, qk);
+                const double v1 = colp[l][pk], v2 = colp[l][qk];
                 sp = TM(v1 + v2);
                 sm = TM(v1 - v2);
             }
@@ -276,9 +298,10 @@ __global__ void __launch_bounds__(GT) mirror_gemm_kernel(GemmArgs a, const Tile*
         }
         __syncthreads();
     }
-    const int row = row0 + tr;
+    int row = row0 + tr;
     if (row >= h) return;
-    const int mrow = mirror_index(row, fz, rev);
+    int mrow;
+    mirror_pq(row, nbm, fz, rev, row, mrow);
 #pragma unroll
     for (int j = 0; j < 4; ++j) {
         const int c = tc * 4 + j;
@@ -302,7 +325,7 @@ __global__ void __launch_bounds__(GT) mirror_gemm_kernel(GemmArgs a, const Tile*
 template <int BMT>
 static void launch_shape(const GemmArgs& a, const Tile* d_tiles, int ntiles, int epi, cudaStream_t s) {
     dim3 grid(ntiles, (a.M + BMT - 1) / BMT);
-    if (a.mirror_nb > 0) {
+    if (a.mirror_nb != 0) {
         if (a.fp32 && epi == 1)
             mirror_gemm_kernel<1, float, BMT><<<grid, GT, 0, s>>>(a, d_tiles);
         else if (a.fp32)
@@ -1525,6 +1548,30 @@ __global__ void mirror_halves_kernel(T* __restrict__ H, const T* __restrict__ Ma
 void k_mirror_halves(double* H, const double* Mat, int fz, int nb, cudaStream_t s) {
     const long long h = (long long)nb * fz / 2;
     mirror_halves_kernel<double><<<(unsigned)((h * h + 255) / 256), 256, 0, s>>>(H, Mat, fz, nb);
+    count_launches(1);
+}
+
+// count matrices of size m = nblk * fz (fz even) at stride m^2, z-reversal
+// inside each block: H[c] = [Hp; Hm] of size 2 (m/2)^2
+__global__ void mirror_halves_nodes_kernel(double* __restrict__ H, const double* __restrict__ Mat, long long count,
+                                           int fz, int nblk) {
+    const long long m = (long long)nblk * fz, h = m / 2, hb = fz / 2;
+    const long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx >= count * h * h) return;
+    const long long c = idx / (h * h), e = idx - c * h * h;
+    const long long i = e / h, j = e - i * h;
+    const long long pi = (i / hb) * fz + i % hb;
+    const long long pj = (j / hb) * fz + j % hb, qj = (j / hb) * fz + fz - 1 - j % hb;
+    const double* A = Mat + c * m * m;
+    const double x = A[pi * m + pj], y = A[pi * m + qj];
+    H[c * 2 * h * h + e] = 0.5 * (x + y);
+    H[c * 2 * h * h + h * h + e] = 0.5 * (x - y);
+}
+
+void k_mirror_halves_nodes(double* H, const double* Mat, long long count, int fz, int nblk, cudaStream_t s) {
+    const long long h = (long long)nblk * fz / 2, tot = count * h * h;
+    if (tot <= 0) return;
+    mirror_halves_nodes_kernel<<<(unsigned)((tot + 255) / 256), 256, 0, s>>>(H, Mat, count, fz, nblk);
     count_launches(1);
 }
 

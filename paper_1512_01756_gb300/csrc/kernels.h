@@ -115,6 +115,9 @@ void k_mirror_symmetrize(double* Mat, int fz, int nb, cudaStream_t s);
 // Hp, Hm = (Mat[i][j] +- Mat[i][mirror(j)]) / 2 for i, j < h.
 void k_mirror_halves(double* H, const double* Mat, int fz, int nb, cudaStream_t s);
 void k_mirror_halves_f(float* H, const float* Mat, int fz, int nb, cudaStream_t s);
+// Halves of count slot matrices (nblk blocks of fz values, fz even, stride
+// (nblk fz)^2) under the z-reversal inside each block: H[c] = [Hp; Hm].
+void k_mirror_halves_nodes(double* H, const double* Mat, long long count, int fz, int nblk, cudaStream_t s);
 // done[r] = active[r] ? 0 : 1 for r < R
 void k_invert_flags(int* done, const int* active, int R, cudaStream_t s);
 // K <- K - (K u) u^T (row-major d x d, w: d scratch): the projected coarse division

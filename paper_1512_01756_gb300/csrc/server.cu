@@ -71,14 +71,15 @@ bool same_problem(const Request& a, const Request& b) {
 }
 
 // Device bytes of a batch: operators per k^2 (slot inverses, G, block-Jacobi
-// inverses and the mirror-form halves of the interior ones, coarse operator)
+// inverses, the mirror-form halves of the interior ones and of the slots,
+// coarse operator)
 // plus, per right-hand side, the Krylov basis and the work vectors of the solve.
 long long footprint(const smpm_grid& g, int nop, int R) {
     const long long n = g.order + 1, fz = n * g.mz, nfz = n * fz, mx = g.mx;
     const long long d = (long long)(mx - 1) * (g.deflation_groups ? g.mz : 1);
     const long long m = g.restart > 0 ? g.restart : 64;
     const long long ld = 2 * fz * mx + fz + 32, r = nfz * mx;
-    const long long op = 3 * (2 * n * fz * fz) + 3 * 4 * fz * fz + 4 * 16 * fz * fz + 10 * fz * fz + d * d + 6 * 4 * fz;
+    const long long op = 3 * (3 * n * fz * fz) + 3 * 4 * fz * fz + 4 * 16 * fz * fz + 10 * fz * fz + d * d + 6 * 4 * fz;
     const long long per_rhs = (m + 1) * ld * (g.precision == 1 ? 2 : 1) + 12 * ld + 8 * r + 3 * (m + 2) * ((2 * fz * mx + 1023) / 1024);
     return 8 * (nop * op + (long long)R * per_rhs) + (64LL << 20);
 }

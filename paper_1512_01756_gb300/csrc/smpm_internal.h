@@ -110,8 +110,9 @@ struct GemmArgs {
     int fp32;                 // 1: mats are float, arithmetic in FP32 (EPI 0 only)
     double* out_lo;           // EPI 3: low parts of the compensated out = add + acc
     int shape;                // tile shape: 0 = 16 rows x 32 columns, 1 = 8 rows x 64 columns
-    int mirror_nb;            // > 0: mirror form over columns of mirror_nb faces of `face` values:
-    int face;                 //   mats holds [Hp; Hm] (h x h each, h = M = K = mirror_nb face / 2)
+    int mirror_nb;            // > 0: mirror form over columns of mirror_nb faces of `face` values;
+                              // < 0: over -mirror_nb blocks of `face` values reversed inside each;
+    int face;                 //   mats holds [Hp; Hm] (h x h each, h = M = K = |mirror_nb| face / 2)
 };
 
 // Number of kernels libsmpm has launched in this process.

@@ -1,14 +1,17 @@
-"""Mirror form of the interior Schur blocks and block-Jacobi pairs.
+"""Mirror forms of the dense products.
 
 With uniform h_x an interior strip (and an interior block-Jacobi pair) is
 symmetric under the reflection of x about its centre, so its class matrix
 commutes with the reversal of its faces and splits into two half-size
 products (the symmetric and antisymmetric parts of the column): half the
 FLOPs of the dense apply (the oracle's assembled S has that symmetry to
-rounding: tests/test_oracle_schur.py).  Through the C ABI, the mirror-form
-S x and M^-1 x must equal the full products of a handle set up with
-SMPM_NO_MIRROR=1 (the full form) to rounding, solves must agree, and the
-profiled FLOPs of one S x must be about half of the full form's.
+rounding: tests/test_oracle_schur.py).  With uniform h_z the same holds for
+the fast strip solver's slot inverses under the reversal of the z-nodes.
+Through the C ABI, the mirror-form S x, M^-1 x, B A^-1 b and A^-1 b of a
+handle set up with SMPM_MIRROR=1 (mirror form at every size) must equal the
+full products of one set up with SMPM_MIRROR=0 to rounding, solves must
+agree, and the profiled FLOPs must be about half of the full form's; by
+default small batches keep the full products of S and M^-1.
 """
 import numpy as np
 import pytest
@@ -40,10 +43,11 @@ def _rel(a, b):
 def _pair(smpm, monkeypatch, shape, k2, precision=0):
     mx, mz, order, lx, lz, zr = shape
     grid = smpm.make_grid(mx, mz, order, lx, lz, z_ratio=zr, precision=precision)
+    monkeypatch.setenv("SMPM_MIRROR", "1")
     s_mir = smpm.Solver(grid, k2)
-    monkeypatch.setenv("SMPM_NO_MIRROR", "1")
+    monkeypatch.setenv("SMPM_MIRROR", "0")
     s_full = smpm.Solver(grid, k2)
-    monkeypatch.delenv("SMPM_NO_MIRROR")
+    monkeypatch.delenv("SMPM_MIRROR")
     return s_mir, s_full
 
 
@@ -59,6 +63,16 @@ def test_mirror_products_equal_full(smpm, monkeypatch, shape, k2):
     s_mir.apply("Minv", X, a)
     s_full.apply("Minv", X, b)
     assert max(_rel(a[i], b[i]) for i in range(3)) < 1e-10
+    # the refined fast strip solves (z-mirror slot products on uniform-z grids)
+    Bv = np.random.default_rng(4).standard_normal((3, g.r))
+    a, b = np.empty_like(X), np.empty_like(X)
+    s_mir.apply("bS", Bv, a)
+    s_full.apply("bS", Bv, b)
+    assert max(_rel(a[i], b[i]) for i in range(3)) < 1e-11
+    ar, br = np.empty_like(Bv), np.empty_like(Bv)
+    s_mir.apply("Ainv", Bv, ar)
+    s_full.apply("Ainv", Bv, br)
+    assert max(_rel(ar[i], br[i]) for i in range(3)) < 1e-11
     # solves of the same right-hand side (both to 1e-11)
     f = np.random.default_rng(6).uniform(0, 1, g.r)
     u1, u2 = np.zeros_like(f), np.zeros_like(f)
@@ -93,24 +107,51 @@ def test_mirror_fp32_blocks(smpm, monkeypatch, precision):
     assert _rel(u1, u2) < 1e-9
 
 
-def test_mirror_halves_the_schur_flops(smpm, monkeypatch):
-    """Profiled FLOPs of one S x on 256 x 4, order 12: the 254 interior strips
+def test_mirror_halves_the_flops(smpm, monkeypatch):
+    """Profiled FLOPs on 256 x 4, order 12.  One S x: the 254 interior strips
     in the mirror form, the two boundary strips (f_z stored rows each) full:
     (2 * 4 + 254 * 4) / (2 * 4 + 254 * 8) = 0.502 of the full form (in units
-    of f_z^2 FLOPs per column)."""
+    of f_z^2 FLOPs per column).  One refined A^-1 b: every slot product in the
+    z-mirror form, exactly half."""
     shape = (256, 4, 12, 64.0, 1.0, 1.0)
     g = Grid(*shape[:5])
     s_mir, s_full = _pair(smpm, monkeypatch, shape, 0.0)
     X = np.random.default_rng(9).standard_normal((4, g.k))
     y = np.empty_like(X)
-    fl = []
+    Bv = np.random.default_rng(10).standard_normal((4, g.r))
+    yr = np.empty_like(Bv)
+    fl, fl_a = [], []
     for s in (s_mir, s_full):
-        s.apply("S", X, y)          # tile-shape tuning happens outside the profile
-        s.profile(True)
-        s.apply("S", X, y)
-        fl.append(s.profile_read()["flops"])
-        s.profile(False)
+        for kind, x, out, acc in (("S", X, y, fl), ("Ainv", Bv, yr, fl_a)):
+            s.apply(kind, x, out)          # tile-shape tuning happens outside the profile
+            s.profile(True)
+            s.apply(kind, x, out)
+            acc.append(s.profile_read()["flops"])
+            s.profile(False)
         s.close()
     fz = g.fz
     assert fl[1] == pytest.approx(4 * (2 * (2 * fz * 2 * fz) + 254 * 2 * (2 * fz) ** 2), rel=1e-12)
     assert fl[0] / fl[1] == pytest.approx(1024 / 2040, rel=1e-9)
+    assert fl_a[0] / fl_a[1] == pytest.approx(0.5, rel=1e-9)
+
+
+def test_small_batches_keep_the_full_products(smpm):
+    """By default the x-mirror form of S and M^-1 (one more launch per
+    product) is used only where it saves enough FLOPs: not for one right-hand
+    side on 8 x 2, order 8; yes for 128 on 256 x 4, order 12."""
+    fl = {}
+    for shape, R in (((8, 2, 8, 4.0, 1.0), 1), ((256, 4, 12, 64.0, 1.0), 128)):
+        g = Grid(*shape)
+        s = smpm.Solver(smpm.make_grid(*shape), 0.0, torch.cuda.current_stream())
+        X = torch.randn(R, g.k, dtype=torch.float64, device="cuda")
+        Y = torch.empty_like(X)
+        s.apply("S", X, Y)
+        s.profile(True)
+        s.apply("S", X, Y)
+        p = s.profile_read()
+        s.profile(False)
+        s.close()
+        full = R * (2 * (2 * g.fz * 2 * g.fz) + (g.mx - 2) * 2 * (2 * g.fz) ** 2)
+        fl[shape[0]] = (p["launches"], p["flops"] / full)
+    assert fl[8] == (1, pytest.approx(1.0, rel=1e-12))
+    assert fl[256][0] == 2 and fl[256][1] == pytest.approx(1024 / 2040, rel=1e-9)
