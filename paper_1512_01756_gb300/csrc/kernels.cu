@@ -240,6 +240,7 @@ __global__ void __launch_bounds__(GT) mirror_gemm_kernel(GemmArgs a, const Tile*
     const int tr = tid / CG, tc = tid % CG;
     TM accp[4] = {TM(0), TM(0), TM(0), TM(0)};
     TM accm[4] = {TM(0), TM(0), TM(0), TM(0)};
+    const bool live = row0 + tr < h;
 
     const double* colp[(BNT * BK) / GT];
 #pragma unroll
@@ -275,7 +276,10 @@ __global__ void __launch_bounds__(GT) mirror_gemm_kernel(GemmArgs a, const Tile*
             Bm[kk][c] = sm;
         }
         __syncthreads();
-        if (k0 + BK <= h) {
+        if (!live) {
+            // padded row of the last row tile: its products are never stored
+            // (warp-uniform where h is a multiple of the rows a warp covers)
+        } else if (k0 + BK <= h) {
 #pragma unroll
             for (int kk = 0; kk < BK; ++kk) {
                 const TM ap = Ap[kk][tr], am = Am[kk][tr];
