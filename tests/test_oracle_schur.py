@@ -123,3 +123,22 @@ def test_schur_commutes_with_x_reflection(shape, k2):
     if zr != 1.0:
         Q = np.array([(i // fz) * fz + (fz - 1 - i % fz) for i in range(g.k)])
         assert np.abs(S[np.ix_(Q, Q)] - S).max() > 1e-3 * np.abs(S).max()
+
+
+@pytest.mark.parametrize("shape,k2", [((4, 2, 5, 2.0, 1.0, 1.0), 0.0), ((5, 4, 4, 2.0, 1.0, 1.0), 7.5)])
+def test_schur_commutes_with_z_reversal(shape, k2):
+    """With uniform h_z (and the Neumann condition at both z-ends) the domain
+    is symmetric under z -> l_z - z, which reverses the z-nodes of every face
+    and keeps the faces in place; the assembled S commutes with it.  The
+    library's z-mirror form of the fast strip solver's slot products rests on
+    this symmetry of L_z (Sec. 2.2, Sec. 5)."""
+    mx, mz, order, lx, lz, zr = shape
+    g = Grid(mx, mz, order, lx, lz, z_ratio=zr)
+    S = schur_dense(g, assemble_L(g, k2))[0]
+    fz = g.fz
+    P = np.array([(i // fz) * fz + (fz - 1 - i % fz) for i in range(g.k)])
+    assert np.abs(S[np.ix_(P, P)] - S).max() < 1e-12 * np.abs(S).max()
+    # the same map is not a symmetry once z is stretched
+    gs = Grid(mx, mz, order, lx, lz, z_ratio=1.3)
+    Ss = schur_dense(gs, assemble_L(gs, k2))[0]
+    assert np.abs(Ss[np.ix_(P, P)] - Ss).max() > 1e-3 * np.abs(Ss).max()
