@@ -58,14 +58,15 @@ extern "C" {
 
 typedef struct smpm_solver* smpm_handle;
 
-/* Grid and solver options.  Defaults used when a field is 0: tau_scale -30,
+/* Grid and solver options.  Defaults used when a field is 0: tau_scale -0.1,
  * z_ratio 1, restart 64, max_iter 2000.  tau_scale is signed in the
- * convention of Eq. smpm_poisson; negative values damp inter-element jumps. */
+ * convention of Eq. smpm_poisson; negative values damp inter-element jumps
+ * (|tau_scale| below ~0.028 leaves anti-damped jump modes at orders >= 8). */
 typedef struct {
     int mx, mz, order;      /* elements in x and z, polynomial order (n = order+1)   */
     double lx, lz;          /* domain [0,lx] x [0,lz]                                */
     double z_ratio;         /* geometric z-stretch h_{e+1} = z_ratio h_e, 1 = uniform */
-    double tau_scale;       /* penalty tau = tau_scale*N(N+1)/h_perp on every edge    */
+    double tau_scale;       /* penalty tau = tau_scale*(N(N+1)/h_perp)^2 on every edge */
     int deflation_groups;   /* 0: one deflation vector per interface (Sec. 3.3);
                                1: one per interface and element row                  */
     int restart;            /* GMRES restart length m                                */

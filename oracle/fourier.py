@@ -8,7 +8,7 @@ into one 2-D problem per wavenumber: (L - k_j^2 I) u_j = f_j.  The oracle takes
 the plain route: a real DFT along y (numpy rfft), one independent 2-D solve per
 mode for the real and imaginary parts (L is real), and the inverse DFT.
 
-Reading (listed in the design doc): k_j = 2 pi j / l_y for j = 0 .. m_y/2 (the
+Reading (Sec. 5 prints h_y in the wavenumber): k_j = 2 pi j / l_y for j = 0 .. m_y/2 (the
 printed h_y in the wavenumber is read as l_y; the Nyquist mode is kept).  Mode 0
 is the singular Poisson-Neumann problem and gets the null-space projection and
 the zero-mean gauge; the other modes are regular Helmholtz problems.

@@ -20,17 +20,22 @@ What this module computes
 * ``split``: A (entries coupling nodes of the same vertical strip), the
   inclusion E of the interface nodes (Sec. 2.3) and B := E^T (L - A).
 
-Readings of the paper used here (each is listed in the design doc):
+Readings of the paper used here (where Sec. 2.2 leaves a choice open):
 * n GLL points means polynomial order N = n - 1.
-* tau is not given (Sec. 2.2 leaves it to stability criteria and a heuristic):
-  tau = tau_scale * N (N + 1) / h_perp on every edge, h_perp the own element's
-  length normal to that edge, tau_scale = -30 by default.  In the sign
-  convention of Eq. smpm_poisson a positive tau anti-damps the modes that jump
-  across an interface (the 1-D operators then have eigenvalues with positive
-  real part, an unstable discretisation, and the Helmholtz problems of Sec. 5
-  become indefinite for k^2 above a few thousand); the stable choice is
-  negative, and |tau_scale| = 30 removes every such eigenvalue on grids up to
-  order 12.  tau does not depend on k^2 (Sec. 5).
+* tau is not given (Sec. 2.2 leaves it to stability criteria and a
+  heuristic): tau = tau_scale * (N (N + 1) / h_perp)^2 on every edge, h_perp
+  the own element's length normal to that edge, tau_scale = -0.1 by default.
+  In the sign convention of Eq. smpm_poisson a positive tau anti-damps the
+  modes that jump across an interface (the operator then has eigenvalues with
+  positive real part, an unstable discretisation, and the Helmholtz problems
+  of Sec. 5 become indefinite), so the stable sign is negative.  With the
+  literal Robin operator R = I + n.grad the smallest stable |tau| grows as
+  N^4 / h^2: in this parameterisation it is ~0.028 at every order from 8 to
+  20 and every element length from 1/128 to 2 (0.010 at order 4), so -0.1
+  keeps a margin of 3.6 everywhere.  The earlier form tau_scale N (N + 1) / h
+  has no such constant: at a fixed tau_scale it turns unstable as h shrinks
+  (order 16 needed |tau_scale| >= 119 at h = 1/16).  tau does not depend on
+  k^2 (Sec. 5).
 * A corner node receives the terms of both edges it lies on.
 * Neumann data g is given per physical boundary side (west/east: one value per
   z-node, south/north: one value per x-node), so a corner node sees the g of
@@ -50,7 +55,7 @@ from .lgl import lgl_nodes_weights, diff_matrix
 
 
 class Grid:
-    def __init__(self, mx, mz, order, lx, lz, z_ratio=1.0, tau_scale=-30.0):
+    def __init__(self, mx, mz, order, lx, lz, z_ratio=1.0, tau_scale=-0.1):
         if mx < 2 or mz < 1 or order < 1:
             raise ValueError("need mx >= 2, mz >= 1, order >= 1")
         self.mx, self.mz, self.order = int(mx), int(mz), int(order)
@@ -73,8 +78,8 @@ class Grid:
         self.nx = n * self.mx
         self.r = self.nx * self.fz
         self.k = 2 * self.fz * (self.mx - 1)
-        self.tau_x = self.tau_scale * N * (N + 1) / self.hx
-        self.tau_z = self.tau_scale * N * (N + 1) / self.hz
+        self.tau_x = self.tau_scale * (N * (N + 1) / self.hx) ** 2
+        self.tau_z = self.tau_scale * (N * (N + 1) / self.hz) ** 2
 
     # ----- indexing -------------------------------------------------------
     def node(self, ex, a, ez, b):

@@ -99,7 +99,7 @@ bool make_geometry(int mx, int mz, int order, double lx, double lz, double z_rat
     }
     if (!(lx > 0) || !(lz > 0)) { msg = "domain lengths must be positive"; return false; }
     if (z_ratio == 0.0) z_ratio = 1.0;
-    if (tau_scale == 0.0) tau_scale = -30.0;
+    if (tau_scale == 0.0) tau_scale = -0.1;
     if (!(z_ratio > 0)) { msg = "z_ratio must be positive"; return false; }
     if (!std::isfinite(tau_scale)) { msg = "tau_scale must be finite"; return false; }
     if (groups != 0 && groups != 1) { msg = "deflation_groups must be 0 or 1"; return false; }
@@ -118,10 +118,13 @@ bool make_geometry(int mx, int mz, int order, double lx, double lz, double z_rat
     g.zb.assign(mz + 1, 0.0);
     for (int e = 0; e < mz; ++e) g.zb[e + 1] = g.zb[e] + g.hz[e];
     g.zb[mz] = lz;
+    // tau = tau_scale (N (N+1) / h_perp)^2 per edge, h_perp the own element's
+    // length normal to the edge: the smallest |tau| without anti-damped jump
+    // modes grows as N^4 / h^2 and is ~0.028 (N (N+1) / h)^2 at every order
     const double NN = (double)g.N * (g.N + 1.0);
-    g.tau_x = tau_scale * NN / g.hx;
+    g.tau_x = tau_scale * (NN / g.hx) * (NN / g.hx);
     g.tau_z.resize(mz);
-    for (int e = 0; e < mz; ++e) g.tau_z[e] = tau_scale * NN / g.hz[e];
+    for (int e = 0; e < mz; ++e) g.tau_z[e] = tau_scale * (NN / g.hz[e]) * (NN / g.hz[e]);
     gll(g.n, g.xi, g.w);
     gll_diff(g.xi, g.D);
     const int n = g.n;

@@ -21,7 +21,7 @@ struct Geometry {
     int mx = 0, mz = 0, order = 0, n = 0, N = 0;
     int fz = 0, nx = 0;                   // z-nodes per strip column, x-nodes total
     long long r = 0, k = 0;               // grid nodes, Schur unknowns
-    double lx = 0, lz = 0, hx = 0, tau_x = 0, z_ratio = 1, tau_scale = -30;
+    double lx = 0, lz = 0, hx = 0, tau_x = 0, z_ratio = 1, tau_scale = -0.1;
     std::vector<double> hz, zb, tau_z;    // per z-element
     std::vector<double> xi, w, D, D2;     // GLL data (row-major n x n)
     int ng = 1;                           // deflation groups per interface

@@ -133,7 +133,7 @@ def _stream_ptr(stream):
     return ctypes.c_void_p(int(stream))
 
 
-def make_grid(mx, mz, order, lx, lz, z_ratio=1.0, tau_scale=-30.0, deflation_groups=0, restart=64,
+def make_grid(mx, mz, order, lx, lz, z_ratio=1.0, tau_scale=-0.1, deflation_groups=0, restart=64,
               max_iter=2000, precision=0):
     return Grid(mx, mz, order, lx, lz, z_ratio, tau_scale, deflation_groups, restart, max_iter, precision)
 

@@ -115,15 +115,63 @@ def test_helmholtz_spectral_convergence():
     assert errs[0] > 1e-5 and errs[-1] < 1e-9 and errs[1] < errs[0] * 1e-2
 
 
-@pytest.mark.parametrize("shape", [(8, 2, 8, 4.0, 1.0, 1.0), (8, 4, 12, 2.0, 1.0, 1.0), (8, 8, 10, 2.0, 1.0, 1.0)])
+def _one_d_spectra(mx, mz, order, hx, lz, zr, tau_scale):
+    """Eigenvalues of the 1-D factors of L = L_x (+) L_z (pinned by
+    test_kronecker_sum_structure): L_x from a one-element-row grid with m_x
+    elements of length hx, L_z from a two-strip grid with the m_z elements of
+    the z-mesh.  Each diagonal block read out of L carries the other factor's
+    constant diagonal shift; L_x 1 = L_z 1 = 0 gives that shift."""
+    out = []
+    for g, idx in ((Grid(mx, 1, order, mx * hx, 1.0, tau_scale=tau_scale), "x"),
+                   (Grid(2, mz, order, 1.0, lz, z_ratio=zr, tau_scale=tau_scale), "z")):
+        L = assemble_L(g).tocsr()
+        sel = np.arange(g.nx) * g.fz if idx == "x" else np.arange(g.fz)
+        M = L[sel][:, sel].toarray()
+        shift = (M @ np.ones(M.shape[0]))[0]
+        out.append(np.linalg.eigvals(M) - shift)
+    return out
+
+
+# element shapes of every workload: (m_x used for L_x, m_z, order, h_x, l_z, z_ratio)
+PENALTY_SHAPES = [
+    (8, 2, 8, 0.5, 1.0, 1.0),        # 8 x 2 elements on 4 x 1, order 8
+    (16, 4, 12, 0.25, 1.0, 1.0),     # 256 x 4 on 64 x 1, order 12
+    (16, 8, 10, 0.25, 1.0, 1.0),     # 128 x 8 on 32 x 1, order 10 (the Fourier-mode problems)
+    (16, 16, 16, 0.0625, 1.0, 1.2),  # 512 x 16 on 32 x 1, order 16, z stretched by 1.2
+    (16, 16, 16, 0.0625, 1.0, 1.0),  # 1024 x 16 on 64 x 1, order 16 (serving)
+    (16, 16, 12, 0.0625, 1.0, 1.0),  # 512 x 16 / 1024 x 16, order 12 (serving)
+    (16, 8, 16, 0.125, 1.0, 1.0),    # 256 x 8 on 32 x 1, order 16 (serving)
+    (16, 2, 6, 0.5, 1.0, 1.0),       # 64 x 2 on 32 x 1, order 6 (serving)
+]
+
+
+@pytest.mark.parametrize("shape", PENALTY_SHAPES)
 def test_default_penalty_has_no_antidamped_modes(shape):
-    """Stability reading of tau: at the default (negative) tau_scale the SMPM
-    operator has no eigenvalue with positive real part on the element shapes
-    of the 4x1, long-domain and 3-D workloads (so every Helmholtz shift k^2 > 0
-    gives a definite problem); with a positive tau the inter-element jump
-    modes come out anti-damped."""
+    """Stability reading of tau: at the default tau_scale no eigenvalue of the
+    SMPM operator has a positive real part on the element shapes of every
+    workload, orders 6 to 16 and element lengths 1/88 to 1/2 included (so
+    every Helmholtz shift k^2 > 0 gives a definite problem).  The spectrum of
+    L is the set of sums of the two 1-D spectra, so both are checked."""
+    mx, mz, order, hx, lz, zr = shape
+    for ev in _one_d_spectra(mx, mz, order, hx, lz, zr, -0.1):
+        assert ev.real.max() < 1e-12 * np.abs(ev).max()
+
+
+@pytest.mark.parametrize("shape", [(16, 16, 16, 0.0625, 1.0, 1.0), (16, 8, 12, 0.125, 1.0, 1.0)])
+def test_penalty_pin_is_sensitive(shape):
+    """The check above fails for a penalty that is too weak or of the wrong
+    sign: tau_scale = -0.02 (below the ~0.028 threshold) and +0.1 both leave
+    jump modes with a positive real part."""
+    mx, mz, order, hx, lz, zr = shape
+    for ts in (-0.02, 0.1):
+        worst = max(ev.real.max() / np.abs(ev).max() for ev in _one_d_spectra(mx, mz, order, hx, lz, zr, ts))
+        assert worst > 1e-6
+
+
+@pytest.mark.parametrize("shape", [(8, 2, 8, 4.0, 1.0, 1.0), (8, 4, 12, 2.0, 1.0, 1.0), (4, 4, 10, 1.0, 1.0, 1.2)])
+def test_default_penalty_full_spectrum(shape):
+    """The same stability statement on the full assembled L of small grids
+    (no use of the Kronecker structure)."""
     mx, mz, order, lx, lz, zr = shape
     ev = np.linalg.eigvals(assemble_L(Grid(mx, mz, order, lx, lz, z_ratio=zr)).toarray())
     assert ev.real.max() < 1e-8 * np.abs(ev).max()
-    ev_pos = np.linalg.eigvals(assemble_L(Grid(mx, mz, order, lx, lz, z_ratio=zr, tau_scale=10.0)).toarray())
-    assert ev_pos.real.max() > 1e2
