@@ -1,20 +1,40 @@
 #!/usr/bin/env python3
-"""Throughput of the deflated block-Jacobi Schur-complement GMRES solve.
+"""Served vs plain FP64 deflated block-Jacobi Schur-complement GMRES.
 
-Workload: the 2-D Poisson-Neumann long-domain problem, 256 x 4 elements of
-order 12 on [0, 64] x [0, 1] (r = 173,056 nodes, k = 26,520 Schur unknowns),
-f = a seeded sum of 32 random low-wavenumber cos-cos modes, g = 0, plain FP64
-path (Alg. seq: block-Jacobi + deflation, CGS2 GMRES) to a relative Schur
-residual of 1e-10.  A step solves one batch of --rhs (default 128)
-independent right-hand sides (each with its own Krylov space) through the C
-ABI; value = solved
-right-hand sides per second over all ranks (each rank its own batch: weak
-scaling, no collective on the data path).
+Default workload (the headline line): a stream of Poisson / Helmholtz solve
+requests -- grids drawn uniformly from 64x2, 128x4, 256x8, 512x16 and 1024x16
+elements (square elements, domain [0, mx/mz] x [0, 1]), orders uniform from
+{6, 8, 12, 16}, k^2 = 0 with probability 0.1 else log-uniform on
+[1e-2, 1e4], f a seeded sum of 32 cos-cos modes per request -- each solved to
+a relative Schur residual of 1e-10 (Alg. seq; the Helmholtz form of Sec. 5).
+A step is --requests-per-step (default 100) consecutive requests of the
+stream, so --steps 20 is the 2000-request stream.  Two paths serve it:
 
-  python bench.py [--gpus N] [--steps K] [--warmup W] [--rhs R] [--impl reference]
+* plain: one request at a time, smpm_setup + smpm_solve + smpm_release,
+  FP64 throughout;
+* served: the serving runtime (smpm_server_*: worker streams, continuous
+  batching of same-grid requests, HBM-footprint admission, operator cache),
+  nested mixed precision (FP64 flexible GMRES outside, FP32 inner DBJ-GMRES).
 
---impl reference times the CPU oracle (oracle/, numpy/scipy FP64, Alg. seq
-with Householder GMRES) on the host cores on the same workload and metric.
+value = served solves/s with the whole stream submitted at once (inputs
+resident in HBM); plain_value = the plain path's solves/s; p50/p99 latency
+(completion - arrival, setup included) of both under Poisson arrivals at the
+rate where the plain path saturates (its measured service rate; the plain
+path's latencies follow from its measured service times by the FIFO queue
+recursion, the served ones are measured live).  e2e = the served solves/s
+with f and u in pinned host memory (the copies inside the library calls).
+Every rank serves its own stream (weak scaling, no collective on the data
+path).
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+                  [--workload serve|poisson2d|small|modes3d|mixed]
+
+--workload poisson2d is the 256 x 4, order-12 batched FP64 solve (128
+right-hand sides per step); small / modes3d / mixed are the 8 x 2 latency,
+3-D Fourier-mode and 512 x 16 mixed-precision configurations.  --impl
+reference times the CPU oracle (oracle/, numpy/scipy FP64, Alg. seq with
+Householder GMRES) on the host cores on a bounded sample of the same
+workload.
 """
 import argparse
 import hashlib
@@ -32,25 +52,32 @@ sys.path.insert(0, ROOT)
 GRID = dict(mx=256, mz=4, order=12, lx=64.0, lz=1.0)
 WORKLOAD = "2-D Poisson-Neumann, 256x4 elements, order 12, domain 64x1, 32 seeded cos-cos modes, g=0"
 METRIC = "solves/s at 1e-10 rel. residual (plain FP64 DBJ-GMRES)"
+METRIC_SERVE = "solves/s at 1e-10 rel. residual, p50/p99 latency: served vs plain FP64 GMRES"
 TOL = 1e-10
 FP64_NOMINAL_TFLOPS = 1.25     # GB300 FP64 (non-tensor and tensor), profiling recipe table
+# FP32 CUDA-core peak from unit counts and clock: 152 SMs x 128 FP32 lanes x 2 FLOP x 2.07 GHz
+FP32_SIMT_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12
+ORACLE_MAX_NODES = 50_000      # cpu_baseline / reference arm: requests the oracle finishes in seconds
 L2_FLUSH_BYTES = 256 << 20
 
 
 def parse():
     p = argparse.ArgumentParser()
     p.add_argument("--gpus", type=int, default=1)
-    p.add_argument("--steps", type=int, default=5)
+    p.add_argument("--steps", type=int, default=20)
     p.add_argument("--warmup", type=int, default=3)
     p.add_argument("--rhs", type=int, default=128, help="right-hand sides per step (one batched solve)")
     p.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    p.add_argument("--cpu-sample", type=int, default=2, help="oracle right-hand sides in the cpu_baseline leg")
+    p.add_argument("--cpu-sample", type=int, default=2, help="poisson2d: oracle right-hand sides in the cpu_baseline leg")
     p.add_argument("--no-cpu-baseline", action="store_true")
-    p.add_argument("--workload", default="poisson2d", choices=["poisson2d", "small", "modes3d", "mixed", "serve"],
-                   help="poisson2d: the default bench line; small / modes3d / mixed / serve: the 8x2 latency, 3-D, "
-                        "mixed-precision and serving configurations, measured separately (not the driver's "
-                        "bench line)")
-    p.add_argument("--requests", type=int, default=200, help="serve: requests in the stream")
+    p.add_argument("--no-secondary", action="store_true", help="serve: skip the 256x4 secondary figure")
+    p.add_argument("--workload", default="serve", choices=["serve", "poisson2d", "small", "modes3d", "mixed"],
+                   help="serve: the request stream, served vs plain (the default line); poisson2d / small / "
+                        "modes3d / mixed: the 256x4 batched, 8x2 latency, 3-D and mixed-precision configurations")
+    p.add_argument("--requests-per-step", type=int, default=100, help="serve: requests of the stream per step")
+    p.add_argument("--cpu-seconds", type=float, default=20.0, help="serve: oracle time budget of the cpu_baseline leg")
+    p.add_argument("--profiled-requests", type=int, default=300,
+                   help="serve: requests re-run with the dense-product profile on (roofline)")
     p.add_argument("--mixed-rhs", type=int, default=16, help="mixed: right-hand sides per step")
     p.add_argument("--workers", type=int, default=4, help="serve: server worker threads (one stream each)")
     p.add_argument("--max-batch", type=int, default=16, help="serve: requests per batch at most")
@@ -216,7 +243,7 @@ def run_reference(args):
     return 0
 
 
-def run_ours(args):
+def run_poisson2d(args):
     import numpy as np
     import torch
     import torch.distributed as dist
@@ -251,24 +278,31 @@ def run_ours(args):
     clocks = Clocks(local)
     clocks.start()
     l0 = smpm.kernel_launches()
+
+    def timed_steps():
+        ts, sts = [], []
+        for _ in range(args.steps):
+            flush.fill_(1.0)                      # evict L2 between steps (not timed)
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            st = solver.solve(Fd, Ud, tol=TOL)
+            e1.record(stream)
+            e1.synchronize()
+            ts.append(e0.elapsed_time(e1))
+            sts.append(st.as_dict())
+        return ts, sts
+    times, stats = timed_steps()              # the value: profile off
+    launches = smpm.kernel_launches() - l0
+    barrier()
+    clk = clocks.stop()
+    # roofline: the same steps again with events around every dense-product launch
     solver.profile(True)
     solver.profile_read(reset=True)
-    times, stats = [], []
-    for _ in range(args.steps):
-        flush.fill_(1.0)                      # evict L2 between steps (not timed)
-        e0 = torch.cuda.Event(enable_timing=True)
-        e1 = torch.cuda.Event(enable_timing=True)
-        e0.record(stream)
-        st = solver.solve(Fd, Ud, tol=TOL)
-        e1.record(stream)
-        e1.synchronize()
-        times.append(e0.elapsed_time(e1))
-        stats.append(st.as_dict())
-    launches = smpm.kernel_launches() - l0
+    times_prof, _ = timed_steps()
     prof = solver.profile_read(reset=True)
     solver.profile(False)
     barrier()
-    clk = clocks.stop()
     ms = sum(times) / len(times)
     ms_max = max_over_ranks(ms, dev, world)
     worst_res = max(s["rel_resid_true"] for s in stats)
@@ -301,7 +335,8 @@ def run_ours(args):
                 "peak_source": "recipe FP64 1.25 TFLOP/s (GB300); measured DFMA probe %.3f TFLOP/s" % fp64_probe,
                 "flops_per_launch": prof["flops"] / launches_gemm,
                 "ms_per_launch": prof["ms"] / launches_gemm,
-                "gemm_share_of_step": prof["ms"] / (ms * args.steps)}
+                "gemm_share_of_step": prof["ms"] / sum(times_prof),
+                "profiled_ms_per_step": sum(times_prof) / len(times_prof)}
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
@@ -476,164 +511,370 @@ def serve_rhs(smpm, grid, lx, seed):
     return ((Cx * c) @ Cz.T).reshape(-1)
 
 
+def serve_requests(n, seed, smpm=None, precision=2):
+    """The stream's requests with their grids (plain FP64 and served form)."""
+    reqs = serve_stream(n, seed)
+    for q in reqs:
+        q["lx"] = q["mx"] / q["mz"]
+        q["r"] = (q["order"] + 1) ** 2 * q["mx"] * q["mz"]
+        if smpm is not None:
+            q["grid"] = smpm.make_grid(q["mx"], q["mz"], q["order"], q["lx"], 1.0)
+            q["grid_served"] = smpm.make_grid(q["mx"], q["mz"], q["order"], q["lx"], 1.0, precision=precision)
+    return reqs
+
+
+def oracle_serve_sample(reqs, seconds, max_nodes=ORACLE_MAX_NODES, max_count=None):
+    """The CPU oracle (setup + Alg. seq solve per request) on the stream's
+    requests in order, skipping grids above max_nodes nodes, until `seconds`
+    of wall time (at least two requests) or max_count requests.  Returns
+    (requests solved, wall seconds, effective cores, largest grid)."""
+    from oracle.smpm import Grid
+    from oracle.schur import StripSchur
+    from oracle import dbj
+    from paper_1512_01756_gb300 import inputs
+    done, biggest, big_r = 0, "", 0
+    c0, w0 = os.times(), time.perf_counter()
+    for q in reqs:
+        if q["r"] > max_nodes:
+            continue
+        g = Grid(q["mx"], q["mz"], q["order"], q["lx"], 1.0)
+        X, Z = g.coords()
+        f, _ = inputs.cos_modes(X, Z, q["lx"], 1.0, inputs.cos_modes_spec(q["seed"]))
+        _, info = dbj.solve(g, f, k2=q["k2"], method="dbj", tol=TOL, schur=StripSchur(g, q["k2"]))
+        assert info["schur_residual"] < 10 * TOL
+        done += 1
+        if q["r"] > big_r:
+            big_r, biggest = q["r"], f'{q["mx"]}x{q["mz"]} order {q["order"]}'
+        if max_count is not None and done >= max_count:
+            break
+        if max_count is None and done >= 2 and time.perf_counter() - w0 > seconds:
+            break
+    w1, c1 = time.perf_counter(), os.times()
+    cores = max(1, round(((c1.user - c0.user) + (c1.system - c0.system)) / (w1 - w0)))
+    return done, w1 - w0, cores, biggest
+
+
+def _pct(v, p):
+    import numpy as np
+    return float(np.percentile(np.asarray(v) * 1e3, p))
+
+
+def _served_pass(srv, reqs, f_of, u_of, arrivals=None, poll_sleep=0.0002):
+    """Serve reqs through srv: all at once (arrivals None) or at the given
+    arrival offsets (seconds from the call).  Returns (wall span s,
+    latencies s, batch sizes, worst residual)."""
+    tickets, lat, batch, worst = {}, [], [], 0.0
+    sub = [0.0] * len(reqs)
+    t0 = time.perf_counter()
+    nxt = 0
+    while nxt < len(reqs) or tickets:
+        now = time.perf_counter() - t0
+        while nxt < len(reqs) and (arrivals is None or arrivals[nxt] <= now):
+            q = reqs[nxt]
+            sub[nxt] = time.perf_counter() - t0
+            tickets[srv.submit(q["grid_served"], q["k2"], f_of(nxt), u_of(nxt), tol=TOL)] = nxt
+            nxt += 1
+        for tk in list(tickets):
+            st = srv.poll(tk)
+            if st is not None:
+                i = tickets[tk]
+                # completion - arrival: the wait before the submit call plus
+                # the server's own submit-to-completion time
+                lat.append(st.solve_ms * 1e-3 + (sub[i] - arrivals[i] if arrivals is not None else 0.0))
+                batch.append(st.restarts)
+                worst = max(worst, st.rel_resid_true)
+                del tickets[tk]
+        time.sleep(poll_sleep)
+    span = time.perf_counter() - t0
+    return span, lat, batch, worst
+
+
 def run_serve(args):
-    """Serving: the request stream served one at a time by the plain FP64 path
-    (smpm_setup + smpm_solve + smpm_release per request) and by the server
-    (continuous batching over worker streams), with Poisson arrivals at the
-    rate where the plain path saturates (its measured mean service rate)."""
+    """The headline line: the request stream served one at a time by the
+    plain FP64 path and by the serving runtime (module docstring)."""
     import numpy as np
     import torch
+    import torch.distributed as dist
     import __graft_entry__
     __graft_entry__.build()
     from paper_1512_01756_gb300 import smpm, inputs
-    dev = torch.device("cuda", 0)
-    torch.cuda.set_device(dev)
-    stream = torch.cuda.current_stream()
-    reqs = serve_stream(args.requests, inputs.seed_for(5))
-    for q in reqs:
-        q["grid"] = smpm.make_grid(q["mx"], q["mz"], q["order"], q["mx"] / q["mz"], 1.0)
-        # the served form may run the mixed-precision solve (same FP64 true residual)
-        q["grid_served"] = smpm.make_grid(q["mx"], q["mz"], q["order"], q["mx"] / q["mz"], 1.0,
-                                          precision=args.served_precision)
-        q["f"] = torch.from_numpy(serve_rhs(smpm, q["grid"], q["mx"] / q["mz"], q["seed"])).to(dev)
-        q["u_plain"] = torch.zeros_like(q["f"])
-        q["u_served"] = torch.zeros_like(q["f"])
-    # warm-up (library, cuSOLVER kernels of every matrix size, allocator, GEMM
-    # tile tuning): one k^2 = 1 solve per grid and order of the stream, so that
-    # neither pass below pays a first-use cost
-    wg = smpm.make_grid(64, 2, 6, 32.0, 1.0)
-    wf = torch.from_numpy(serve_rhs(smpm, wg, 32.0, 1)).to(dev)
-    wu = torch.zeros_like(wf)
-    for _ in range(max(args.warmup, 1)):
-        s = smpm.Solver(wg, 1.0, stream)
-        s.solve(wf, wu, tol=TOL)
-        s.close()
-    seen = set()
-    for q in reqs:
-        key = (q["mx"], q["mz"], q["order"])
-        if key in seen:
-            continue
-        seen.add(key)
-        for k2w in (1.0, 0.0):
-            for gw in {id(q["grid"]): q["grid"], id(q["grid_served"]): q["grid_served"]}.values():
-                s = smpm.Solver(gw, k2w, stream)
-                s.solve(q["f"], q["u_plain"], tol=TOL)
-                s.close()
-    torch.cuda.synchronize()
-    srv = smpm.Server(nworkers=args.workers, max_batch=args.max_batch)
-    t = srv.submit(wg, 2.0, wf, wu, tol=TOL)
-    while srv.poll(t) is None:
-        time.sleep(0.001)
-    torch.cuda.synchronize()
 
-    # plain FP64, one request at a time
-    clocks = Clocks(0)
+    rank, local, world = rank_env()
+    dev = torch.device("cuda", local)
+    torch.cuda.set_device(dev)
+    if world > 1:
+        dist.init_process_group("nccl", device_id=dev)
+    stream = torch.cuda.current_stream()
+    K, W, per = args.steps, args.warmup, args.requests_per_step
+    N = K * per
+    seed = inputs.seed_for(5) + 100_000 * rank          # every rank its own stream
+    reqs = serve_requests(N, seed, smpm, args.served_precision)
+    offs = np.concatenate([[0], np.cumsum([q["r"] for q in reqs])])
+    total = int(offs[-1])
+    # f of every request in one pinned host buffer (the e2e pass reads it
+    # there); the device-resident passes read a device copy
+    Fh = torch.empty(total, dtype=torch.float64, pin_memory=True)
+    Fn = Fh.numpy()
+    for i, q in enumerate(reqs):
+        Fn[offs[i]:offs[i + 1]] = serve_rhs(smpm, q["grid"], q["lx"], q["seed"])
+    Fd = Fh.to(dev)
+    Up = torch.zeros(total, dtype=torch.float64, device=dev)
+    Us = torch.zeros_like(Up)
+    Ub = torch.zeros_like(Up)
+    Uh = torch.zeros(total, dtype=torch.float64, pin_memory=True)
+    view = lambda T, i: T[int(offs[i]):int(offs[i + 1])]
+    srv_args = dict(nworkers=args.workers, max_batch=args.max_batch)
+
+    def barrier():
+        torch.cuda.synchronize()
+        if world > 1:
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    # warm-up steps: one request of every grid and order of the stream (k^2
+    # drawn as in the stream, its own seed), plain and served, so that neither
+    # timed pass pays a first-use cost (library load, cuSOLVER kernels of every
+    # matrix size, allocator pools, GEMM tile tuning)
+    wr = inputs.rng(seed + 55_555)
+    for w in range(W):
+        warm = []
+        for mx, mz in SERVE_GRIDS:
+            for order in SERVE_ORDERS:
+                k2 = 0.0 if w == 0 else (0.0 if wr.random() < 0.1 else float(10.0 ** wr.uniform(-2, 4)))
+                q = {"mx": mx, "mz": mz, "order": order, "k2": k2, "lx": mx / mz, "seed": seed + 77_777 + len(warm)}
+                q["grid"] = smpm.make_grid(mx, mz, order, q["lx"], 1.0)
+                q["grid_served"] = smpm.make_grid(mx, mz, order, q["lx"], 1.0, precision=args.served_precision)
+                q["f"] = torch.from_numpy(serve_rhs(smpm, q["grid"], q["lx"], q["seed"])).to(dev)
+                q["u"] = torch.zeros_like(q["f"])
+                warm.append(q)
+        for q in warm:
+            s = smpm.Solver(q["grid"], q["k2"], stream)
+            s.solve(q["f"], q["u"], tol=TOL)
+            s.close()
+        srv = smpm.Server(**srv_args)
+        _served_pass(srv, warm, lambda i: warm[i]["f"], lambda i: warm[i]["u"])
+        srv.close()
+        del warm
+    barrier()
+
+    clocks = Clocks(local)
     clocks.start()
-    service, iters_plain, res_plain = [], [], []
-    for q in reqs:
-        torch.cuda.synchronize()
-        w0 = time.perf_counter()
+    l0 = smpm.kernel_launches()
+    # 1. plain FP64, one request at a time (setup + solve + release each)
+    service, res_plain, it_plain = [], [], []
+    for i, q in enumerate(reqs):
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
         s = smpm.Solver(q["grid"], q["k2"], stream)
-        st = s.solve(q["f"], q["u_plain"], tol=TOL)
+        st = s.solve(view(Fd, i), view(Up, i), tol=TOL)
         s.close()
-        torch.cuda.synchronize()
-        service.append(time.perf_counter() - w0)
-        iters_plain.append(st.iters)
+        e1.record(stream)
+        e1.synchronize()
+        service.append(e0.elapsed_time(e1) * 1e-3)
         res_plain.append(st.rel_resid_true)
-        q["setup_ms"], q["solve_ms"] = st.setup_ms, st.solve_ms
-    lam = len(reqs) / sum(service)
-    arrivals = np.cumsum(inputs.rng(inputs.seed_for(5) + 7).exponential(1.0 / lam, len(reqs)))
+        it_plain.append(st.iters)
+        q["setup_ms"] = st.setup_ms
+    plain_span = sum(service)
+    lam = N / plain_span                               # the plain path's saturation rate
+    arrivals = np.cumsum(inputs.rng(seed + 7).exponential(1.0 / lam, N))
+    arrivals -= arrivals[0]
     end, lat_plain = 0.0, []
-    for a, sv in zip(arrivals, service):
+    for a, sv in zip(arrivals, service):               # FIFO single server
         end = max(end, a) + sv
         lat_plain.append(end - a)
-    plain_rate = len(reqs) / (end - arrivals[0])
+    barrier()
 
-    # served: submit at the arrival times, poll until every ticket is done
-    l0 = smpm.kernel_launches()
-    tickets, done, lat_served, batch_sizes, res_served = {}, {}, [], [], []
-    t0 = time.perf_counter()
-    nxt = 0
-    while len(done) < len(reqs):
-        now = time.perf_counter() - t0
-        while nxt < len(reqs) and arrivals[nxt] - arrivals[0] <= now:
-            q = reqs[nxt]
-            tickets[srv.submit(q["grid_served"], q["k2"], q["f"], q["u_served"], tol=TOL)] = nxt
-            nxt += 1
-        for tk, i in list(tickets.items()):
-            st = srv.poll(tk)
-            if st is not None:
-                done[i] = time.perf_counter() - t0
-                lat_served.append(st.solve_ms * 1e-3)
-                batch_sizes.append(st.restarts)
-                res_served.append(st.rel_resid_true)
-                del tickets[tk]
-        time.sleep(0.0002)
-    served_span = max(done.values())
+    # 2. served, Poisson arrivals at that rate (latency)
+    srv = smpm.Server(**srv_args)
+    arr_span, lat_served, batch_arr, worst_arr = _served_pass(srv, reqs, lambda i: view(Fd, i), lambda i: view(Us, i),
+                                                              arrivals)
     torch.cuda.synchronize()
+    srv.close()
+    barrier()
+
+    # 3. served capacity: the whole stream submitted at once (the value)
+    srv = smpm.Server(**srv_args)
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    burst_wall, _, batch_burst, worst_burst = _served_pass(srv, reqs, lambda i: view(Fd, i), lambda i: view(Ub, i))
+    torch.cuda.synchronize()
+    e1.record(stream)
+    e1.synchronize()
+    burst_span = e0.elapsed_time(e1) * 1e-3
+    srv.close()
     launches = smpm.kernel_launches() - l0
+    barrier()
 
-    # served capacity: the whole stream submitted at once (offered load above
-    # what the server completes) to a fresh server (empty operator cache: only
-    # repeats within the stream reuse operators), results checked against the
-    # first pass
-    srv.close()
-    srv = smpm.Server(nworkers=args.workers, max_batch=args.max_batch)
-    for q in reqs:
-        q["u_burst"] = torch.zeros_like(q["f"])
-    t0 = time.perf_counter()
-    burst = [srv.submit(q["grid_served"], q["k2"], q["f"], q["u_burst"], tol=TOL) for q in reqs]
-    pend = set(burst)
-    res_burst = []
-    while pend:
-        for tk in list(pend):
-            st = srv.poll(tk)
-            if st is not None:
-                res_burst.append(st.rel_resid_true)
-                pend.discard(tk)
-        time.sleep(0.0002)
-    burst_span = time.perf_counter() - t0
+    # 4. e2e: the same burst with f and u in pinned host memory
+    srv = smpm.Server(**srv_args)
     torch.cuda.synchronize()
-    clk = clocks.stop()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    _, _, _, worst_e2e = _served_pass(srv, reqs, lambda i: view(Fh, i), lambda i: view(Uh, i))
+    torch.cuda.synchronize()
+    e1.record(stream)
+    e1.synchronize()
+    e2e_span = e0.elapsed_time(e1) * 1e-3
     srv.close()
-    diffs_burst = [float(torch.linalg.norm(q["u_burst"] - q["u_plain"]) / torch.linalg.norm(q["u_plain"]))
-                   for q in reqs]
-    diffs = [float(torch.linalg.norm(q["u_served"] - q["u_plain"]) / torch.linalg.norm(q["u_plain"])) for q in reqs]
+    barrier()
+    clk = clocks.stop()
 
-    def pct(v, p):
-        return float(np.percentile(np.asarray(v) * 1e3, p))
+    # results: every served result against the plain FP64 one (relative 2-norm
+    # and max-norm), the host-buffer results against the device ones
+    def diffs(U):
+        d2, dm = 0.0, 0.0
+        for i in range(N):
+            a, b = view(U, i), view(Up, i)
+            nb_ = float(torch.linalg.norm(b))
+            d2 = max(d2, float(torch.linalg.norm(a - b)) / nb_)
+            dm = max(dm, float((a - b).abs().max() / b.abs().max()))
+        return d2, dm
+    d_arr, dmax_arr = diffs(Us)
+    d_burst, dmax_burst = diffs(Ub)
+    d_e2e = float((Uh.to(dev) - Ub).abs().max() / Ub.abs().max())
 
-    by_grid = {}
-    for q, sv in zip(reqs, service):
-        key = f'{q["mx"]}x{q["mz"]} p{q["order"]}'
-        e = by_grid.setdefault(key, {"n": 0, "service_ms": 0.0, "setup_ms": 0.0})
-        e["n"] += 1
-        e["service_ms"] += sv * 1e3
-        e["setup_ms"] += q["setup_ms"]
-    for e in by_grid.values():
-        e["service_ms"] /= e["n"]
-        e["setup_ms"] /= e["n"]
-    line = {"workload": f"serving: {len(reqs)} Poisson/Helmholtz requests, grids {SERVE_GRIDS} on [0, mx/mz] x [0, 1], "
-                        f"orders {SERVE_ORDERS}, k^2 = 0 (10 %) else log-uniform [1e-2, 1e4], cos-cos f; Poisson "
-                        f"arrivals at the plain path's saturation rate {lam:.2f}/s",
-            "metric": "solves/s at 1e-10 rel. residual, p50/p99 latency: served vs plain FP64",
-            "unit": "solves/s", "value": len(reqs) / burst_span, "dtype": "f64", "data": "synthetic",
-            "value_is": "served capacity: the stream submitted at once",
-            "served": {"precision": ["FP64", "mixed: FP64 FGMRES, FP32 block-Jacobi",
-                                     "nested mixed"][args.served_precision],
-                       "capacity_solves_per_s": len(reqs) / burst_span,
-                       "solves_per_s_at_arrival_rate": len(reqs) / served_span, "p50_ms": pct(lat_served, 50),
-                       "p99_ms": pct(lat_served, 99), "workers": args.workers, "max_batch": args.max_batch,
-                       "mean_batch": float(np.mean(batch_sizes)),
-                       "worst_rel_resid": max(max(res_served), max(res_burst))},
-            "plain_fp64": {"capacity_solves_per_s": lam, "solves_per_s_at_arrival_rate": plain_rate,
-                           "p50_ms": pct(lat_plain, 50), "p99_ms": pct(lat_plain, 99),
-                           "mean_service_ms": 1e3 * float(np.mean(service)), "worst_rel_resid": max(res_plain)},
-            "served_vs_plain_max_rel_diff": max(max(diffs), max(diffs_burst)),
+    # 5. roofline of the dense products in this mix: the first requests re-run
+    # through a server with the per-launch profile on (events around every
+    # dense-product launch, so not timed above)
+    P = min(N, args.profiled_requests)
+    smpm.profile_all(True)
+    smpm.profile_split(None, reset=True)
+    srv = smpm.Server(**srv_args)
+    _served_pass(srv, reqs[:P], lambda i: view(Fd, i), lambda i: view(Ub, i))
+    torch.cuda.synchronize()
+    srv.close()
+    prof = smpm.profile_split(None, reset=True)
+    smpm.profile_all(False)
+    fp64, fp32 = prof["fp64"], prof["fp32"]
+    ach64 = fp64["flops"] / (fp64["ms"] * 1e-3) / 1e12 if fp64["ms"] > 0 else None
+    ach32 = fp32["flops"] / (fp32["ms"] * 1e-3) / 1e12 if fp32["ms"] > 0 else None
+    roofline = {"bound": "alu", "kernel": "mirror_gemm_kernel + class_gemm_kernel, FP64 launches (Schur products, "
+                                          "block-Jacobi, strip-solver slots) of the served mix",
+                "achieved": ach64, "peak": FP64_NOMINAL_TFLOPS, "unit": "TFLOP/s",
+                "frac": ach64 / FP64_NOMINAL_TFLOPS if ach64 else None, "traffic": None,
+                "peak_source": "recipe FP64 1.25 TFLOP/s (GB300; MEASURED_PEAKS.json has no FP64 figure)",
+                "flops_per_launch": fp64["flops"] / max(fp64["launches"], 1),
+                "ms_per_launch": fp64["ms"] / max(fp64["launches"], 1), "launches": fp64["launches"],
+                "sample": f"the first {P} requests of the stream re-served with the per-launch profile on",
+                "fp32_launches": {"achieved": ach32, "peak": FP32_SIMT_TFLOPS, "unit": "TFLOP/s",
+                                  "frac": ach32 / FP32_SIMT_TFLOPS if ach32 else None, "launches": fp32["launches"],
+                                  "peak_source": "152 SMs x 128 FP32 lanes x 2 FLOP x 2.07 GHz"}}
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        n_o, secs, cores, biggest = oracle_serve_sample(reqs, args.cpu_seconds)
+        cpu = {"value": n_o / secs, "unit": "solves/s", "cores": cores, "kind": "oracle",
+               "sample": f"the first {n_o} requests of the stream with at most {ORACLE_MAX_NODES} nodes "
+                         f"(largest {biggest}; the larger grids skipped), setup + solve each, {secs:.1f} s"}
+
+    span_max = max_over_ranks(burst_span, dev, world)
+    e2e_max = max_over_ranks(e2e_span, dev, world)
+    bytes_f = total * 8
+    line = {"metric": METRIC_SERVE, "value": N * world / span_max, "unit": "solves/s", "n_gpus": world,
+            "steps": K, "warmup": W, "ms_per_step": 1e3 * span_max / K, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64+f32", "data": "synthetic",
+            "config": {"workload": f"serving: {N} Poisson/Helmholtz requests ({per} per step), grids {SERVE_GRIDS} "
+                                   f"on [0, mx/mz] x [0, 1], orders {SERVE_ORDERS}, k^2 = 0 (10 %) else log-uniform "
+                                   f"[1e-2, 1e4], cos-cos f",
+                       "tol": TOL, "served": "smpm_server: %d workers, batches of <= %d same-grid requests, %s"
+                       % (args.workers, args.max_batch, ["FP64", "mixed (FP32 block-Jacobi)",
+                                                         "nested mixed (FP64 FGMRES, FP32 inner DBJ-GMRES)"][args.served_precision]),
+                       "plain": "smpm_setup + smpm_solve + smpm_release per request, FP64, one at a time",
+                       "arrivals": f"Poisson at the plain path's saturation rate {lam:.2f}/s",
+                       "l2": f"inputs larger than L2: every request reads its own f and writes its own u "
+                             f"({2 * bytes_f / 2**30:.1f} GiB per pass)",
+                       "parallelism": f"independent request streams per GPU x{world}"},
+            "plain_value": N / plain_span,
+            "p50_ms": _pct(lat_served, 50), "p99_ms": _pct(lat_served, 99),
+            "plain_p50_ms": _pct(lat_plain, 50), "plain_p99_ms": _pct(lat_plain, 99),
+            "served": {"capacity_solves_per_s": N / burst_span, "solves_per_s_at_arrival_rate": N / arr_span,
+                       "mean_batch_burst": float(np.mean(batch_burst)), "mean_batch_arrivals": float(np.mean(batch_arr)),
+                       "worst_rel_resid": max(worst_arr, worst_burst, worst_e2e),
+                       "max_rel_diff_vs_plain": max(d_arr, d_burst), "max_abs_diff_vs_plain_rel_to_max": max(dmax_arr, dmax_burst)},
+            "plain_fp64": {"solves_per_s": N / plain_span, "mean_service_ms": 1e3 * plain_span / N,
+                           "worst_rel_resid": max(res_plain), "mean_iters": float(np.mean(it_plain))},
+            "e2e": {"value": N * world / e2e_max, "unit": "solves/s", "h2d_bytes_per_step": bytes_f // K,
+                    "d2h_bytes_per_step": bytes_f // K, "max_diff_vs_device_pass": d_e2e},
+            "gpu_launches": launches, "roofline": roofline, "cpu_baseline": cpu, "clocks": clk,
             "latency": "completion - arrival, operator setup included",
-            "operator_cache": "each pass starts with an empty cache; a request reuses operators only when "
-                              "an earlier request of the same stream had its grid options and k^2",
-            "gpu_launches": launches, "clocks": clk, "per_grid_plain": by_grid}
+            "timing": "CUDA events on the launching stream around each pass, device synchronised on both sides"}
+    if rank == 0 and not args.no_secondary:
+        line["secondary_poisson2d"] = poisson2d_summary(args, smpm, dev, stream)
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        dist.destroy_process_group()
+    return 0
+
+
+def poisson2d_summary(args, smpm, dev, stream, steps=5, warmup=3):
+    """The 256 x 4, order-12 batched FP64 solve (128 right-hand sides) as a
+    secondary figure of the serving line: solves/s with the profile off, and
+    the dense products' FLOP rate from a separate profiled pass."""
+    import torch
+    from paper_1512_01756_gb300 import inputs
+    solver = smpm.Solver(smpm.make_grid(**GRID), 0.0, stream)
+    x, z = solver.coords()
+    F = make_f(x, z, args.rhs, inputs.seed_for(1))
+    Fd = torch.from_numpy(F).to(dev)
+    Ud = torch.empty_like(Fd)
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
+
+    def timed(n):
+        ts, st = [], None
+        for _ in range(n):
+            flush.fill_(1.0)
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            st = solver.solve(Fd, Ud, tol=TOL)
+            e1.record(stream)
+            e1.synchronize()
+            ts.append(e0.elapsed_time(e1))
+        return sum(ts) / len(ts), st
+    timed(warmup)
+    ms, st = timed(steps)
+    solver.profile(True)
+    solver.profile_read(reset=True)
+    ms_prof, _ = timed(steps)
+    prof = solver.profile_read(reset=True)
+    solver.profile(False)
+    solver.close()
+    ach = prof["flops"] / (prof["ms"] * 1e-3) / 1e12 if prof["ms"] > 0 else None
+    return {"workload": WORKLOAD + f", {args.rhs} right-hand sides per step, plain FP64",
+            "solves_per_s": args.rhs / (ms * 1e-3), "ms_per_step": ms, "iters": st.iters,
+            "worst_rel_resid": st.rel_resid_true, "ms_per_step_profiled": ms_prof,
+            "gemm_tflops": ach, "gemm_frac_of_fp64_nominal": ach / FP64_NOMINAL_TFLOPS if ach else None,
+            "gemm_share_of_step": prof["ms"] / (ms_prof * steps)}
+
+
+def run_reference_serve(args):
+    """Reference arm of the serving line: the CPU oracle on the host cores, one
+    request of the same stream per step (requests above ORACLE_MAX_NODES
+    nodes skipped: the oracle takes minutes on them), setup + solve."""
+    rank, _, world = rank_env()
+    if rank != 0:
+        return 0
+    from paper_1512_01756_gb300 import inputs
+    reqs = serve_requests(4 * (args.warmup + args.steps) + 64, inputs.seed_for(5))
+    small = [q for q in reqs if q["r"] <= ORACLE_MAX_NODES]
+    oracle_serve_sample(small[:args.warmup], 0.0, max_count=args.warmup)
+    n, secs, cores, biggest = oracle_serve_sample(small[args.warmup:], 0.0, max_count=args.steps)
+    val = n / secs
+    line = {"impl": "reference", "metric": METRIC_SERVE, "value": val, "unit": "solves/s", "n_gpus": world,
+            "steps": n, "warmup": args.warmup, "ms_per_step": 1e3 * secs / n, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": "serving stream (grids %s, orders %s, k^2 = 0 (10 %%) else log-uniform "
+                                   "[1e-2, 1e4]), requests with at most %d nodes" % (SERVE_GRIDS, SERVE_ORDERS,
+                                                                                   ORACLE_MAX_NODES),
+                       "solver": "oracle Alg. seq, Householder GMRES, one request at a time"},
+            "cpu_baseline": {"value": val, "unit": "solves/s", "cores": cores, "kind": "oracle",
+                             "sample": f"{n} requests of the stream, one per step, setup + solve (largest {biggest})"},
+            "e2e": {"value": val, "unit": "solves/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
     return 0
 
@@ -641,12 +882,12 @@ def run_serve(args):
 def main():
     args = parse()
     if args.impl == "reference":
-        return run_reference(args)
+        return run_reference_serve(args) if args.workload == "serve" else run_reference(args)
     if args.workload == "serve":
         return run_serve(args)
     if args.workload != "poisson2d":
         return run_other(args)
-    return run_ours(args)
+    return run_poisson2d(args)
 
 
 if __name__ == "__main__":

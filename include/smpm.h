@@ -39,7 +39,14 @@
  *   SMPM_INNER_STEPS sets the inner steps of precision 2; SMPM_MIRROR=0|1
  *   (read at setup) turns the mirror-symmetric half-size products of the
  *   interior strips, block-Jacobi pairs and slot inverses off, or on at every
- *   batch size (by default S and M^-1 use them where they save enough work).
+ *   batch size (by default S and M^-1 use them where they save enough work);
+ *   SMPM_PERSISTENT=0 runs the Arnoldi steps of a restart cycle as separate
+ *   launches (graph-replayed step groups) instead of one persistent
+ *   cooperative kernel; SMPM_PERSIST_WAIT_NS sets the time limit of one
+ *   grid-barrier wait of that kernel (default 2e9 ns).  Test hook (it only
+ *   makes the solve fail): SMPM_PERSIST_STALL=1 makes every barrier wait for
+ *   one block more than the grid holds, so the first wait runs out of time
+ *   and the solve returns SMPM_ETIMEOUT.
  */
 #ifndef SMPM_H
 #define SMPM_H
@@ -55,6 +62,8 @@ extern "C" {
 #define SMPM_EBREAKDOWN (-4)  /* NaN/Inf or Arnoldi breakdown                  */
 #define SMPM_ECUDA (-5)       /* a CUDA / cuSOLVER call failed                 */
 #define SMPM_EBUSY (-6)       /* smpm_poll: request still running              */
+#define SMPM_ETIMEOUT (-7)    /* a device-side wait gave up (the persistent kernel's
+                                 grid barrier); the context stays usable       */
 
 typedef struct smpm_solver* smpm_handle;
 
@@ -214,22 +223,36 @@ int smpm_probe_fp64(void* stream, double* tflops);
 /* Profiling of the dense class-GEMM launches (the Schur products, block-Jacobi
  * applies and strip solves): when enabled, every such launch is bracketed by
  * CUDA events on the handle's stream and its algorithmic FLOPs
- * (2 x stored rows x K x active columns) are counted on the device.
- * smpm_profile_read returns the totals since the last reset. */
+ * (2 x stored rows x K x active columns of a full product, 4 x rows x h x
+ * active columns of a mirror-form one) are counted on the device.
+ * smpm_profile_read returns the totals since the last reset (h = NULL: the
+ * totals of every handle of the process).  Profiling turns graph replay off
+ * while it is enabled. */
 int smpm_profile(smpm_handle h, int enable);
 int smpm_profile_read(smpm_handle h, long long* launches, double* flops, double* ms, int reset);
+/* The same totals split by the precision of the launches (precision 0: FP64
+ * products, 1: FP32 products of the mixed forms).  h = NULL reads the totals
+ * of every handle of the process (harvested at the end of each solve), and
+ * smpm_profile(NULL, enable) makes every handle created afterwards profile
+ * (the serving workers' handles included).  SMPM_EINVAL for another
+ * precision. */
+int smpm_profile_split(smpm_handle h, int precision, long long* launches, double* flops, double* ms, int reset);
 
 /* Number of CUDA kernels this library has launched in the process. */
 long long smpm_kernel_launches(void);
 
 /* Allocation-free deflation projection (no counterpart in the paper; an
- * interface for callers that cannot allocate device memory when they call,
- * e.g. code running under CUDA stream capture, real-time loops, or hosts that
- * fix the library's memory up front).  Computes y = P x = x - S Z K Z^T x for
- * operator set 0 of h -- the same result as smpm_apply(h, 2, ...) -- without
- * calling cudaMalloc, cudaFree or any allocating library routine.
+ * interface for callers that cannot allocate device memory when they call:
+ * real-time loops, such as a time stepper projecting every step, that must
+ * not meet the allocator's latency or the device-wide synchronisation that
+ * cudaMalloc / cudaFree can cause, and host applications that give the
+ * library a fixed device-memory budget up front and own every allocation).
+ * Computes y = P x = x - S Z K Z^T x for operator set 0 of h -- the same
+ * result as smpm_apply(h, 2, ...) -- without calling cudaMalloc, cudaFree or
+ * any allocating library routine.
  *   x, y: device pointers to nrhs consecutive k-vectors (interface order as in
- *         smpm_apply); host pointers are rejected with SMPM_EINVAL.
+ *         smpm_apply); y may equal x (in place); host pointers are rejected
+ *         with SMPM_EINVAL.
  *   Scratch: a fixed device array of SMPM_NOALLOC_MAX_DOUBLES doubles inside
  *         the library, held by every GPU that loads it until the process
  *         exits; a call needs 2 * nrhs * d of them (d = (mx - 1) per-interface
@@ -238,7 +261,9 @@ long long smpm_kernel_launches(void);
  *         contents (each call writes every entry it reads first); calls whose
  *         kernels overlap on the GPU race on it, so order them on one stream.
  *   The first call on a device looks up the array's device address
- *         (cudaGetSymbolAddress); make that first call before any stream
+ *         (cudaGetSymbolAddress) and keeps it for the process, which assumes
+ *         the device's primary context is not reset (cudaDeviceReset) while
+ *         the library is in use; make that first call before any stream
  *         capture.  Work is queued on the handle's stream; the call returns
  *         without synchronising. */
 #define SMPM_NOALLOC_MAX_DOUBLES 65536
@@ -260,7 +285,9 @@ int smpm_apply_deflation_noalloc(smpm_handle h, int nrhs, const double* x, doubl
  * its estimated device footprint (operators of each k2, Krylov bases and work
  * vectors per request) fits device_budget_bytes beside the batches in flight
  * (<= 0: 80 % of the free device memory at create time); a batch that fits
- * nowhere runs alone.
+ * nowhere runs alone, and a request whose own footprint exceeds the budget is
+ * refused: smpm_submit still returns SMPM_OK and a ticket, and smpm_poll
+ * reports SMPM_ENOMEM for it.
  *   f, g, u: host or device pointers of r, nb and r doubles, owned by the
  *   caller, which must keep them valid and unchanged until smpm_poll() has
  *   returned something other than SMPM_EBUSY for the ticket.  g may be NULL.

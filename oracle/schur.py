@@ -45,11 +45,22 @@ def shifted_inverse_iteration(M, sigma, steps=3, seed=0):
     return _fix_sign(v)
 
 
-def left_null_sparse(L, steps=3, rel_shift=1e-12, seed=0):
-    """Unit left null vector of a large sparse singular L: inverse iteration
-    with a sparse LU of (L^T - sigma I), sigma a tiny multiple of max|L|."""
-    sigma = rel_shift * abs(L).max()
-    T = (L.T - sigma * sp.identity(L.shape[0])).tocsc()
+def left_null_sparse(L, steps=4, rel_shift=1e-12, seed=0):
+    """Unit left null vector of a large sparse singular L: the shifted inverse
+    iteration of Sec. 2.4 (a few solves with a sparse LU of M^T - sigma I),
+    run on the row-equilibrated operator M = D L, D = diag(1 / max_j |L_ij|).
+
+    The rows of the SMPM operator span many orders of magnitude (the penalty
+    rows carry tau (u + n.grad u) with tau ~ (N (N+1) / h)^2, the interior rows
+    only the Laplacian), so a shift that is "small" against max |L| can exceed
+    the smallest nonzero eigenvalue of L on long or finely stretched meshes,
+    and the iteration then converges to a mixture of eigenvectors.  On M every
+    row has unit size, sigma = rel_shift stays far below M's smallest nonzero
+    eigenvalue, and the left null vector of L is D times that of M
+    (w^T M = 0  <=>  (D w)^T L = 0)."""
+    d = 1.0 / abs(L).max(axis=1).toarray().ravel()
+    M = (sp.diags(d) @ L).tocsr()
+    T = (M.T - rel_shift * sp.identity(L.shape[0])).tocsc()
     lu = spla.splu(T)
     rng = np.random.default_rng(seed)
     v = rng.standard_normal(L.shape[0])
@@ -57,7 +68,8 @@ def left_null_sparse(L, steps=3, rel_shift=1e-12, seed=0):
     for _ in range(steps):
         v = lu.solve(v)
         v /= np.linalg.norm(v)
-    return _fix_sign(v)
+    u = d * v
+    return _fix_sign(u / np.linalg.norm(u))
 
 
 def alg_schur_direct(g: Grid, f, gb=None, k2=0.0):

@@ -21,6 +21,7 @@
 
 #include <algorithm>
 #include <array>
+#include <atomic>
 #include <chrono>
 #include <cstdlib>
 #include <cstdio>
@@ -158,12 +159,19 @@ struct Solver {
         cudaGraphExec_t exec = nullptr;
         long long launches = 0;              // library kernels in the graph
         std::vector<cudaEvent_t> ev;         // GEMM event pairs (profiling)
+        std::vector<char> f32;               // 1 for an FP32 launch, per event pair
     };
     std::map<std::array<int, 4>, GroupGraph> graphs;
     std::map<std::array<int, 4>, int> group_seen;
     cudaStream_t cap_stream = nullptr;
     std::vector<cudaEvent_t>* cap_events = nullptr;   // set while capturing with profiling on
+    std::vector<char>* cap_f32 = nullptr;
     bool graphs_ok = true;
+    // persistent Arnoldi kernel: barrier counter and status word (device),
+    // off for the handle once a cooperative launch has been refused
+    bool persist_ok = true;
+    unsigned int* d_pbar = nullptr;
+    int* d_pstatus = nullptr;
     bool capturing = false;                 // a group is being captured (no tuning, no syncs)
     void drop_graphs() {
         for (auto& kv : graphs) {
@@ -175,10 +183,11 @@ struct Solver {
     }
     bool prof = false;
     std::vector<cudaEvent_t> ev;
+    std::vector<char> ev_f32;               // precision of each recorded launch (1 = FP32)
     int ev_used = 0;
-    unsigned long long* d_flops = nullptr;
-    long long prof_launches = 0;
-    double prof_ms = 0.0, prof_flops = 0.0;
+    unsigned long long* d_flops = nullptr;  // [0] FP64 launches, [1] FP32 launches
+    long long prof_launches[2] = {0, 0};    // per precision: FP64, FP32
+    double prof_ms[2] = {0.0, 0.0}, prof_flops[2] = {0.0, 0.0};
 
     template <class T>
     T* dalloc(size_t n, std::vector<void*>& list) {
@@ -1347,14 +1356,18 @@ static constexpr int kEventPairs = 8192;
 static std::mutex g_tune_mu;
 static std::map<std::array<int, 7>, int> g_tune;
 
-static int tune_shape(Solver& S, GemmArgs& a, const TileSet& ts, int epi, bool& launched) {
-    launched = false;
-    if (ts.n[1] <= 0 || epi == 3) return 0;
+static std::array<int, 7> tune_key(const GemmArgs& a, const TileSet& ts, int epi) {
     int dev = 0;
     cudaGetDevice(&dev);
     int bucket = 0;
     while ((1 << (bucket + 1)) <= ts.n[0]) ++bucket;
-    const std::array<int, 7> key{dev, epi, a.fp32, a.M, a.K, bucket, a.mirror_nb};
+    return {dev, epi, a.fp32, a.M, a.K, bucket, a.mirror_nb};
+}
+
+static int tune_shape(Solver& S, GemmArgs& a, const TileSet& ts, int epi, bool& launched) {
+    launched = false;
+    if (ts.n[1] <= 0 || epi == 3) return 0;
+    const std::array<int, 7> key = tune_key(a, ts, epi);
     {
         std::lock_guard<std::mutex> lk(g_tune_mu);
         auto it = g_tune.find(key);
@@ -1393,7 +1406,8 @@ static void run_gemm(Solver& S, GemmArgs a, const TileSet& ts, int epi) {
     const Tile* tiles = ts.t[sh];
     const int ntiles = ts.n[sh];
     if (S.prof && S.cap_events) {   // inside a graph capture: the graph owns its events
-        a.flops = S.d_flops;
+        a.flops = S.d_flops + (a.fp32 ? 1 : 0);
+        S.cap_f32->push_back(a.fp32 ? 1 : 0);
         cudaEvent_t e0, e1;
         CK(cudaEventCreate(&e0));
         CK(cudaEventCreate(&e1));
@@ -1407,13 +1421,70 @@ static void run_gemm(Solver& S, GemmArgs a, const TileSet& ts, int epi) {
         return;
     }
     const bool rec = S.prof && S.ev_used < kEventPairs;
-    if (S.prof) a.flops = S.d_flops;
-    if (rec) CK(cudaEventRecord(S.ev[2 * S.ev_used], S.stream));
+    if (S.prof) a.flops = S.d_flops + (a.fp32 ? 1 : 0);
+    if (rec) {
+        S.ev_f32[S.ev_used] = a.fp32 ? 1 : 0;
+        CK(cudaEventRecord(S.ev[2 * S.ev_used], S.stream));
+    }
     launch_class_gemm(a, tiles, ntiles, epi, S.stream);
     if (rec) {
         CK(cudaEventRecord(S.ev[2 * S.ev_used + 1], S.stream));
         ++S.ev_used;
     }
+}
+
+// Tile shape a launch of this kind uses (tuning it now, on the real
+// operands, if it has not been tuned in this process yet).
+static int shape_for(Solver& S, const GemmArgs& a, const TileSet& ts, int epi) {
+    if (const char* e = std::getenv("SMPM_TILE_SHAPE")) return std::atoi(e) & 1;
+    if (ts.n[1] <= 0 || epi == 3) return 0;
+    const std::array<int, 7> key = tune_key(a, ts, epi);
+    for (int pass = 0; pass < 2; ++pass) {
+        {
+            std::lock_guard<std::mutex> lk(g_tune_mu);
+            auto it = g_tune.find(key);
+            if (it != g_tune.end()) return it->second;
+        }
+        if (pass == 0) run_gemm(S, a, ts, epi);
+    }
+    return 0;
+}
+
+// One dense-product launch (arguments, tile lists, epilogue).
+struct GemmCall {
+    GemmArgs a;
+    const TileSet* ts;
+    int epi;
+};
+
+static PGemm to_pgemm(Solver& S, const GemmCall& c) {
+    const int sh = shape_for(S, c.a, *c.ts, c.epi);
+    const int bm = sh == 1 ? 8 : 16;
+    PGemm g;
+    g.a = c.a;
+    g.a.shape = sh;
+    g.tiles = c.ts->t[sh];
+    g.ntiles = c.ts->n[sh];
+    g.nrow = (c.a.M + bm - 1) / bm;
+    g.epi = c.epi;
+    return g;
+}
+
+// Process-wide profile totals (every handle's harvested launches; per
+// precision: [0] FP64, [1] FP32), and whether new handles profile.
+static std::mutex g_prof_mu;
+static long long g_prof_launches[2] = {0, 0};
+static double g_prof_ms[2] = {0.0, 0.0}, g_prof_flops[2] = {0.0, 0.0};
+static std::atomic<int> g_prof_default{0};
+
+static void add_prof(Solver& S, int p, long long n, double ms, double flops) {
+    S.prof_launches[p] += n;
+    S.prof_ms[p] += ms;
+    S.prof_flops[p] += flops;
+    std::lock_guard<std::mutex> lk(g_prof_mu);
+    g_prof_launches[p] += n;
+    g_prof_ms[p] += ms;
+    g_prof_flops[p] += flops;
 }
 
 // Accumulate the recorded GEMM launches (after the stream has drained).
@@ -1422,21 +1493,21 @@ static void harvest_profile(Solver& S) {
     for (int i = 0; i < S.ev_used; ++i) {
         float ms = 0.f;
         CK(cudaEventElapsedTime(&ms, S.ev[2 * i], S.ev[2 * i + 1]));
-        S.prof_ms += ms;
+        add_prof(S, S.ev_f32[i] ? 1 : 0, 1, ms, 0.0);
     }
-    S.prof_launches += S.ev_used;
     S.ev_used = 0;
-    unsigned long long fl = 0;
-    CK(cudaMemcpy(&fl, S.d_flops, sizeof(fl), cudaMemcpyDeviceToHost));
-    S.prof_flops += (double)fl;
+    unsigned long long fl[2] = {0, 0};
+    CK(cudaMemcpy(fl, S.d_flops, sizeof(fl), cudaMemcpyDeviceToHost));
+    add_prof(S, 0, 0, 0.0, (double)fl[0]);
+    add_prof(S, 1, 0, 0.0, (double)fl[1]);
     CK(cudaMemset(S.d_flops, 0, sizeof(fl)));
 }
 
 // Schur product out = add + sum_i scatter_i G_i gather_i in (Sec. 3.1,
 // assembled blocks) with the FP64 blocks or their FP32 copies; the interior
 // strips go through the mirror form when the handle has it.
-static void schur_product(Solver& S, const double* in, long long in_rs, long long in_off, double* out,
-                          const double* add, const int* active, bool fp32) {
+static int schur_calls(Solver& S, const double* in, long long in_rs, long long in_off, double* out,
+                       const double* add, const int* active, bool fp32, GemmCall* c) {
     const int fz = S.g.fz, f2 = 2 * fz;
     GemmArgs a = gemm_base(S);
     a.mats = fp32 ? reinterpret_cast<const double*>(S.G32) : S.G;
@@ -1449,19 +1520,27 @@ static void schur_product(Solver& S, const double* in, long long in_rs, long lon
     a.active = active;
     const double* h = fp32 ? reinterpret_cast<const double*>(S.Gh32) : S.Gh;
     if (!S.useG || h == nullptr) {
-        run_gemm(S, a, S.wk.tG, 1);
-        return;
+        c[0] = GemmCall{a, &S.wk.tG, 1};
+        return 1;
     }
-    run_gemm(S, a, S.wk.tGb, 1);
+    c[0] = GemmCall{a, &S.wk.tGb, 1};
     a.mats = h; a.mat_stride = 2LL * fz * fz; a.M = a.K = fz; a.mirror_nb = 2; a.face = fz;
-    run_gemm(S, a, S.wk.tGm, 1);
+    c[1] = GemmCall{a, &S.wk.tGm, 1};
+    return 2;
+}
+
+static void schur_product(Solver& S, const double* in, long long in_rs, long long in_off, double* out,
+                          const double* add, const int* active, bool fp32) {
+    GemmCall c[2];
+    const int n = schur_calls(S, in, in_rs, in_off, out, add, active, fp32, c);
+    for (int i = 0; i < n; ++i) run_gemm(S, c[i].a, *c[i].ts, c[i].epi);
 }
 
 // Block-Jacobi apply out = M_p^-1 in over the pairs p (faces [(4p+1) fz,
 // (4p+5) fz), Sec. 3.2); the interior pairs through the mirror form when the
 // handle has it.
-static void bj_apply(Solver& S, const double* in, long long in_rs, long long in_off, double* out, long long out_rs,
-                     long long out_off, const int* active, bool fp32) {
+static int bj_calls(Solver& S, const double* in, long long in_rs, long long in_off, double* out, long long out_rs,
+                    long long out_off, const int* active, bool fp32, GemmCall* c) {
     const int fz = S.g.fz, f4 = 4 * fz;
     GemmArgs a = gemm_base(S);
     a.mats = fp32 ? reinterpret_cast<const double*>(S.Minv32) : S.Minv;
@@ -1473,12 +1552,20 @@ static void bj_apply(Solver& S, const double* in, long long in_rs, long long in_
     a.active = active;
     const double* h = fp32 ? reinterpret_cast<const double*>(S.Mh32) : S.Mh;
     if (!S.useM || h == nullptr) {
-        run_gemm(S, a, S.wk.tM, 0);
-        return;
+        c[0] = GemmCall{a, &S.wk.tM, 0};
+        return 1;
     }
-    run_gemm(S, a, S.wk.tMb, 0);
+    c[0] = GemmCall{a, &S.wk.tMb, 0};
     a.mats = h; a.mat_stride = 8LL * fz * fz; a.M = a.K = 2 * fz; a.mirror_nb = 4; a.face = fz;
-    run_gemm(S, a, S.wk.tMm, 0);
+    c[1] = GemmCall{a, &S.wk.tMm, 0};
+    return 2;
+}
+
+static void bj_apply(Solver& S, const double* in, long long in_rs, long long in_off, double* out, long long out_rs,
+                     long long out_off, const int* active, bool fp32) {
+    GemmCall c[2];
+    const int n = bj_calls(S, in, in_rs, in_off, out, out_rs, out_off, active, fp32, c);
+    for (int i = 0; i < n; ++i) run_gemm(S, c[i].a, *c[i].ts, c[i].epi);
 }
 
 static int solve_impl(Solver& S, const std::vector<int>& ops, const double* f, const double* gb, double tol,
@@ -1675,6 +1762,16 @@ static int solve_impl(Solver& S, const std::vector<int>& ops, const double* f, c
     bool first = true;
     const int check_every = 4;
     const bool graphs_off = std::getenv("SMPM_NO_GRAPHS") != nullptr;
+    // SMPM_PERSISTENT=0: step groups of separate launches (graph-replayed)
+    // instead of the persistent kernel; SMPM_PERSIST_WAIT_NS: time limit of a
+    // barrier wait (default 2 s); SMPM_PERSIST_STALL=1: test hook, every
+    // barrier waits for a block that does not exist, so the first wait runs
+    // out of time and the solve returns SMPM_ETIMEOUT
+    const char* pe = std::getenv("SMPM_PERSISTENT");
+    const bool persist_off = pe != nullptr && std::atoi(pe) == 0;
+    const char* pw = std::getenv("SMPM_PERSIST_WAIT_NS");
+    const long long persist_wait_ns = pw ? std::max(1000LL, std::atoll(pw)) : 2000000000LL;
+    const bool persist_stall = std::getenv("SMPM_PERSIST_STALL") != nullptr;
     // Extended-precision refinement: when the true residual stalls near tol
     // (the FP64 rounding floor of S x_S, ~ eps |G| |x_S|, reached when |x_S| is
     // far above |b_S|), the iterate is kept as x_S + x_lo (double-double), and
@@ -1805,6 +1902,51 @@ static int solve_impl(Solver& S, const std::vector<int>& ops, const double* f, c
             k_cgs(ka, jj, 2, st_);
             k_normalize(ka, jj, last_allowed, st_);
         };
+        // every step of this cycle in one persistent launch (the default for
+        // precisions 0 and 1 when the profile is off)
+        const bool use_persist = S.persist_ok && !persist_off && !nested && !S.prof;
+        if (use_persist) {
+            if (!S.d_pbar) {
+                S.d_pbar = S.dalloc<unsigned int>(1, S.allocs);
+                S.d_pstatus = S.dalloc<int>(1, S.allocs);
+            }
+            PersistArgs pa;
+            std::memset(&pa, 0, sizeof(pa));
+            pa.ka = ka;
+            GemmCall calls[2];
+            for (int set = 0; set < 2; ++set) {
+                if (set == 1 && !bj_fp32) break;
+                pa.nbj[set] = bj_calls(S, w.V, (long long)(m + 1) * ld, 0, w.z, ld, 0, w.active, set == 1, calls);
+                for (int i = 0; i < pa.nbj[set]; ++i) pa.bj[set][i] = to_pgemm(S, calls[i]);
+            }
+            pa.nsc = schur_calls(S, w.z, ld, 0, w.w, w.z, w.active, false, calls);
+            for (int i = 0; i < pa.nsc; ++i) pa.sc[i] = to_pgemm(S, calls[i]);
+            pa.bj_step = ld;
+            pa.j0 = 0;
+            pa.last_allowed = last_allowed;
+            pa.use_fp32 = bj_fp32 ? 1 : 0;
+            pa.fp64_steps = cycles == 0 ? check_every : 0;    // precision 1: the first group in FP64
+            pa.Zb = mixed ? w.Zb : nullptr;
+            pa.z = w.z;
+            pa.bar = S.d_pbar;
+            pa.status = S.d_pstatus;
+            pa.wait_ns = persist_wait_ns;
+            pa.stall = persist_stall ? 1 : 0;
+            CK(cudaMemsetAsync(S.d_pbar, 0, sizeof(unsigned int), st_));
+            CK(cudaMemsetAsync(S.d_pstatus, 0, sizeof(int), st_));
+            if (k_arnoldi_persistent(pa, st_)) {
+                int h_status = 0;
+                CK(cudaMemcpyAsync(&h_status, S.d_pstatus, sizeof(int), cudaMemcpyDeviceToHost, st_));
+                CK(cudaMemcpyAsync(h_active.data(), w.active, R * sizeof(int), cudaMemcpyDeviceToHost, st_));
+                CK(cudaStreamSynchronize(st_));
+                if (h_status != 0)
+                    throw Err{SMPM_ETIMEOUT, "persistent Arnoldi kernel: a grid barrier wait ran out of time"};
+                j = last_allowed;
+            } else {
+                cudaGetLastError();
+                S.persist_ok = false;                   // step-group launches from now on
+            }
+        }
         while (j < last_allowed) {
             const int cnt = std::min(check_every - j % check_every, last_allowed - j);
             // precision 1: the first step group of the first cycle applies the
@@ -1824,7 +1966,10 @@ static int solve_impl(Solver& S, const std::vector<int>& ops, const double* f, c
                     Solver::GroupGraph g_new;
                     cudaStream_t keep = S.stream;
                     S.stream = st_ = S.cap_stream;
-                    if (S.prof) S.cap_events = &g_new.ev;
+                    if (S.prof) {
+                        S.cap_events = &g_new.ev;
+                        S.cap_f32 = &g_new.f32;
+                    }
                     const long long l0 = launch_count();
                     cudaGraph_t graph = nullptr;
                     cudaError_t e1 = cudaStreamBeginCapture(S.cap_stream, cudaStreamCaptureModeThreadLocal);
@@ -1837,6 +1982,7 @@ static int solve_impl(Solver& S, const std::vector<int>& ops, const double* f, c
                             if (graph) cudaGraphDestroy(graph);
                             S.stream = st_ = keep;
                             S.cap_events = nullptr;
+                            S.cap_f32 = nullptr;
                             S.capturing = false;
                             throw;
                         }
@@ -1845,6 +1991,7 @@ static int solve_impl(Solver& S, const std::vector<int>& ops, const double* f, c
                     }
                     S.stream = st_ = keep;
                     S.cap_events = nullptr;
+                    S.cap_f32 = nullptr;
                     g_new.launches = launch_count() - l0;
                     count_launches((int)-g_new.launches);     // counted again at every replay
                     if (e1 == cudaSuccess && graph)
@@ -1872,8 +2019,7 @@ static int solve_impl(Solver& S, const std::vector<int>& ops, const double* f, c
                 for (size_t e = 0; e + 1 < gg->ev.size(); e += 2) {
                     float ms = 0.f;
                     CK(cudaEventElapsedTime(&ms, gg->ev[e], gg->ev[e + 1]));
-                    S.prof_ms += ms;
-                    ++S.prof_launches;
+                    add_prof(S, gg->f32[e / 2] ? 1 : 0, 1, ms, 0.0);
                 }
             }
             bool any = false;
@@ -2024,6 +2170,38 @@ static int apply_impl(Solver& S, int kind, int R, const double* in, double* out)
     return SMPM_OK;
 }
 
+static void profile_enable(Solver& S, bool enable) {
+    if (enable && S.ev.empty()) {
+        S.ev.resize(2 * kEventPairs);
+        S.ev_f32.assign(kEventPairs, 0);
+        for (auto& e : S.ev) CK(cudaEventCreate(&e));
+        S.d_flops = S.dalloc<unsigned long long>(2, S.allocs);
+        CK(cudaMemsetAsync(S.d_flops, 0, 2 * sizeof(unsigned long long), S.stream));
+    }
+    if (S.prof != enable) {
+        CK(cudaStreamSynchronize(S.stream));
+        S.drop_graphs();
+    }
+    S.prof = enable;
+}
+
+// Totals of precision p (0 FP64, 1 FP32) of handle h, or of the process for h = NULL.
+static void read_prof(smpm_handle h, int p, int reset, long long& n, double& f, double& t) {
+    if (h) {
+        Solver& S = *(Solver*)h;
+        n += S.prof_launches[p];
+        f += S.prof_flops[p];
+        t += S.prof_ms[p];
+        if (reset) { S.prof_launches[p] = 0; S.prof_flops[p] = 0.0; S.prof_ms[p] = 0.0; }
+        return;
+    }
+    std::lock_guard<std::mutex> lk(g_prof_mu);
+    n += g_prof_launches[p];
+    f += g_prof_flops[p];
+    t += g_prof_ms[p];
+    if (reset) { g_prof_launches[p] = 0; g_prof_flops[p] = 0.0; g_prof_ms[p] = 0.0; }
+}
+
 static Solver* make_solver(const smpm_grid* grid, int nop, const double* k2, void* stream) {
     if (!grid) throw Err{SMPM_EINVAL, "grid is null"};
     if (nop < 1) throw Err{SMPM_EINVAL, "need at least one k^2"};
@@ -2048,6 +2226,7 @@ static Solver* make_solver(const smpm_grid* grid, int nop, const double* k2, voi
     if (const char* e = std::getenv("SMPM_INNER_STEPS"))   // inner Arnoldi steps of precision 2
         S->inner_m = std::min(64, std::max(2, std::atoi(e)));
     setup_solver(*S);
+    if (g_prof_default.load()) profile_enable(*S, true);
     return S.release();
 }
 
@@ -2070,14 +2249,6 @@ static int guarded(F&& fn) {
 
 // Operator data of operator set 0 for the allocation-free deflation
 // projection (noalloc.cu); reads the handle only.
-struct DeflView {
-    int fz, mx, ng, d;
-    long long k;
-    const double* K;
-    const double* rho;
-    const int* strip_cls;
-    cudaStream_t stream;
-};
 
 bool deflation_view(smpm_handle h, DeflView* v, std::string& msg) {
     if (!h) { msg = "null handle"; return false; }
@@ -2345,31 +2516,36 @@ const char* smpm_last_error(void) { return g_last_error.c_str(); }
 
 int smpm_profile(smpm_handle h, int enable) {
     return guarded([&] {
-        if (!h) throw Err{SMPM_EINVAL, "null handle"};
-        Solver& S = *(Solver*)h;
-        if (enable && S.ev.empty()) {
-            S.ev.resize(2 * kEventPairs);
-            for (auto& e : S.ev) CK(cudaEventCreate(&e));
-            S.d_flops = S.dalloc<unsigned long long>(1, S.allocs);
-            CK(cudaMemset(S.d_flops, 0, sizeof(unsigned long long)));
+        if (!h) {   // process-wide default for the handles created from now on
+            g_prof_default.store(enable != 0);
+            return SMPM_OK;
         }
-        if (S.prof != (enable != 0)) {
-            CK(cudaStreamSynchronize(S.stream));
-            S.drop_graphs();
-        }
-        S.prof = enable != 0;
+        profile_enable(*(Solver*)h, enable != 0);
         return SMPM_OK;
     });
 }
 
 int smpm_profile_read(smpm_handle h, long long* launches, double* flops, double* ms, int reset) {
     return guarded([&] {
-        if (!h) throw Err{SMPM_EINVAL, "null handle"};
-        Solver& S = *(Solver*)h;
-        if (launches) *launches = S.prof_launches;
-        if (flops) *flops = S.prof_flops;
-        if (ms) *ms = S.prof_ms;
-        if (reset) { S.prof_launches = 0; S.prof_flops = 0.0; S.prof_ms = 0.0; }
+        long long n = 0;
+        double f = 0.0, t = 0.0;
+        for (int p = 0; p < 2; ++p) read_prof(h, p, reset, n, f, t);
+        if (launches) *launches = n;
+        if (flops) *flops = f;
+        if (ms) *ms = t;
+        return SMPM_OK;
+    });
+}
+
+int smpm_profile_split(smpm_handle h, int precision, long long* launches, double* flops, double* ms, int reset) {
+    return guarded([&] {
+        if (precision != 0 && precision != 1) throw Err{SMPM_EINVAL, "precision must be 0 (FP64) or 1 (FP32)"};
+        long long n = 0;
+        double f = 0.0, t = 0.0;
+        read_prof(h, precision, reset, n, f, t);
+        if (launches) *launches = n;
+        if (flops) *flops = f;
+        if (ms) *ms = t;
         return SMPM_OK;
     });
 }

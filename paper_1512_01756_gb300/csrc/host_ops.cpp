@@ -309,30 +309,55 @@ void BandLU::solve_T(double* b) const {
     }
 }
 
-// Left null vector by inverse iteration on a band built by `fill`.
+// Left null vector by inverse iteration on a band built by `fill`, after
+// scaling every row to unit maximum (D L: the penalty rows are ~1e6 times
+// the Laplacian rows, and the LU's rounding then stays relative to each row
+// instead of to the largest one).  w^T (D L) = 0 gives u = D w.  The shift
+// sigma = 1e-15 must stay far below the smallest nonzero eigenvalue of D L;
+// a larger one only if that factorisation meets an exact zero pivot.
 static bool left_null_from(int n, int bw, const std::function<void(const Adder&)>& fill,
                            std::vector<double>& v, std::string& msg) {
-    BandLU lu;
-    lu.init(n, bw, bw);
-    double amax = 0.0;
-    fill([&](int i, int j, double x) { lu.at(i, j) += x; });
-    for (int j = 0; j < n; ++j)
-        for (int i = std::max(0, j - bw); i <= std::min(n - 1, j + bw); ++i)
-            amax = std::max(amax, std::fabs(lu.at(i, j)));
-    const double sigma = 1e-12 * amax;
-    for (int i = 0; i < n; ++i) lu.at(i, i) -= sigma;
-    if (!lu.factor()) { msg = "null-vector factorisation hit a zero pivot"; return false; }
-    v.assign(n, 0.0);
-    for (int i = 0; i < n; ++i) v[i] = 1.0 + 0.01 * std::sin(1.0 + 3.0 * i);
-    for (int it = 0; it < 3; ++it) {
-        lu.solve_T(v.data());
+    msg = "null-vector factorisation hit a zero pivot";
+    for (double sigma : {1e-15, 1e-13, 1e-12}) {
+        BandLU lu;
+        lu.init(n, bw, bw);
+        fill([&](int i, int j, double x) { lu.at(i, j) += x; });
+        std::vector<double> d(n, 0.0);
+        for (int i = 0; i < n; ++i) {
+            for (int j = std::max(0, i - bw); j <= std::min(n - 1, i + bw); ++j)
+                d[i] = std::max(d[i], std::fabs(lu.at(i, j)));
+            d[i] = d[i] > 0.0 ? 1.0 / d[i] : 1.0;
+            for (int j = std::max(0, i - bw); j <= std::min(n - 1, i + bw); ++j) lu.at(i, j) *= d[i];
+        }
+        for (int i = 0; i < n; ++i) lu.at(i, i) -= sigma;
+        if (!lu.factor()) continue;
+        std::vector<double> w(n);
+        for (int i = 0; i < n; ++i) w[i] = 1.0 + 0.01 * std::sin(1.0 + 3.0 * i);
+        bool ok = true;
+        for (int it = 0; it < 6 && ok; ++it) {
+            lu.solve_T(w.data());
+            double s = 0.0;
+            for (double x : w) s += x * x;
+            s = std::sqrt(s);
+            if (!(s > 0) || !std::isfinite(s)) {
+                msg = "null-vector iteration diverged";
+                ok = false;
+                break;
+            }
+            for (double& x : w) x /= s;
+        }
+        if (!ok) continue;
+        v.assign(n, 0.0);
         double s = 0.0;
-        for (double x : v) s += x * x;
+        for (int i = 0; i < n; ++i) {
+            v[i] = d[i] * w[i];
+            s += v[i] * v[i];
+        }
         s = std::sqrt(s);
-        if (!(s > 0) || !std::isfinite(s)) { msg = "null-vector iteration diverged"; return false; }
         for (double& x : v) x /= s;
+        return true;
     }
-    return true;
+    return false;
 }
 
 bool left_null_banded(const std::vector<double>& M, int n, int bw, std::vector<double>& v,

@@ -10,6 +10,7 @@
 // FP64 arithmetic is bound by the DFMA pipe on this part, so the dense applies
 // are register-tiled SIMT GEMMs over tiles that share one class matrix; the
 // vector kernels are chunked streams over the face vectors.
+#include <algorithm>
 #include <atomic>
 #include <cmath>
 
@@ -32,14 +33,15 @@ __device__ __forceinline__ double warp_sum(double v) {
     return v;
 }
 
-// Sum over a block of VB threads; every thread gets the result.
+// Sum over a block of NT threads; every thread gets the result.
+template <int NT = VB>
 __device__ __forceinline__ double block_sum(double v, double* sh) {
     v = warp_sum(v);
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
     __syncthreads();
     if (lane == 0) sh[wid] = v;
     __syncthreads();
-    double t = lane < (VB / 32) ? sh[lane] : 0.0;
+    double t = lane < (NT / 32) ? sh[lane] : 0.0;
     t = warp_sum(t);
     return t;
 }
@@ -56,12 +58,24 @@ __device__ __forceinline__ double block_sum(double v, double* sh) {
 // TM: element type of the class matrices and of the arithmetic (double, or
 // float for the FP32 block-Jacobi of the mixed-precision solve: FP64 vectors are
 // rounded to FP32 on load, products accumulate in FP32, results are stored in FP64).
-template <int EPI, typename TM, int BMT = BM>
-__global__ void __launch_bounds__(GT) class_gemm_kernel(GemmArgs a, const Tile* __restrict__ tiles) {
+// Shared-memory words of one GEMM tile: the A slab (BK x (BMT + 1)) and the
+// B slab (BK x (BNT + 4)), both a multiple of 16 bytes; twice that for the
+// mirror form (two A and two B slabs).
+template <typename TM, int BMT>
+__host__ __device__ constexpr int gemm_smem_words() {
+    return BK * (BMT + 1) + BK * (4 * GT / BMT + 4);
+}
+
+// One BMT x BNT output tile of the class GEMM: tile t of the launch, row tile
+// `by`; As_ / Bs_ are the tile's shared slabs (16-byte aligned).  Run by GT
+// threads (threadIdx.x < GT) of one block.
+template <int EPI, typename TM, int BMT>
+__device__ __forceinline__ void class_gemm_tile(const GemmArgs& a, const Tile t, int by, TM* As_, TM* Bs_) {
     constexpr int BNT = 4 * GT / BMT;          // columns per tile (4 per thread)
     constexpr int CG = GT / BMT;               // column groups of four
-    const Tile t = tiles[blockIdx.x];
-    const int row0 = blockIdx.y * BMT;
+    auto As = reinterpret_cast<TM (*)[BMT + 1]>(As_);
+    auto Bs = reinterpret_cast<TM (*)[BNT + 4]>(__builtin_assume_aligned(Bs_, 16));
+    const int row0 = by * BMT;
     const int lo = a.row_lo[t.mat], hi = a.row_hi[t.mat];
     if (row0 >= hi || row0 + BMT <= lo) return;
     if (a.active) {
@@ -77,8 +91,6 @@ __global__ void __launch_bounds__(GT) class_gemm_kernel(GemmArgs a, const Tile* 
         atomicAdd(a.flops, 2ULL * (unsigned long long)max(0, r_hi - r_lo) * (unsigned long long)a.K *
                                (unsigned long long)cols);
     }
-    __shared__ TM As[BK][BMT + 1];
-    __shared__ __align__(16) TM Bs[BK][BNT + 4];
     const TM* __restrict__ A = reinterpret_cast<const TM*>(a.mats) + (long long)t.mat * a.mat_stride;
     const int tid = threadIdx.x;
     const int tr = tid / CG, tc = tid % CG;    // row 0..BMT-1, column group 0..CG-1
@@ -172,6 +184,17 @@ __global__ void __launch_bounds__(GT) class_gemm_kernel(GemmArgs a, const Tile* 
     }
 }
 
+template <int EPI, typename TM, int BMT = BM>
+__global__ void __launch_bounds__(GT) class_gemm_kernel(GemmArgs a, const Tile* __restrict__ tiles) {
+    constexpr int BNT = 4 * GT / BMT;
+    __shared__ TM As[BK][BMT + 1];
+    __shared__ __align__(16) TM Bs[BK][BNT + 4];
+    // 1-D grid, the row tiles of a column tile consecutive: the tile's input
+    // columns are read by all its row tiles while they are still in L2
+    const int nrow = (a.M + BMT - 1) / BMT, tile = blockIdx.x / nrow;
+    class_gemm_tile<EPI, TM, BMT>(a, tiles[tile], blockIdx.x - tile * nrow, &As[0][0], &Bs[0][0]);
+}
+
 // ---------------------------------------------------------------------------
 // Mirror form of the class GEMM.  With uniform h_x an interior strip, and an
 // interior block-Jacobi pair, is symmetric under the reflection of x about its
@@ -211,12 +234,16 @@ __device__ __forceinline__ void mirror_pq(int k, int nb, int face, int rev, int&
     }
 }
 
+// One output tile of the mirror form (two A slabs and two B slabs).
 template <int EPI, typename TM, int BMT>
-__global__ void __launch_bounds__(GT) mirror_gemm_kernel(GemmArgs a, const Tile* __restrict__ tiles) {
+__device__ __forceinline__ void mirror_gemm_tile(const GemmArgs& a, const Tile t, int by, TM* A_, TM* B_) {
     constexpr int BNT = 4 * GT / BMT;
     constexpr int CG = GT / BMT;
-    const Tile t = tiles[blockIdx.x];
-    const int row0 = blockIdx.y * BMT;
+    auto Ap = reinterpret_cast<TM (*)[BMT + 1]>(A_);
+    auto Am = reinterpret_cast<TM (*)[BMT + 1]>(A_ + BK * (BMT + 1));
+    auto Bp = reinterpret_cast<TM (*)[BNT + 4]>(__builtin_assume_aligned(B_, 16));
+    auto Bm = reinterpret_cast<TM (*)[BNT + 4]>(__builtin_assume_aligned(B_ + BK * (BNT + 4), 16));
+    const int row0 = by * BMT;
     const int h = a.M;
     if (row0 >= h) return;
     if (a.active) {
@@ -231,8 +258,6 @@ __global__ void __launch_bounds__(GT) mirror_gemm_kernel(GemmArgs a, const Tile*
         const int rows = min(h, row0 + BMT) - row0;
         atomicAdd(a.flops, 4ULL * (unsigned long long)rows * (unsigned long long)h * (unsigned long long)cols);
     }
-    __shared__ TM Ap[BK][BMT + 1], Am[BK][BMT + 1];
-    __shared__ __align__(16) TM Bp[BK][BNT + 4], Bm[BK][BNT + 4];
     const TM* __restrict__ Hp = reinterpret_cast<const TM*>(a.mats) + (long long)t.mat * a.mat_stride;
     const TM* __restrict__ Hm = Hp + (long long)h * h;
     const int nbm = a.mirror_nb, fz = a.face, rev = (a.mirror_nb - 1) * a.face;
@@ -326,9 +351,18 @@ __global__ void __launch_bounds__(GT) mirror_gemm_kernel(GemmArgs a, const Tile*
     }
 }
 
+template <int EPI, typename TM, int BMT>
+__global__ void __launch_bounds__(GT) mirror_gemm_kernel(GemmArgs a, const Tile* __restrict__ tiles) {
+    constexpr int BNT = 4 * GT / BMT;
+    __shared__ TM Ap[2][BK][BMT + 1];
+    __shared__ __align__(16) TM Bp[2][BK][BNT + 4];
+    const int nrow = (a.M + BMT - 1) / BMT, tile = blockIdx.x / nrow;
+    mirror_gemm_tile<EPI, TM, BMT>(a, tiles[tile], blockIdx.x - tile * nrow, &Ap[0][0][0], &Bp[0][0][0]);
+}
+
 template <int BMT>
 static void launch_shape(const GemmArgs& a, const Tile* d_tiles, int ntiles, int epi, cudaStream_t s) {
-    dim3 grid(ntiles, (a.M + BMT - 1) / BMT);
+    dim3 grid(ntiles * ((a.M + BMT - 1) / BMT));
     if (a.mirror_nb != 0) {
         if (a.fp32 && epi == 1)
             mirror_gemm_kernel<1, float, BMT><<<grid, GT, 0, s>>>(a, d_tiles);
@@ -373,11 +407,13 @@ __device__ __forceinline__ bool gate_ok(const KArgs& a, int r, int gate) {
     return gate == 0 ? a.active[r] != 0 : a.done[r] == 0;
 }
 
-__global__ void deflate_sum_kernel(KArgs a, const double* __restrict__ v, const double* __restrict__ vsub,
-                                   int gate) {
-    const int r = blockIdx.y;
+// Z^T (v - vsub) for right-hand side r: one warp per deflation group, NT
+// threads per (virtual) block bx.
+template <int NT>
+__device__ __forceinline__ void deflate_sum_body(const KArgs& a, const double* __restrict__ v,
+                                                 const double* __restrict__ vsub, int gate, int bx, int r) {
     if (!gate_ok(a, r, gate)) return;
-    const int wg = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
+    const int wg = (bx * NT + (int)threadIdx.x) >> 5, lane = threadIdx.x & 31;
     if (wg >= a.d) return;
     const int t = wg / a.ng, gi = wg % a.ng, gs = a.fz / a.ng;
     const long long off = (long long)r * a.ld + (long long)(2 * t + 1) * a.fz + (long long)gi * gs;
@@ -391,6 +427,11 @@ __global__ void deflate_sum_kernel(KArgs a, const double* __restrict__ v, const 
     if (lane == 0) a.q[(long long)r * a.d + wg] = s;
 }
 
+__global__ void deflate_sum_kernel(KArgs a, const double* __restrict__ v, const double* __restrict__ vsub,
+                                   int gate) {
+    deflate_sum_body<VB>(a, v, vsub, gate, blockIdx.x, blockIdx.y);
+}
+
 static void deflate_sum_gate(const KArgs& a, const double* v, const double* vsub, int gate, cudaStream_t s) {
     dim3 grid((a.d * 32 + VB - 1) / VB, a.R);
     deflate_sum_kernel<<<grid, VB, 0, s>>>(a, v, vsub, gate);
@@ -401,10 +442,11 @@ void k_deflate_sum(const KArgs& a, const double* v, const double* vsub, cudaStre
     deflate_sum_gate(a, v, vsub, 0, s);
 }
 
-__global__ void coarse_kernel(KArgs a, int gate) {
-    const int r = blockIdx.y;
+// c = K q for right-hand side r: one warp per coarse row.
+template <int NT>
+__device__ __forceinline__ void coarse_body(const KArgs& a, int gate, int bx, int r) {
     if (!gate_ok(a, r, gate)) return;
-    const int i = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
+    const int i = (bx * NT + (int)threadIdx.x) >> 5, lane = threadIdx.x & 31;
     if (i >= a.d) return;
     if (!a.K) {                       // no deflation (the outer flexible GMRES of the nested form)
         if (lane == 0) a.c[(long long)r * a.d + i] = 0.0;
@@ -416,6 +458,10 @@ __global__ void coarse_kernel(KArgs a, int gate) {
     for (int j = lane; j < a.d; j += 32) s = fma(K[j], q[j], s);
     s = warp_sum(s);
     if (lane == 0) a.c[(long long)r * a.d + i] = s;
+}
+
+__global__ void coarse_kernel(KArgs a, int gate) {
+    coarse_body<VB>(a, gate, blockIdx.x, blockIdx.y);
 }
 
 void k_coarse(const KArgs& a, cudaStream_t s) {
@@ -476,14 +522,14 @@ __device__ __forceinline__ double zc_at(const KArgs& a, int r, long long e) {
 // ---------------------------------------------------------------------------
 // CGS2 Arnoldi step (Sec. 3.1 orthogonalisation; CGS applied twice)
 // ---------------------------------------------------------------------------
-__global__ void __launch_bounds__(VB) cgs_kernel(KArgs a, int j, int mode) {
-    const int r = blockIdx.y;
+// Chunk bx of right-hand side r; sm: ch + m + 2 + 32 doubles of shared memory.
+template <int NT>
+__device__ __forceinline__ void cgs_body(const KArgs& a, int j, int mode, int bx, int r, double* sm) {
     if (!a.active[r]) return;
-    extern __shared__ double sm[];
     double* wsh = sm;                 // [ch]
     double* hsh = sm + a.ch;          // [m+2]
     double* red = hsh + (a.m + 2);    // [32]
-    const long long e0 = (long long)blockIdx.x * a.ch;
+    const long long e0 = (long long)bx * a.ch;
     const long long e1 = min(e0 + (long long)a.ch, a.kp);
     const int len = (int)(e1 - e0);
     double* w = a.w + (long long)r * a.ld;
@@ -491,38 +537,38 @@ __global__ void __launch_bounds__(VB) cgs_kernel(KArgs a, int j, int mode) {
     const int nv = j + 1;
     const long long pstride = (long long)a.nch * (a.m + 2);
     if (mode == 0) {
-        for (int e = threadIdx.x; e < len; e += VB) {
+        for (int e = threadIdx.x; e < len; e += NT) {
             double x = w[e0 + e] - szc_at(a, r, e0 + e);
             wsh[e] = x;
             w[e0 + e] = x;
         }
     } else {
         const double* pin = (mode == 1 ? a.part1 : a.part2) + (long long)r * pstride;
-        for (int i = threadIdx.x; i < nv; i += VB) {
+        for (int i = threadIdx.x; i < nv; i += NT) {
             double s = 0.0;
             for (int ch = 0; ch < a.nch; ++ch) s += pin[(long long)ch * (a.m + 2) + i];
             hsh[i] = s;
         }
         __syncthreads();
-        for (int e = threadIdx.x; e < len; e += VB) {
+        for (int e = threadIdx.x; e < len; e += NT) {
             double x = w[e0 + e];
             for (int i = 0; i < nv; ++i) x = fma(-Vr[(long long)i * a.ld + e0 + e], hsh[i], x);
             wsh[e] = x;
             w[e0 + e] = x;
         }
-        if (blockIdx.x == 0) {
+        if (bx == 0) {
             if (mode == 1)
-                for (int i = threadIdx.x; i < nv; i += VB) a.htmp[(long long)r * (a.m + 1) + i] = hsh[i];
+                for (int i = threadIdx.x; i < nv; i += NT) a.htmp[(long long)r * (a.m + 1) + i] = hsh[i];
             else
-                for (int i = threadIdx.x; i < nv; i += VB)
+                for (int i = threadIdx.x; i < nv; i += NT)
                     a.Hc[((long long)r * a.m + j) * (a.m + 1) + i] = a.htmp[(long long)r * (a.m + 1) + i] + hsh[i];
         }
     }
     __syncthreads();
     if (mode <= 1) {
-        double* pout = (mode == 0 ? a.part1 : a.part2) + (long long)r * pstride + (long long)blockIdx.x * (a.m + 2);
+        double* pout = (mode == 0 ? a.part1 : a.part2) + (long long)r * pstride + (long long)bx * (a.m + 2);
         const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-        for (int i = wid; i < nv; i += VB / 32) {
+        for (int i = wid; i < nv; i += NT / 32) {
             const double* vi = Vr + (long long)i * a.ld + e0;
             double s = 0.0;
             for (int e = lane; e < len; e += 32) s = fma(vi[e], wsh[e], s);
@@ -531,10 +577,15 @@ __global__ void __launch_bounds__(VB) cgs_kernel(KArgs a, int j, int mode) {
         }
     } else {
         double s = 0.0;
-        for (int e = threadIdx.x; e < len; e += VB) s = fma(wsh[e], wsh[e], s);
-        s = block_sum(s, red);
-        if (threadIdx.x == 0) a.part1[(long long)r * pstride + (long long)blockIdx.x * (a.m + 2)] = s;
+        for (int e = threadIdx.x; e < len; e += NT) s = fma(wsh[e], wsh[e], s);
+        s = block_sum<NT>(s, red);
+        if (threadIdx.x == 0) a.part1[(long long)r * pstride + (long long)bx * (a.m + 2)] = s;
     }
+}
+
+__global__ void __launch_bounds__(VB) cgs_kernel(KArgs a, int j, int mode) {
+    extern __shared__ double sm[];
+    cgs_body<VB>(a, j, mode, blockIdx.x, blockIdx.y, sm);
 }
 
 void k_cgs(const KArgs& a, int j, int mode, cudaStream_t s) {
@@ -544,27 +595,29 @@ void k_cgs(const KArgs& a, int j, int mode, cudaStream_t s) {
     count_launches(1);
 }
 
+template <int NT = VB>
 __device__ double reduce_part(const KArgs& a, int r, int slot, double* red) {
     const long long pstride = (long long)a.nch * (a.m + 2);
     const double* p = a.part1 + (long long)r * pstride;
     double s = 0.0;
-    for (int ch = threadIdx.x; ch < a.nch; ch += VB) s += p[(long long)ch * (a.m + 2) + slot];
-    return block_sum(s, red);
+    for (int ch = threadIdx.x; ch < a.nch; ch += NT) s += p[(long long)ch * (a.m + 2) + slot];
+    return block_sum<NT>(s, red);
 }
 
-__global__ void __launch_bounds__(VB) normalize_kernel(KArgs a, int j, int last_allowed) {
-    const int r = blockIdx.y;
+// beta = ||w||, V[j+1] = w / beta over chunk bx, and (block bx = 0) the Givens
+// update of the Hessenberg column and the convergence flags of rhs r.
+template <int NT>
+__device__ __forceinline__ void normalize_body(const KArgs& a, int j, int last_allowed, int bx, int r, double* red) {
     if (!a.active[r]) return;
-    __shared__ double red[32];
-    const double beta = sqrt(reduce_part(a, r, 0, red));
+    const double beta = sqrt(reduce_part<NT>(a, r, 0, red));
     const bool bad = !(beta > 1e-300) || !isfinite(beta);
-    const long long e0 = (long long)blockIdx.x * a.ch;
+    const long long e0 = (long long)bx * a.ch;
     const long long e1 = min(e0 + (long long)a.ch, a.kp);
     const double* w = a.w + (long long)r * a.ld;
     double* vn = a.V + ((long long)r * (a.m + 1) + (j + 1)) * a.ld;
     const double inv = bad ? 0.0 : 1.0 / beta;
-    for (long long e = e0 + threadIdx.x; e < e1; e += VB) vn[e] = w[e] * inv;
-    if (blockIdx.x == 0 && threadIdx.x == 0) {
+    for (long long e = e0 + threadIdx.x; e < e1; e += NT) vn[e] = w[e] * inv;
+    if (bx == 0 && threadIdx.x == 0) {
         double* h = a.Hc + ((long long)r * a.m + j) * (a.m + 1);
         double* cs = a.cs + (long long)r * a.m;
         double* sn = a.sn + (long long)r * a.m;
@@ -592,10 +645,209 @@ __global__ void __launch_bounds__(VB) normalize_kernel(KArgs a, int j, int last_
     }
 }
 
+__global__ void __launch_bounds__(VB) normalize_kernel(KArgs a, int j, int last_allowed) {
+    __shared__ double red[32];
+    normalize_body<VB>(a, j, last_allowed, blockIdx.x, blockIdx.y, red);
+}
+
 void k_normalize(const KArgs& a, int j, int last_allowed, cudaStream_t s) {
     dim3 grid(a.nch, a.R);
     normalize_kernel<<<grid, VB, 0, s>>>(a, j, last_allowed);
     count_launches(1);
+}
+
+// ---------------------------------------------------------------------------
+// Persistent Arnoldi kernel: every step of a restart cycle (block-Jacobi
+// apply, Schur product, deflation restriction and coarse product, the three
+// CGS2 passes, normalisation and Givens update) for every active right-hand
+// side in one cooperative launch.  Each phase is the work of one of the
+// launches above, spread over the resident blocks as virtual blocks; phases
+// are separated by a grid-wide barrier whose every wait has a time limit:
+// a block that waits longer sets *status and all blocks leave at their next
+// barrier (no block ever spins without bound).
+// ---------------------------------------------------------------------------
+static constexpr int PT = GT;   // threads of a persistent block (one GEMM tile each)
+
+__device__ __forceinline__ unsigned int ld_acquire_u32(const unsigned int* p) {
+    unsigned int v;
+    asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+
+__device__ __forceinline__ unsigned long long global_ns() {
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+// Grid-wide barrier number `epoch` (counted from 1): arrive on the counter,
+// wait until every block of the grid (one more under the stall test) has
+// arrived.  Returns false when this block, or another one, gave up.
+__device__ bool grid_barrier(const PersistArgs& p, unsigned int epoch, int* flag) {
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        const unsigned int target = epoch * gridDim.x + (p.stall ? 1u : 0u);
+        int ok = 1;
+        __threadfence();
+        atomicAdd(p.bar, 1u);
+        const unsigned long long t0 = global_ns();
+        unsigned int spins = 0;
+        while (ld_acquire_u32(p.bar) < target) {
+            if (*(volatile int*)p.status != 0) { ok = 0; break; }
+            if ((++spins & 31u) == 0 && global_ns() - t0 > (unsigned long long)p.wait_ns) {
+                atomicCAS(p.status, 0, 1);
+                ok = 0;
+                break;
+            }
+            __nanosleep(64);
+        }
+        __threadfence();
+        *flag = ok;
+    }
+    __syncthreads();
+    return *flag != 0;
+}
+
+// One tile of a dense product, dispatched on precision, form, epilogue and
+// tile shape; sm: the block's shared memory (16-byte aligned).
+__device__ __forceinline__ void pgemm_tile(const GemmArgs& a, const Tile t, int by, int epi, double* sm) {
+    if (a.mirror_nb != 0) {
+        if (a.fp32) {
+            float* f = reinterpret_cast<float*>(sm);
+            if (a.shape == 1) {
+                if (epi) mirror_gemm_tile<1, float, 8>(a, t, by, f, f + 2 * BK * 9);
+                else mirror_gemm_tile<0, float, 8>(a, t, by, f, f + 2 * BK * 9);
+            } else {
+                if (epi) mirror_gemm_tile<1, float, 16>(a, t, by, f, f + 2 * BK * 17);
+                else mirror_gemm_tile<0, float, 16>(a, t, by, f, f + 2 * BK * 17);
+            }
+        } else {
+            if (a.shape == 1) {
+                if (epi) mirror_gemm_tile<1, double, 8>(a, t, by, sm, sm + 2 * BK * 9);
+                else mirror_gemm_tile<0, double, 8>(a, t, by, sm, sm + 2 * BK * 9);
+            } else {
+                if (epi) mirror_gemm_tile<1, double, 16>(a, t, by, sm, sm + 2 * BK * 17);
+                else mirror_gemm_tile<0, double, 16>(a, t, by, sm, sm + 2 * BK * 17);
+            }
+        }
+        return;
+    }
+    if (a.fp32) {
+        float* f = reinterpret_cast<float*>(sm);
+        if (a.shape == 1) {
+            if (epi) class_gemm_tile<1, float, 8>(a, t, by, f, f + BK * 9);
+            else class_gemm_tile<0, float, 8>(a, t, by, f, f + BK * 9);
+        } else {
+            if (epi) class_gemm_tile<1, float, 16>(a, t, by, f, f + BK * 17);
+            else class_gemm_tile<0, float, 16>(a, t, by, f, f + BK * 17);
+        }
+    } else {
+        if (a.shape == 1) {
+            if (epi) class_gemm_tile<1, double, 8>(a, t, by, sm, sm + BK * 9);
+            else class_gemm_tile<0, double, 8>(a, t, by, sm, sm + BK * 9);
+        } else {
+            if (epi) class_gemm_tile<1, double, 16>(a, t, by, sm, sm + BK * 17);
+            else class_gemm_tile<0, double, 16>(a, t, by, sm, sm + BK * 17);
+        }
+    }
+}
+
+// The tiles of n product launches as one list of virtual blocks; the row
+// tiles of a column tile are consecutive (its input columns are read while
+// they are still in L2).  in_add shifts every launch's input offset.
+__device__ void gemm_phase(const PGemm* g, int n, long long in_add, double* sm) {
+    int total = 0;
+    for (int i = 0; i < n; ++i) total += g[i].ntiles * g[i].nrow;
+    for (int v = blockIdx.x; v < total; v += gridDim.x) {
+        int i = 0, vv = v;
+        while (vv >= g[i].ntiles * g[i].nrow) {
+            vv -= g[i].ntiles * g[i].nrow;
+            ++i;
+        }
+        GemmArgs a = g[i].a;
+        a.in_off += in_add;
+        const int tile = vv / g[i].nrow, by = vv - tile * g[i].nrow;
+        pgemm_tile(a, g[i].tiles[tile], by, g[i].epi, sm);
+        __syncthreads();
+    }
+}
+
+__global__ void __launch_bounds__(PT, 4) arnoldi_persistent_kernel(PersistArgs p) {
+    extern __shared__ __align__(16) double psm[];
+    __shared__ int flag;
+    const KArgs& a = p.ka;
+    unsigned int epoch = 0;
+    const int ngx = (a.d * 32 + PT - 1) / PT;       // virtual blocks per rhs of the deflation phases
+    for (int j = p.j0; j < p.last_allowed; ++j) {
+        const int set = (p.use_fp32 && j >= p.fp64_steps) ? 1 : 0;
+        gemm_phase(p.bj[set], p.nbj[set], (long long)j * p.bj_step, psm);          // z = M^-1 v_j
+        if (!grid_barrier(p, ++epoch, &flag)) return;
+        gemm_phase(p.sc, p.nsc, 0, psm);                                           // w = S z
+        if (p.Zb) {                                                                // FGMRES keeps z_j
+            const long long n = (long long)a.R * a.kp;
+            for (long long e = (long long)blockIdx.x * PT + threadIdx.x; e < n; e += (long long)gridDim.x * PT) {
+                const int r = (int)(e / a.kp);
+                const long long i = e - (long long)r * a.kp;
+                if (a.active[r]) p.Zb[(long long)r * a.m * a.ld + (long long)j * a.ld + i] = p.z[(long long)r * a.ld + i];
+            }
+        }
+        if (!grid_barrier(p, ++epoch, &flag)) return;
+        for (int v = blockIdx.x; v < ngx * a.R; v += gridDim.x) deflate_sum_body<PT>(a, a.w, nullptr, 0, v % ngx, v / ngx);
+        if (!grid_barrier(p, ++epoch, &flag)) return;
+        for (int v = blockIdx.x; v < ngx * a.R; v += gridDim.x) coarse_body<PT>(a, 0, v % ngx, v / ngx);
+        if (!grid_barrier(p, ++epoch, &flag)) return;
+        for (int mode = 0; mode < 3; ++mode) {
+            for (int v = blockIdx.x; v < a.nch * a.R; v += gridDim.x) {
+                cgs_body<PT>(a, j, mode, v % a.nch, v / a.nch, psm);
+                __syncthreads();
+            }
+            if (!grid_barrier(p, ++epoch, &flag)) return;
+        }
+        for (int v = blockIdx.x; v < a.nch * a.R; v += gridDim.x) {
+            normalize_body<PT>(a, j, p.last_allowed, v % a.nch, v / a.nch, psm);
+            __syncthreads();
+        }
+        if (!grid_barrier(p, ++epoch, &flag)) return;
+        int any = 0;
+        for (int r = 0; r < a.R; ++r) any |= *(volatile const int*)(a.active + r);
+        if (!any) return;
+    }
+}
+
+bool k_arnoldi_persistent(const PersistArgs& p, cudaStream_t s) {
+    int dev = 0, coop = 0, sms = 0, per_sm = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return false;
+    cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (!coop) return false;
+    // shared memory: the largest GEMM tile (mirror form, FP64, 8-row tiles)
+    // or the CGS2 chunk buffer
+    const size_t gemm_sm = sizeof(double) * 2 * (size_t)(BK * 9 + BK * (4 * GT / 8 + 4));
+    const size_t cgs_sm = sizeof(double) * (size_t)(p.ka.ch + p.ka.m + 2 + 32);
+    const size_t smem = gemm_sm > cgs_sm ? gemm_sm : cgs_sm;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, arnoldi_persistent_kernel, PT, smem) != cudaSuccess ||
+        per_sm < 1)
+        return false;
+    // as many blocks as the largest phase has virtual blocks, at most what
+    // fits on the device (a small problem keeps its barriers cheap)
+    long long work = (long long)p.ka.nch * p.ka.R;
+    work = std::max(work, (long long)((p.ka.d * 32 + PT - 1) / PT) * p.ka.R);
+    for (int set = 0; set < 2; ++set) {
+        long long t = 0;
+        for (int i = 0; i < p.nbj[set]; ++i) t += (long long)p.bj[set][i].ntiles * p.bj[set][i].nrow;
+        work = std::max(work, t);
+    }
+    long long tsc = 0;
+    for (int i = 0; i < p.nsc; ++i) tsc += (long long)p.sc[i].ntiles * p.sc[i].nrow;
+    work = std::max(work, tsc);
+    const long long cap = (long long)per_sm * sms;
+    PersistArgs q = p;
+    void* args[] = {&q};
+    const dim3 grid((unsigned)std::max(1LL, std::min(cap, work))), block(PT);
+    if (cudaLaunchCooperativeKernel((const void*)arnoldi_persistent_kernel, grid, block, args, smem, s) != cudaSuccess)
+        return false;
+    count_launches(1);
+    return true;
 }
 
 // Residual at the start of a restart cycle: r = (bS - s) - S Z c, c = K Z^T (bS - s).

@@ -72,6 +72,42 @@ void k_deflate_coarse_pending(const KArgs& a, const double* v, cudaStream_t s);
 // x_S += t + Z (c0 - c) for rhs that ran this cycle.
 void k_xs_update(const KArgs& a, double* xS, const double* t, const double* c0, cudaStream_t s);
 
+// One dense-product launch as the persistent Arnoldi kernel runs it: the
+// GEMM arguments, the device tile list of the chosen tile shape (a.shape)
+// and the launch's column tiles and row tiles; a.mirror_nb != 0 selects the
+// mirror form.
+struct PGemm {
+    GemmArgs a;
+    const Tile* tiles;
+    int ntiles, nrow;
+    int epi;                       // 0: store, 1: add a.add
+};
+
+// The Arnoldi steps j0 .. last_allowed-1 of one restart cycle for every
+// active right-hand side in one cooperative launch (Sec. 3, Alg. seq step 4:
+// block-Jacobi apply, Schur product, deflation, CGS2, normalisation and
+// Givens per step), the phases separated by grid-wide barriers.
+struct PersistArgs {
+    KArgs ka;
+    PGemm bj[2][2];                // block-Jacobi launches: [0] FP64 blocks, [1] FP32 blocks
+    int nbj[2];
+    PGemm sc[2];                   // Schur product launches
+    int nsc;
+    long long bj_step;             // block-Jacobi input offset per step (the basis slot stride)
+    int j0, last_allowed;
+    int fp64_steps;                // steps j < fp64_steps use the FP64 blocks
+    int use_fp32;                  // steps from fp64_steps on use the FP32 blocks
+    double* Zb;                    // flexible GMRES: z_j kept at Zb + r*m*ld + j*ld (null: off)
+    const double* z;               // the block-Jacobi output z_j ([R][ld])
+    unsigned int* bar;             // barrier counter, zero at launch
+    int* status;                   // set to 1 by a barrier wait that ran out of time
+    long long wait_ns;             // time limit of one barrier wait
+    int stall;                     // test hook: every barrier waits for one block more than the grid has
+};
+// Launch the persistent kernel on `s` (cooperative launch, as many blocks as
+// fit on the device); false if the device cannot launch it cooperatively.
+bool k_arnoldi_persistent(const PersistArgs& p, cudaStream_t s);
+
 // RHS assembly b = f + tau g at the physical boundary, per rhs; partial
 // dots with u_L for the projection (uL[r] may be null).
 struct GridArgs {

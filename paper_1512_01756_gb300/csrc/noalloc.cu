@@ -1,11 +1,11 @@
 // Allocation-free variant of the deflation projection y = P x = x - S Z K Z^T x.
 //
 // Why it exists: some callers of this library cannot allocate device memory
-// at the point where they need the projection -- code running while a CUDA
-// stream is being captured into a graph (cudaMalloc is not a capturable
-// operation), real-time loops that must not hit the allocator's latency or
-// its synchronisation, and hosts that hand the library a fixed memory budget
-// up front.  smpm_apply() may grow the handle's workspace on first use;
+// at the point where they need the projection -- real-time loops (a time
+// stepper calling the projection every step) that must not hit the
+// allocator's latency or the device-wide synchronisation cudaMalloc and
+// cudaFree can cause, and host applications that hand the library a fixed
+// device-memory budget up front and own every allocation themselves.  smpm_apply() may grow the handle's workspace on first use;
 // smpm_apply_deflation_noalloc() never allocates: its only scratch (the coarse
 // vectors q = Z^T x and c = K q) lives in the file-scope device array below,
 // which every GPU that loads the library holds until the process exits.
@@ -27,18 +27,6 @@
 #include "smpm_internal.h"
 
 namespace smpm {
-
-// View of the operator data a deflation projection needs (filled by api.cu).
-struct DeflView {
-    int fz, mx, ng, d;
-    long long k;
-    const double* K;          // [d][d]
-    const double* rho;        // [3 classes][2 sides][ng][2 fz]
-    const int* strip_cls;     // [mx] (device)
-    cudaStream_t stream;
-};
-bool deflation_view(smpm_handle h, DeflView* v, std::string& msg);
-void set_last_error(const std::string& msg);
 
 static constexpr long long kNoallocMax = SMPM_NOALLOC_MAX_DOUBLES;
 static __device__ __align__(256) double g_noalloc_scratch[kNoallocMax];
@@ -81,8 +69,9 @@ __global__ void na_coarse_kernel(DeflView v, int R, const double* __restrict__ q
 // y = x - S Z c.  Unpadded position i is face F = i / fz + 1 of the strip-face
 // numbering (face 2 s + side); Z c is c_{t,g} on both faces of interface t and S
 // adds the G row sums rho of the two strips touching it.
-__global__ void na_correct_kernel(DeflView v, int R, const double* __restrict__ x, const double* __restrict__ c,
-                                  double* __restrict__ y) {
+// x and y may be the same buffer (each thread reads and then writes its own
+// element), so neither is marked __restrict__.
+__global__ void na_correct_kernel(DeflView v, int R, const double* x, const double* __restrict__ c, double* y) {
     const int r = blockIdx.y;
     const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= v.k || r >= R) return;
@@ -114,7 +103,10 @@ __global__ void na_correct_kernel(DeflView v, int R, const double* __restrict__ 
     y[(long long)r * v.k + i] = x[(long long)r * v.k + i] - val;
 }
 
-// Device address of the scratch array, looked up once per device.
+// Device address of the scratch array, looked up once per device (the
+// cache assumes the device's primary context lives as long as the process:
+// after cudaDeviceReset the module is loaded again and the address must be
+// looked up again, which this cache would not do).
 static std::mutex g_na_mutex;
 static double* g_na_ptr[64] = {nullptr};
 

@@ -332,11 +332,23 @@ int smpm_submit(smpm_server_t srv, const smpm_grid* grid, double k2, const doubl
     q->k2 = k2; q->tol = tol; q->f = f; q->g = g; q->u = u;
     q->t_submit = now_ms();
     *ticket = q->id;
+    // admission: a request whose footprint alone exceeds the budget can never
+    // run; it is refused at once and reported by smpm_poll
+    const long long est = footprint(*grid, 1, 1);
     {
         std::lock_guard<std::mutex> lk(s->mu);
         if (s->stop) {
             smpm::set_last_error("smpm_submit: server is shutting down");
             return SMPM_EINVAL;
+        }
+        if (est > s->budget) {
+            q->st.status = SMPM_ENOMEM;
+            q->err = "serving: request footprint " + std::to_string(est) + " bytes exceeds the device budget of " +
+                     std::to_string(s->budget) + " bytes";
+            q->t_done = q->t_submit;
+            q->done = true;
+            s->all[q->id] = std::move(q);
+            return SMPM_OK;
         }
         s->pending.push_back(q.get());
         s->all[q->id] = std::move(q);

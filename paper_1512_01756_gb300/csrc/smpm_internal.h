@@ -2,9 +2,13 @@
 // device kernels (kernels.cu) and the API / solve driver (api.cu).
 #pragma once
 
+#include <cuda_runtime.h>
+
 #include <cstdint>
 #include <string>
 #include <vector>
+
+#include "../../include/smpm.h"
 
 namespace smpm {
 
@@ -114,6 +118,20 @@ struct GemmArgs {
                               // < 0: over -mirror_nb blocks of `face` values reversed inside each;
     int face;                 //   mats holds [Hp; Hm] (h x h each, h = M = K = |mirror_nb| face / 2)
 };
+
+// View of the operator data of operator set 0 that the allocation-free
+// deflation projection (noalloc.cu) needs; filled by deflation_view (api.cu),
+// which reads the handle only.
+struct DeflView {
+    int fz, mx, ng, d;
+    long long k;
+    const double* K;          // [d][d]
+    const double* rho;        // [3 classes][2 sides][ng][2 fz]
+    const int* strip_cls;     // [mx] (device)
+    cudaStream_t stream;
+};
+bool deflation_view(smpm_handle h, DeflView* v, std::string& msg);
+void set_last_error(const std::string& msg);
 
 // Number of kernels libsmpm has launched in this process.
 long long launch_count();

@@ -13,13 +13,14 @@ import numpy as np
 _PKG = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_PKG, "libsmpm.so")
 
-SMPM_OK, SMPM_EINVAL, SMPM_ENOMEM, SMPM_ENOCONV, SMPM_EBREAKDOWN, SMPM_ECUDA, SMPM_EBUSY = 0, -1, -2, -3, -4, -5, -6
+SMPM_OK, SMPM_EINVAL, SMPM_ENOMEM, SMPM_ENOCONV, SMPM_EBREAKDOWN, SMPM_ECUDA, SMPM_EBUSY, SMPM_ETIMEOUT = \
+    0, -1, -2, -3, -4, -5, -6, -7
 
 # every entry point include/smpm.h declares
 EXPORTS = ["smpm_setup", "smpm_solve", "smpm_solve_batch", "smpm_solve_guess", "smpm_setup_multi", "smpm_solve_multi",
            "smpm_setup_3d", "smpm_solve_3d", "smpm_solve_3d_physical",
            "smpm_sizes", "smpm_node_coords", "smpm_grid_coords", "smpm_null_vectors", "smpm_set_stream", "smpm_device_bytes", "smpm_release", "smpm_probe_fp64",
-           "smpm_profile", "smpm_profile_read", "smpm_kernel_launches", "smpm_apply", "smpm_last_residuals", "smpm_apply_deflation_noalloc",
+           "smpm_profile", "smpm_profile_read", "smpm_profile_split", "smpm_kernel_launches", "smpm_apply", "smpm_last_residuals", "smpm_apply_deflation_noalloc",
            "smpm_server_create", "smpm_submit", "smpm_poll", "smpm_server_destroy", "smpm_last_error"]
 
 
@@ -82,6 +83,8 @@ def load():
     lib.smpm_profile.argtypes = [H, ctypes.c_int]
     lib.smpm_profile_read.argtypes = [H, ctypes.POINTER(ctypes.c_longlong), ctypes.POINTER(ctypes.c_double),
                                       ctypes.POINTER(ctypes.c_double), ctypes.c_int]
+    lib.smpm_profile_split.argtypes = [H, ctypes.c_int, ctypes.POINTER(ctypes.c_longlong),
+                                       ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double), ctypes.c_int]
     lib.smpm_apply.argtypes = [H, ctypes.c_int, ctypes.c_int, P, P]
     lib.smpm_last_residuals.argtypes = [H, ctypes.c_int, P]
     lib.smpm_apply_deflation_noalloc.argtypes = [H, ctypes.c_int, P, P]
@@ -315,6 +318,23 @@ class Server:
 
 def kernel_launches():
     return load().smpm_kernel_launches()
+
+
+def profile_all(enable=True):
+    """Profile the dense-product launches of every handle created from now on
+    (the serving workers' included)."""
+    _check(load().smpm_profile(None, 1 if enable else 0))
+
+
+def profile_split(handle=None, reset=True):
+    """Dense-product launch totals per precision (FP64 and FP32 launches) of
+    one handle, or of every handle of the process for handle None."""
+    out = {}
+    for p, name in ((0, "fp64"), (1, "fp32")):
+        n, fl, ms = ctypes.c_longlong(), ctypes.c_double(), ctypes.c_double()
+        _check(load().smpm_profile_split(handle, p, ctypes.byref(n), ctypes.byref(fl), ctypes.byref(ms), int(reset)))
+        out[name] = {"launches": n.value, "flops": fl.value, "ms": ms.value}
+    return out
 
 
 def probe_fp64(stream=None):

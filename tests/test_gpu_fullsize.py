@@ -23,6 +23,13 @@ SHAPE = (256, 4, 12, 64.0, 1.0)
 R = 128
 
 
+def _rel(a, b):
+    """Relative error in the 2-norm and in the max-norm, the larger of the two
+    (a local error on one face of a long vector shows in the second)."""
+    a, b = np.asarray(a), np.asarray(b)
+    return max(np.linalg.norm(a - b) / np.linalg.norm(b), np.abs(a - b).max() / np.abs(b).max())
+
+
 @pytest.fixture(scope="module")
 def smpm():
     if not torch.cuda.is_available():
@@ -57,13 +64,12 @@ def test_bench_workload_sampled_vs_oracle(smpm):
         _, ue = inputs.cos_modes(X, Z, 64.0, 1.0, sp)
         ue = ue - np.dot(w, ue) / w.sum()
         assert abs(np.dot(w, U[i])) < 1e-10 * np.abs(U[i]).max()     # zero-mean gauge
-        assert np.linalg.norm(U[i] - ue) < 1e-9 * np.linalg.norm(ue), i
+        assert _rel(U[i], ue) < 1e-9, (i, _rel(U[i], ue))
     sch = StripSchur(g)
     for i in (0, 11):
         u_ref, _ = dbj.solve(g, F[i], method="dbj", tol=1e-13, schur=sch)
-        nrm = np.linalg.norm(u_ref)
-        rel10 = np.linalg.norm(out[1e-10][i] - u_ref) / nrm
-        rel11 = np.linalg.norm(out[1e-11][i] - u_ref) / nrm
+        rel10 = _rel(out[1e-10][i], u_ref)
+        rel11 = _rel(out[1e-11][i], u_ref)
         print(f"rhs {i}: rel error at tol 1e-10 {rel10:.2e}, at 1e-11 {rel11:.2e}")
         assert rel10 < 1e-9, (i, rel10)
         assert rel11 < 1e-9, (i, rel11)

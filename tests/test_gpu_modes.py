@@ -32,6 +32,13 @@ from oracle.smpm import Grid, assemble_L  # noqa: E402
 from oracle import fourier  # noqa: E402
 
 
+def _rel(a, b):
+    """Relative error in the 2-norm and in the max-norm, the larger of the two
+    (a local error on one face of a long vector shows in the second)."""
+    a, b = np.asarray(a), np.asarray(b)
+    return max(np.linalg.norm(a - b) / np.linalg.norm(b), np.abs(a - b).max() / np.abs(b).max())
+
+
 @pytest.fixture(scope="module")
 def smpm():
     if not torch.cuda.is_available():
@@ -66,7 +73,7 @@ def test_small_3d_matches_oracle(smpm):
     s.close()
     u = fourier.inverse(_unstack(Uh.cpu().numpy()), my)
     assert st.rel_resid_true <= 1e-10
-    assert np.linalg.norm(u - u_ref) / np.linalg.norm(u_ref) < 1e-9
+    assert _rel(u, u_ref) < 1e-9
 
 
 @pytest.fixture(scope="module")
@@ -147,9 +154,21 @@ def test_full_size_sampled_modes_match_oracle(smpm, full3d):
                 continue
             u_ref, _ = dbj.solve(g, b, k2=ks[j] ** 2, method="dbj", tol=1e-13, schur=sch, coarse="rank1")
             u = part(uh[:, j])
-            rel = np.linalg.norm(u - u_ref) / np.linalg.norm(u_ref)
+            rel = _rel(u, u_ref)
             print(f"mode {j} {part.__name__}: rel {rel:.2e}")
             assert rel < 1e-9, (j, part.__name__, rel)
+    # mode 0 as given (the paper's U[0,1] data, mostly incompatible: each side
+    # projects it with its own left null vector, Eq. regularize_poisson)
+    b0_raw = fh[:, 0].real.copy()
+    u_ref0, _ = dbj.solve(g, b0_raw, method="dbj", tol=1e-13, coarse="rank1")
+    rel0 = _rel(uh[:, 0].real, u_ref0)
+    print(f"mode 0 (as given): rel {rel0:.2e}")
+    # the data is far from compatible (mean ~0.5), so the projection removes
+    # most of it and the result moves with the left null vector: in the oracle
+    # alone, perturbing the entries of L by one rounding unit moves this
+    # solution by 0.8e-9 to 3.9e-9; the two independently computed null
+    # vectors are held to 1e-8
+    assert rel0 < 1e-8, rel0
     # mode 0 made consistent first (its component along the oracle's u_L
     # removed, Eq. regularize_poisson), through a 2-D handle of the grid
     from oracle.schur import left_null_sparse
@@ -162,7 +181,7 @@ def test_full_size_sampled_modes_match_oracle(smpm, full3d):
     s2.close()
     assert st0.rel_resid_true <= 1e-11
     u_ref, _ = dbj.solve(g, b0, method="dbj", tol=1e-13, coarse="rank1")
-    rel = np.linalg.norm(u0 - u_ref) / np.linalg.norm(u_ref)
+    rel = _rel(u0, u_ref)
     print(f"mode 0 (consistent): rel {rel:.2e}")
     assert rel < 1e-9, rel
 
@@ -182,7 +201,7 @@ def test_small_3d_physical_matches_oracle(smpm):
     st = s.solve_3d_physical(np.ascontiguousarray(f3.T), u3, tol=1e-10)
     s.close()
     assert st.rel_resid_true <= 1e-10
-    assert np.linalg.norm(u3.T - u_ref) / np.linalg.norm(u_ref) < 1e-9
+    assert _rel(u3.T, u_ref) < 1e-9
 
 
 def test_full_size_physical_separable_manufactured(smpm, full3d):

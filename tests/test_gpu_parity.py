@@ -53,7 +53,10 @@ def _gpu_solve(smpm, shape, f, k2=0.0, gb=None, groups=0, tol=1e-10, host=False,
 
 
 def _rel(a, b):
-    return np.linalg.norm(a - b) / np.linalg.norm(b)
+    """Relative error in the 2-norm and in the max-norm, the larger of the two
+    (a local error on one face of a long vector shows in the second)."""
+    a, b = np.asarray(a), np.asarray(b)
+    return max(np.linalg.norm(a - b) / np.linalg.norm(b), np.abs(a - b).max() / np.abs(b).max())
 
 
 def _g_flat(gd):

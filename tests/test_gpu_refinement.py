@@ -19,6 +19,13 @@ torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
 
 
+def _rel(a, b):
+    """Relative error in the 2-norm and in the max-norm, the larger of the two
+    (a local error on one face of a long vector shows in the second)."""
+    a, b = np.asarray(a), np.asarray(b)
+    return max(np.linalg.norm(a - b) / np.linalg.norm(b), np.abs(a - b).max() / np.abs(b).max())
+
+
 @pytest.fixture(scope="module")
 def smpm():
     if not torch.cuda.is_available():
@@ -70,9 +77,9 @@ def test_forced_extended_refinement_matches_plain(smpm, monkeypatch):
         assert st.status == 0 and st.rel_resid_true <= 1e-11 and st.restarts >= 2, st.as_dict()
         out.append(u)
     monkeypatch.delenv("SMPM_REFINE_EXTENDED")
-    assert np.linalg.norm(out[1] - out[0]) / np.linalg.norm(out[0]) < 1e-10
+    assert _rel(out[1], out[0]) < 1e-10
     u_ref, _ = direct_solve(Grid(*shape), f)
-    assert np.linalg.norm(out[1] - u_ref) / np.linalg.norm(u_ref) < 1e-9
+    assert _rel(out[1], u_ref) < 1e-9
 
 
 def test_graph_replay_matches_direct_launches(smpm, monkeypatch):
@@ -151,8 +158,8 @@ def test_warm_start_from_a_guess(smpm, k2):
     s.close()
     u_ref, _ = direct_solve(g, f, None, k2)
     assert st_cold.status == 0 and st_same.status == 0 and st_warm.status == 0
-    assert st_same.iters <= 1 and np.linalg.norm(u_same - u_cold) < 1e-9 * np.linalg.norm(u_cold)
+    assert st_same.iters <= 1 and _rel(u_same, u_cold) < 1e-9
     assert st_warm.iters < st_cold.iters, (st_warm.iters, st_cold.iters)
     assert st_warm.rel_resid_true <= 1e-10
-    assert np.linalg.norm(u_warm - u_ref) < 1e-9 * np.linalg.norm(u_ref)
+    assert _rel(u_warm, u_ref) < 1e-9
     assert st_zero.iters == st_cold.iters and np.array_equal(u_zero, u_cold)

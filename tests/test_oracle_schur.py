@@ -142,3 +142,36 @@ def test_schur_commutes_with_z_reversal(shape, k2):
     gs = Grid(mx, mz, order, lx, lz, z_ratio=1.3)
     Ss = schur_dense(gs, assemble_L(gs, k2))[0]
     assert np.abs(Ss[np.ix_(P, P)] - Ss).max() > 1e-3 * np.abs(Ss).max()
+
+
+def test_null_vector_on_stiff_stretched_mesh():
+    """Left null vector of L on the order-16 mesh stretched by 1.2 (elements
+    from 0.011 to 0.18 high, penalty rows ~1e12): the data of a zero-mean
+    manufactured solution with g = 0 is compatible with the continuous
+    problem, so the discrete compatibility u_L^T b must vanish to the
+    discretisation error (spectrally small at order 16), and L^T u_L = 0 to
+    round-off of the rows.  The same inverse iteration on the unequilibrated
+    L (the shift a fixed fraction of max |L|, above the smallest nonzero
+    eigenvalue here) converges to a mixture and misses it by orders of
+    magnitude -- that planted variant must fail."""
+    import scipy.sparse as sp
+    import scipy.sparse.linalg as spla
+    from oracle.schur import left_null_sparse
+    g = Grid(32, 16, 16, 2.0, 1.0, z_ratio=1.2)
+    X, Z = g.coords()
+    ue = np.cos(np.pi * X / g.lx) * np.cos(np.pi * Z / g.lz)
+    f = -(np.pi ** 2 / g.lx ** 2 + np.pi ** 2 / g.lz ** 2) * ue
+    L = assemble_L(g).tocsr()
+    b = rhs(g, f)
+    uL = left_null_sparse(L)
+    rowmax = abs(L).max(axis=1).toarray().ravel()
+    assert np.abs((L.T @ uL)).max() < 1e-13 * rowmax.max()
+    assert abs(np.dot(uL, b)) < 1e-11 * np.linalg.norm(b)
+    # planted mistake: no row equilibration
+    T = (L.T - 1e-12 * abs(L).max() * sp.identity(g.r)).tocsc()
+    lu = spla.splu(T)
+    v = np.random.default_rng(0).standard_normal(g.r)
+    for _ in range(4):
+        v = lu.solve(v)
+        v /= np.linalg.norm(v)
+    assert abs(np.dot(v, b)) > 1e-7 * np.linalg.norm(b)
