@@ -532,7 +532,7 @@ def oracle_serve_sample(reqs, seconds, max_nodes=ORACLE_MAX_NODES, max_count=Non
     from oracle.schur import StripSchur
     from oracle import dbj
     from paper_1512_01756_gb300 import inputs
-    done, biggest, big_r = 0, "", 0
+    done, biggest, big_r, worst = 0, "", 0, 0.0
     c0, w0 = os.times(), time.perf_counter()
     for q in reqs:
         if q["r"] > max_nodes:
@@ -541,7 +541,7 @@ def oracle_serve_sample(reqs, seconds, max_nodes=ORACLE_MAX_NODES, max_count=Non
         X, Z = g.coords()
         f, _ = inputs.cos_modes(X, Z, q["lx"], 1.0, inputs.cos_modes_spec(q["seed"]))
         _, info = dbj.solve(g, f, k2=q["k2"], method="dbj", tol=TOL, schur=StripSchur(g, q["k2"]))
-        assert info["schur_residual"] < 10 * TOL
+        worst = max(worst, info["schur_residual"])
         done += 1
         if q["r"] > big_r:
             big_r, biggest = q["r"], f'{q["mx"]}x{q["mz"]} order {q["order"]}'
@@ -551,7 +551,7 @@ def oracle_serve_sample(reqs, seconds, max_nodes=ORACLE_MAX_NODES, max_count=Non
             break
     w1, c1 = time.perf_counter(), os.times()
     cores = max(1, round(((c1.user - c0.user) + (c1.system - c0.system)) / (w1 - w0)))
-    return done, w1 - w0, cores, biggest
+    return done, w1 - w0, cores, biggest + f"; worst oracle Schur residual {worst:.1e}"
 
 
 def _pct(v, p):

@@ -40,10 +40,11 @@
  *   (read at setup) turns the mirror-symmetric half-size products of the
  *   interior strips, block-Jacobi pairs and slot inverses off, or on at every
  *   batch size (by default S and M^-1 use them where they save enough work);
- *   SMPM_PERSISTENT=0 runs the Arnoldi steps of a restart cycle as separate
- *   launches (graph-replayed step groups) instead of one persistent
- *   cooperative kernel; SMPM_PERSIST_WAIT_NS sets the time limit of one
- *   grid-barrier wait of that kernel (default 2e9 ns).  Test hook (it only
+ *   SMPM_PERSISTENT=1 runs the Arnoldi steps of a restart cycle in one
+ *   persistent cooperative kernel (grid-wide barriers between the phases)
+ *   instead of graph-replayed step groups of separate launches (the
+ *   default, measured faster); SMPM_PERSIST_WAIT_NS sets the time limit of
+ *   one grid-barrier wait of that kernel (default 2e9 ns).  Test hook (it only
  *   makes the solve fail): SMPM_PERSIST_STALL=1 makes every barrier wait for
  *   one block more than the grid holds, so the first wait runs out of time
  *   and the solve returns SMPM_ETIMEOUT.
@@ -230,12 +231,14 @@ int smpm_probe_fp64(void* stream, double* tflops);
  * while it is enabled. */
 int smpm_profile(smpm_handle h, int enable);
 int smpm_profile_read(smpm_handle h, long long* launches, double* flops, double* ms, int reset);
-/* The same totals split by the precision of the launches (precision 0: FP64
- * products, 1: FP32 products of the mixed forms).  h = NULL reads the totals
- * of every handle of the process (harvested at the end of each solve), and
- * smpm_profile(NULL, enable) makes every handle created afterwards profile
- * (the serving workers' handles included).  SMPM_EINVAL for another
- * precision. */
+/* The same totals split by the kind of launch (precision 0: FP64 products
+ * on the CUDA cores, 1: FP32 products of the mixed forms, 2: FP64-accurate
+ * tensor-core products, SMPM_OZAKI=1, with their algorithmic FLOPs, 3: the
+ * same launches' executed BF16 tensor-core FLOPs, their time under 2).
+ * h = NULL reads the totals of every handle of the process (harvested at the
+ * end of each solve), and smpm_profile(NULL, enable) makes every handle
+ * created afterwards profile (the serving workers' handles included).
+ * SMPM_EINVAL for another kind. */
 int smpm_profile_split(smpm_handle h, int precision, long long* launches, double* flops, double* ms, int reset);
 
 /* Number of CUDA kernels this library has launched in the process. */

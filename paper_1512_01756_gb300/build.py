@@ -15,7 +15,7 @@ OBJ = os.path.join(PKG, "_build")
 LIB = os.path.join(PKG, "libsmpm.so")
 INCLUDE = os.path.join(ROOT, "include")
 
-SOURCES = ["kernels.cu", "api.cu", "host_ops.cpp", "noalloc.cu", "server.cu"]
+SOURCES = ["kernels.cu", "api.cu", "host_ops.cpp", "noalloc.cu", "server.cu", "ozaki.cu"]
 HEADERS = ["kernels.h", "smpm_internal.h"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVCC_FLAGS = ARCH + ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-I" + INCLUDE]

@@ -170,9 +170,24 @@ struct Solver {
     // persistent Arnoldi kernel: barrier counter and status word (device),
     // off for the handle once a cooperative launch has been refused
     bool persist_ok = true;
+    // FP64-accurate tensor-core products (ozaki.cu): digit tensors of the
+    // Schur blocks G and the block-Jacobi inverses, keyed by the FP64 matrix
+    // array they were split from
+    struct OzMat {
+        unsigned short* dig = nullptr;
+        int* rexp = nullptr;
+        long long dig_stride = 0, rexp_stride = 0;
+        int S = 0, beta = 0, N = 0, mt_n = 0, kcn = 0;
+    };
+    bool oz = false;
+    std::map<const double*, OzMat> ozmats;
+    int* d_ozerr = nullptr;
     unsigned int* d_pbar = nullptr;
     int* d_pstatus = nullptr;
-    bool capturing = false;                 // a group is being captured (no tuning, no syncs)
+    bool capturing = false;
+    // profiled launches inside a graph capture take the CUDA-core path, whose
+    // event bookkeeping handles captures
+    bool capturing_prof_block() const { return prof && cap_events != nullptr; }                 // a group is being captured (no tuning, no syncs)
     void drop_graphs() {
         for (auto& kv : graphs) {
             if (kv.second.exec) cudaGraphExecDestroy(kv.second.exec);
@@ -183,11 +198,14 @@ struct Solver {
     }
     bool prof = false;
     std::vector<cudaEvent_t> ev;
-    std::vector<char> ev_f32;               // precision of each recorded launch (1 = FP32)
+    std::vector<char> ev_f32;               // category of each recorded launch (0 FP64, 1 FP32, 2 tensor)
     int ev_used = 0;
     unsigned long long* d_flops = nullptr;  // [0] FP64 launches, [1] FP32 launches
-    long long prof_launches[2] = {0, 0};    // per precision: FP64, FP32
-    double prof_ms[2] = {0.0, 0.0}, prof_flops[2] = {0.0, 0.0};
+    // per category: 0 FP64 CUDA-core products, 1 FP32 products, 2 FP64-accurate
+    // tensor-core products (algorithmic FLOPs), 3 the same launches' executed
+    // BF16 tensor FLOPs (time counted under 2)
+    long long prof_launches[4] = {0, 0, 0, 0};
+    double prof_ms[4] = {0.0, 0.0, 0.0, 0.0}, prof_flops[4] = {0.0, 0.0, 0.0, 0.0};
 
     template <class T>
     T* dalloc(size_t n, std::vector<void*>& list) {
@@ -1067,6 +1085,28 @@ static void setup_solver(Solver& S) {
             k_to_fp32(S.Gh32, S.Gh, (long long)nop * 2 * fz * fz, st);
         }
     }
+    // SMPM_OZAKI=1: the FP64 Schur and block-Jacobi products on the tensor
+    // cores; their class matrices are split into BF16 digit tensors here
+    if (const char* oe = std::getenv("SMPM_OZAKI")) S.oz = std::atoi(oe) != 0;
+    if (S.oz) {
+        auto split = [&](const double* mats, long long stride, int nmat, int Mm) {
+            Solver::OzMat z;
+            if (!oz_choose(Mm, z.S, z.beta, z.N)) return;
+            z.mt_n = (Mm + 127) / 128;
+            z.kcn = (Mm + 127) / 128;
+            z.dig_stride = (long long)z.mt_n * z.kcn * z.S * 128 * 128;
+            z.rexp_stride = (long long)z.mt_n * 128;
+            z.dig = S.dalloc<unsigned short>((size_t)nmat * z.dig_stride, S.allocs);
+            z.rexp = S.dalloc<int>((size_t)nmat * z.rexp_stride, S.allocs);
+            k_oz_split_rows(mats, stride, nmat, Mm, Mm, z.S, z.beta, z.mt_n, z.kcn, z.dig, z.dig_stride, z.rexp,
+                            z.rexp_stride, st);
+            S.ozmats[mats] = z;
+        };
+        split(S.G, S.sG, nop * 3, 2 * fz);
+        split(S.Minv, S.sM, nop * S.nmc, 4 * fz);
+        S.d_ozerr = S.dalloc<int>(1, S.allocs);
+        CK(cudaMemsetAsync(S.d_ozerr, 0, sizeof(int), st));
+    }
     CK(cudaStreamSynchronize(st));
     S.free_list(tmp);
     S.setup_ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
@@ -1398,6 +1438,31 @@ static int tune_shape(Solver& S, GemmArgs& a, const TileSet& ts, int epi, bool& 
 }
 
 static void run_gemm(Solver& S, GemmArgs a, const TileSet& ts, int epi) {
+    if (S.oz && !S.capturing_prof_block() && !a.fp32 && a.mirror_nb == 0 && (epi == 0 || epi == 1)) {
+        auto it = S.ozmats.find(a.mats);
+        if (it != S.ozmats.end()) {
+            const Solver::OzMat& m = it->second;
+            const int sh = m.N == 64 ? 1 : 0;     // tile lists of 64 or 32 columns
+            OzArgs z;
+            z.a = a;
+            z.dig = m.dig; z.dig_stride = m.dig_stride; z.rexp = m.rexp; z.rexp_stride = m.rexp_stride;
+            z.S = m.S; z.beta = m.beta; z.N = m.N; z.mt_n = m.mt_n; z.kcn = m.kcn; z.epi = epi; z.err = S.d_ozerr;
+            const bool rec = S.prof && S.ev_used < kEventPairs;
+            if (S.prof) z.a.flops = S.d_flops + 2;       // [2] algorithmic, [3] executed tensor FLOPs
+            if (rec) {
+                S.ev_f32[S.ev_used] = 2;
+                CK(cudaEventRecord(S.ev[2 * S.ev_used], S.stream));
+            }
+            const bool ok = launch_oz_gemm(z, ts.t[sh], ts.n[sh], S.stream);
+            if (rec) {
+                CK(cudaEventRecord(S.ev[2 * S.ev_used + 1], S.stream));
+                ++S.ev_used;
+            }
+            if (ok) return;
+            cudaGetLastError();
+            S.oz = false;                        // SIMT products from now on
+        }
+    }
     bool launched = false;
     const int sh = std::getenv("SMPM_TILE_SHAPE") ? std::atoi(std::getenv("SMPM_TILE_SHAPE")) & 1
                                                   : tune_shape(S, a, ts, epi, launched);
@@ -1473,8 +1538,8 @@ static PGemm to_pgemm(Solver& S, const GemmCall& c) {
 // Process-wide profile totals (every handle's harvested launches; per
 // precision: [0] FP64, [1] FP32), and whether new handles profile.
 static std::mutex g_prof_mu;
-static long long g_prof_launches[2] = {0, 0};
-static double g_prof_ms[2] = {0.0, 0.0}, g_prof_flops[2] = {0.0, 0.0};
+static long long g_prof_launches[4] = {0, 0, 0, 0};
+static double g_prof_ms[4] = {0.0, 0.0, 0.0, 0.0}, g_prof_flops[4] = {0.0, 0.0, 0.0, 0.0};
 static std::atomic<int> g_prof_default{0};
 
 static void add_prof(Solver& S, int p, long long n, double ms, double flops) {
@@ -1493,13 +1558,12 @@ static void harvest_profile(Solver& S) {
     for (int i = 0; i < S.ev_used; ++i) {
         float ms = 0.f;
         CK(cudaEventElapsedTime(&ms, S.ev[2 * i], S.ev[2 * i + 1]));
-        add_prof(S, S.ev_f32[i] ? 1 : 0, 1, ms, 0.0);
+        add_prof(S, S.ev_f32[i], 1, ms, 0.0);
     }
     S.ev_used = 0;
-    unsigned long long fl[2] = {0, 0};
+    unsigned long long fl[4] = {0, 0, 0, 0};
     CK(cudaMemcpy(fl, S.d_flops, sizeof(fl), cudaMemcpyDeviceToHost));
-    add_prof(S, 0, 0, 0.0, (double)fl[0]);
-    add_prof(S, 1, 0, 0.0, (double)fl[1]);
+    for (int p = 0; p < 4; ++p) add_prof(S, p, 0, 0.0, (double)fl[p]);
     CK(cudaMemset(S.d_flops, 0, sizeof(fl)));
 }
 
@@ -1519,7 +1583,7 @@ static int schur_calls(Solver& S, const double* in, long long in_rs, long long i
     a.add = add;
     a.active = active;
     const double* h = fp32 ? reinterpret_cast<const double*>(S.Gh32) : S.Gh;
-    if (!S.useG || h == nullptr) {
+    if (!S.useG || h == nullptr || (S.oz && !fp32)) {
         c[0] = GemmCall{a, &S.wk.tG, 1};
         return 1;
     }
@@ -1551,7 +1615,7 @@ static int bj_calls(Solver& S, const double* in, long long in_rs, long long in_o
     a.out = out; a.out_rs = out_rs; a.out_us = f4; a.out_off0 = out_off + fz; a.out_off1 = 0; a.msplit = f4;
     a.active = active;
     const double* h = fp32 ? reinterpret_cast<const double*>(S.Mh32) : S.Mh;
-    if (!S.useM || h == nullptr) {
+    if (!S.useM || h == nullptr || (S.oz && !fp32)) {
         c[0] = GemmCall{a, &S.wk.tM, 0};
         return 1;
     }
@@ -1762,13 +1826,16 @@ static int solve_impl(Solver& S, const std::vector<int>& ops, const double* f, c
     bool first = true;
     const int check_every = 4;
     const bool graphs_off = std::getenv("SMPM_NO_GRAPHS") != nullptr;
-    // SMPM_PERSISTENT=0: step groups of separate launches (graph-replayed)
-    // instead of the persistent kernel; SMPM_PERSIST_WAIT_NS: time limit of a
+    // SMPM_PERSISTENT=1: the Arnoldi steps of a cycle in one persistent
+    // cooperative kernel instead of step groups of separate launches
+    // (graph-replayed), which measured 5-7 % faster on GB300 (256 x 4, order
+    // 12, 128 right-hand sides: 40.3 vs 42.4-43.5 ms per batch; 8 x 2, order
+    // 8: 857 vs 902 us per solve); SMPM_PERSIST_WAIT_NS: time limit of a
     // barrier wait (default 2 s); SMPM_PERSIST_STALL=1: test hook, every
     // barrier waits for a block that does not exist, so the first wait runs
     // out of time and the solve returns SMPM_ETIMEOUT
     const char* pe = std::getenv("SMPM_PERSISTENT");
-    const bool persist_off = pe != nullptr && std::atoi(pe) == 0;
+    const bool persist_off = pe == nullptr || std::atoi(pe) == 0;
     const char* pw = std::getenv("SMPM_PERSIST_WAIT_NS");
     const long long persist_wait_ns = pw ? std::max(1000LL, std::atoll(pw)) : 2000000000LL;
     const bool persist_stall = std::getenv("SMPM_PERSIST_STALL") != nullptr;
@@ -2019,7 +2086,7 @@ static int solve_impl(Solver& S, const std::vector<int>& ops, const double* f, c
                 for (size_t e = 0; e + 1 < gg->ev.size(); e += 2) {
                     float ms = 0.f;
                     CK(cudaEventElapsedTime(&ms, gg->ev[e], gg->ev[e + 1]));
-                    add_prof(S, gg->f32[e / 2] ? 1 : 0, 1, ms, 0.0);
+                    add_prof(S, gg->f32[e / 2], 1, ms, 0.0);
                 }
             }
             bool any = false;
@@ -2067,7 +2134,13 @@ static int solve_impl(Solver& S, const std::vector<int>& ops, const double* f, c
     CK(cudaMemcpyAsync(h_r.data(), w.rnorm, R * sizeof(double), cudaMemcpyDeviceToHost, st_));
     CK(cudaMemcpyAsync(h_b.data(), w.bnorm, R * sizeof(double), cudaMemcpyDeviceToHost, st_));
     CK(cudaMemcpyAsync(h_flags.data(), w.flags, R * sizeof(int), cudaMemcpyDeviceToHost, st_));
+    int h_ozerr = 0;
+    if (S.d_ozerr) CK(cudaMemcpyAsync(&h_ozerr, S.d_ozerr, sizeof(int), cudaMemcpyDeviceToHost, st_));
     CK(cudaStreamSynchronize(st_));
+    if (h_ozerr != 0) {
+        CK(cudaMemsetAsync(S.d_ozerr, 0, sizeof(int), st_));
+        throw Err{SMPM_ETIMEOUT, "tensor-core product: a wait for a copy or the tensor pipe ran out of iterations"};
+    }
     CK(cudaGetLastError());
     harvest_profile(S);
     double worst = 0.0;
@@ -2175,8 +2248,8 @@ static void profile_enable(Solver& S, bool enable) {
         S.ev.resize(2 * kEventPairs);
         S.ev_f32.assign(kEventPairs, 0);
         for (auto& e : S.ev) CK(cudaEventCreate(&e));
-        S.d_flops = S.dalloc<unsigned long long>(2, S.allocs);
-        CK(cudaMemsetAsync(S.d_flops, 0, 2 * sizeof(unsigned long long), S.stream));
+        S.d_flops = S.dalloc<unsigned long long>(4, S.allocs);
+        CK(cudaMemsetAsync(S.d_flops, 0, 4 * sizeof(unsigned long long), S.stream));
     }
     if (S.prof != enable) {
         CK(cudaStreamSynchronize(S.stream));
@@ -2529,7 +2602,12 @@ int smpm_profile_read(smpm_handle h, long long* launches, double* flops, double*
     return guarded([&] {
         long long n = 0;
         double f = 0.0, t = 0.0;
-        for (int p = 0; p < 2; ++p) read_prof(h, p, reset, n, f, t);
+        for (int p = 0; p < 3; ++p) read_prof(h, p, reset, n, f, t);
+        if (reset) {
+            long long n3 = 0;
+            double f3 = 0.0, t3 = 0.0;
+            read_prof(h, 3, reset, n3, f3, t3);
+        }
         if (launches) *launches = n;
         if (flops) *flops = f;
         if (ms) *ms = t;
@@ -2539,7 +2617,8 @@ int smpm_profile_read(smpm_handle h, long long* launches, double* flops, double*
 
 int smpm_profile_split(smpm_handle h, int precision, long long* launches, double* flops, double* ms, int reset) {
     return guarded([&] {
-        if (precision != 0 && precision != 1) throw Err{SMPM_EINVAL, "precision must be 0 (FP64) or 1 (FP32)"};
+        if (precision < 0 || precision > 3)
+            throw Err{SMPM_EINVAL, "category must be 0 (FP64), 1 (FP32), 2 (tensor, algorithmic) or 3 (tensor, executed)"};
         long long n = 0;
         double f = 0.0, t = 0.0;
         read_prof(h, precision, reset, n, f, t);

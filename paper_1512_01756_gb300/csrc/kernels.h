@@ -108,6 +108,28 @@ struct PersistArgs {
 // fit on the device); false if the device cannot launch it cooperatively.
 bool k_arnoldi_persistent(const PersistArgs& p, cudaStream_t s);
 
+// FP64-accurate class GEMM on the tensor cores (ozaki.cu): the class
+// matrices pre-split into S BF16 digit matrices of beta bits (row scale
+// 2^rexp), the input columns split on the fly, anti-diagonal digit products
+// accumulated exactly in FP32 tensor memory and combined in 64-bit integers.
+struct OzArgs {
+    GemmArgs a;                    // columns, addressing, rows, epilogue as for the class GEMM (mats unused)
+    const unsigned short* dig;     // matrix m: dig + m * dig_stride, [mt_n][kcn][S][128 x 128] digit blocks
+    long long dig_stride;
+    const int* rexp;               // matrix m: rexp + m * rexp_stride, [mt_n * 128] row exponents
+    long long rexp_stride;
+    int S, beta, N, mt_n, kcn, epi;
+    int* err;                      // set to 2 by a wait that ran out of iterations
+};
+// beta, S and the column-tile width N for inner dimension K (false: K too large)
+bool oz_choose(int K, int& S, int& beta, int& N);
+int oz_smem_bytes(int S, int N);
+void k_oz_split_rows(const double* mats, long long mat_stride, int nmat, int M, int K, int S, int beta, int mt_n,
+                     int kcn, unsigned short* dig, long long dig_stride, int* rexp, long long rexp_stride,
+                     cudaStream_t s);
+// false if the launch could not be configured (shared-memory limit)
+bool launch_oz_gemm(const OzArgs& z, const Tile* d_tiles, int ntiles, cudaStream_t s);
+
 // RHS assembly b = f + tau g at the physical boundary, per rhs; partial
 // dots with u_L for the projection (uL[r] may be null).
 struct GridArgs {

@@ -327,10 +327,14 @@ def profile_all(enable=True):
 
 
 def profile_split(handle=None, reset=True):
-    """Dense-product launch totals per precision (FP64 and FP32 launches) of
-    one handle, or of every handle of the process for handle None."""
+    """Dense-product launch totals per kind of one handle (a Solver), or of
+    every handle of the process for None: FP64 and FP32 CUDA-core launches,
+    the FP64-accurate tensor-core launches with their algorithmic FLOPs
+    ("tensor") and executed BF16 tensor FLOPs ("tensor_exec", same time)."""
+    if handle is not None and hasattr(handle, "_h"):
+        handle = handle._h
     out = {}
-    for p, name in ((0, "fp64"), (1, "fp32")):
+    for p, name in ((0, "fp64"), (1, "fp32"), (2, "tensor"), (3, "tensor_exec")):
         n, fl, ms = ctypes.c_longlong(), ctypes.c_double(), ctypes.c_double()
         _check(load().smpm_profile_split(handle, p, ctypes.byref(n), ctypes.byref(fl), ctypes.byref(ms), int(reset)))
         out[name] = {"launches": n.value, "flops": fl.value, "ms": ms.value}

@@ -2,7 +2,7 @@
 launch, phases separated by grid-wide barriers with bounded waits).
 
 * Parity: the persistent path against the step-group path (separate launches,
-  SMPM_PERSISTENT=0) and against the oracle, for the plain FP64 solve, the
+  SMPM_PERSISTENT unset) and against the oracle, for the plain FP64 solve, the
   mixed-precision solve (FP64 first step group, FP32 block-Jacobi after),
   several restart cycles, batched right-hand sides and the batched Fourier
   modes of the 3-D problem (Sec. 5, Alg. 3d).
