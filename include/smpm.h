@@ -93,6 +93,17 @@ typedef struct {
                                accumulation (its block-Jacobi inverses are
                                factorised in FP32 too; 10 inner steps or 1e-4 relative;
                                SMPM_INNER_STEPS overrides the step count)      */
+    int krylov;             /* 0: every right-hand side (every Fourier mode's real
+                               and imaginary part) keeps its own Krylov space and
+                               meets tol itself; 1: the right-hand sides of one
+                               solve call form one concatenated vector and one
+                               GMRES runs on the block-diagonal operator (Sec. 5,
+                               Implementation; Alg. 3d line 7: all wavenumbers
+                               in one GMRES): every dot product and norm is summed
+                               over them, and the test is ||[r_1 .. r_R]|| <=
+                               tol ||[b_1 .. b_R]|| (a column of small norm may
+                               end above tol relative to itself).  The serving
+                               runtime refuses 1 (SMPM_EINVAL).                */
 } smpm_grid;
 
 typedef struct {
@@ -290,7 +301,8 @@ int smpm_apply_deflation_noalloc(smpm_handle h, int nrhs, const double* x, doubl
  * (<= 0: 80 % of the free device memory at create time); a batch that fits
  * nowhere runs alone, and a request whose own footprint exceeds the budget is
  * refused: smpm_submit still returns SMPM_OK and a ticket, and smpm_poll
- * reports SMPM_ENOMEM for it.
+ * reports SMPM_ENOMEM for it.  grid->krylov must be 0 (SMPM_EINVAL otherwise):
+ * requests batched together keep their own Krylov spaces.
  *   f, g, u: host or device pointers of r, nb and r doubles, owned by the
  *   caller, which must keep them valid and unchanged until smpm_poll() has
  *   returned something other than SMPM_EBUSY for the ticket.  g may be NULL.
@@ -307,6 +319,12 @@ int smpm_submit(smpm_server_t srv, const smpm_grid* grid, double k2, const doubl
                 double tol, double* u, unsigned long long* ticket);
 int smpm_poll(smpm_server_t srv, unsigned long long ticket, smpm_stats* st);
 int smpm_server_destroy(smpm_server_t srv);
+
+/* The estimated device footprint the admission above charges for a batch of
+ * nrhs requests with nop distinct k2 values on grid (bytes, written to
+ * *bytes): a caller sizes device_budget_bytes with it.  SMPM_EINVAL for a
+ * null argument, nop < 1 or nrhs < 1.  Host arithmetic only (no GPU call). */
+int smpm_request_footprint(const smpm_grid* grid, int nop, int nrhs, long long* bytes);
 
 /* Message of the calling thread's last failure ("" if none). */
 const char* smpm_last_error(void);

@@ -103,6 +103,7 @@ struct Solver {
     double *f3hat = nullptr, *g3hat = nullptr, *u3hat = nullptr, *f3stage = nullptr;
     long long cap3 = 0, capg3 = 0;
     int precision = 0;
+    int krylov = 0;                       // 1: one concatenated Krylov space per solve call
     double *uL = nullptr, *uS = nullptr;
     double* oneS = nullptr;                 // right null vector of S(0): 1 on the interface faces, unit norm
     int *rl_GW = nullptr, *rh_GW = nullptr, *rl_M = nullptr, *rh_M = nullptr, *rl_A = nullptr, *rh_A = nullptr;
@@ -1722,6 +1723,7 @@ static int solve_impl(Solver& S, const std::vector<int>& ops, const double* f, c
     ka.op = w.op; ka.strip_cls = S.d_strip_cls;
     ka.active = w.active; ka.done = w.done; ka.nit = w.nit; ka.target = w.target;
     ka.bnorm = w.bnorm; ka.rnorm = w.rnorm; ka.flags = w.flags;
+    ka.grp = S.krylov == 1 ? R : 1;
 
     // Nested mixed-precision form (precision 2): the outer flexible GMRES runs
     // on S itself (no deflation: K = null makes every coarse coefficient zero)
@@ -1971,7 +1973,7 @@ static int solve_impl(Solver& S, const std::vector<int>& ops, const double* f, c
         };
         // every step of this cycle in one persistent launch (the default for
         // precisions 0 and 1 when the profile is off)
-        const bool use_persist = S.persist_ok && !persist_off && !nested && !S.prof;
+        const bool use_persist = S.persist_ok && !persist_off && !nested && !S.prof && ka.grp <= 1;
         if (use_persist) {
             if (!S.d_pbar) {
                 S.d_pbar = S.dalloc<unsigned int>(1, S.allocs);
@@ -2286,6 +2288,8 @@ static Solver* make_solver(const smpm_grid* grid, int nop, const double* k2, voi
         throw Err{SMPM_EINVAL, msg};
     if (grid->precision < 0 || grid->precision > 2)
         throw Err{SMPM_EINVAL, "precision must be 0 (FP64), 1 (FP32 block-Jacobi) or 2 (FP32 inner DBJ-GMRES)"};
+    if (grid->krylov < 0 || grid->krylov > 1)
+        throw Err{SMPM_EINVAL, "krylov must be 0 (one Krylov space per right-hand side) or 1 (concatenated)"};
     S->nop = nop;
     S->k2.assign(k2, k2 + nop);
     int nzero = 0;
@@ -2296,6 +2300,7 @@ static Solver* make_solver(const smpm_grid* grid, int nop, const double* k2, voi
     if (nzero > 1) throw Err{SMPM_EINVAL, "at most one k2 = 0 operator per handle"};
     S->stream = (cudaStream_t)stream;
     S->precision = grid->precision;
+    S->krylov = grid->krylov;
     if (const char* e = std::getenv("SMPM_INNER_STEPS"))   // inner Arnoldi steps of precision 2
         S->inner_m = std::min(64, std::max(2, std::atoi(e)));
     setup_solver(*S);

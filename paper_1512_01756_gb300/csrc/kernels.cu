@@ -588,11 +588,40 @@ __global__ void __launch_bounds__(VB) cgs_kernel(KArgs a, int j, int mode) {
     cgs_body<VB>(a, j, mode, blockIdx.x, blockIdx.y, sm);
 }
 
+// Concatenated Krylov spaces (a.grp > 1): the partial sums of chunk blockIdx.x,
+// slots [0, nslots), summed over the columns of group blockIdx.y that take part
+// (gate 0: active, gate 1: not done) and written back to each of them, so that
+// every column's reduction over chunks yields the dot product (or norm) of the
+// concatenated vectors.  Columns are summed in index order (deterministic).
+__global__ void group_partials_kernel(KArgs a, double* __restrict__ part, int nslots, int gate) {
+    const int ch = blockIdx.x;
+    const int r0 = blockIdx.y * a.grp, r1 = min(r0 + a.grp, a.R);
+    const long long pstride = (long long)a.nch * (a.m + 2);
+    const long long off = (long long)ch * (a.m + 2);
+    for (int i = threadIdx.x; i < nslots; i += blockDim.x) {
+        double sum = 0.0;
+        for (int r = r0; r < r1; ++r)
+            if (gate == 0 ? a.active[r] != 0 : a.done[r] == 0) sum += part[(long long)r * pstride + off + i];
+        for (int r = r0; r < r1; ++r)
+            if (gate == 0 ? a.active[r] != 0 : a.done[r] == 0) part[(long long)r * pstride + off + i] = sum;
+    }
+}
+
+static void group_partials(const KArgs& a, double* part, int nslots, int gate, cudaStream_t s) {
+    if (a.grp <= 1) return;
+    dim3 grid(a.nch, (a.R + a.grp - 1) / a.grp);
+    group_partials_kernel<<<grid, 64, 0, s>>>(a, part, nslots, gate);
+    count_launches(1);
+}
+
 void k_cgs(const KArgs& a, int j, int mode, cudaStream_t s) {
     dim3 grid(a.nch, a.R);
     size_t sh = (size_t)(a.ch + a.m + 2 + 32) * sizeof(double);
     cgs_kernel<<<grid, VB, sh, s>>>(a, j, mode);
     count_launches(1);
+    // mode 0 leaves the first pass's dots in part1, mode 1 the second pass's in
+    // part2, mode 2 the squared norm in part1 slot 0
+    group_partials(a, mode == 1 ? a.part2 : a.part1, mode == 2 ? 1 : j + 1, 0, s);
 }
 
 template <int NT = VB>
@@ -890,6 +919,7 @@ void k_residual(const KArgs& a, const double* bS, const double* sv, cudaStream_t
     dim3 grid(a.nch, a.R);
     residual_kernel<<<grid, VB, 0, s>>>(a, bS, sv);
     count_launches(1);
+    group_partials(a, a.part1, 3, 1, s);   // ||P d||^2, ||b_S||^2, ||b_S - S x_S||^2
 }
 
 __global__ void __launch_bounds__(VB) cycle_start_kernel(KArgs a, double* __restrict__ c0, int stamp, double tol) {

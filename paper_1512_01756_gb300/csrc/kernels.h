@@ -48,6 +48,10 @@ struct KArgs {
     double* xlo;                   // [R][ld]
     const double* s_lo;            // [R][ld]
     const double* s_xlo;           // [R][ld]
+    // right-hand sides per Krylov space: 1 = one space per column; grp > 1:
+    // columns [g grp, (g+1) grp) form one concatenated vector (Sec. 5: all
+    // wavenumbers in one GMRES), every dot product and norm summed over them
+    int grp;
 };
 
 void k_deflate_sum(const KArgs& a, const double* v, const double* vsub, cudaStream_t s);

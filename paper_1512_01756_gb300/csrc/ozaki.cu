@@ -29,9 +29,9 @@
 // memory, one thread issues the tcgen05.mma instructions (M = 128, K = 16),
 // and the eight warps read the S accumulators back (tcgen05.ld: a warp
 // reads its 32 tensor-memory lanes, i.e. rows, for half of the columns) and
-// combine them.  Every wait has an iteration limit; a wait that
-// runs out sets the error word, the CTA stops issuing work, waits (bounded)
-// for its tensor-core work in flight and frees its tensor memory.
+// combine them.  Every wait is limited in time (0.2 s) and in tries; a wait
+// that runs out sets the error word, the CTA stops issuing work, waits
+// (bounded) for its tensor-core work in flight and frees its tensor memory.
 #include <cuda_runtime.h>
 #include <cuda_bf16.h>
 
@@ -47,6 +47,7 @@ constexpr int OZ_THREADS = 256;
 constexpr int OZ_KC = 128;                      // K-chunk: one shared-memory digit block
 constexpr int OZ_BLOCK = 128 * OZ_KC;           // BF16 values of one 128 x 128 digit block
 constexpr long long OZ_SPIN = 1LL << 22;        // iteration limit of every wait
+constexpr unsigned long long OZ_WAIT_NS = 200000000ULL;   // and its time limit (0.2 s)
 
 __device__ __forceinline__ uint32_t smem_addr(const void* p) {
     return (uint32_t)__cvta_generic_to_shared(p);
@@ -79,15 +80,20 @@ __device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, uint32_t bytes) {
                  : "memory");
 }
 
-// Wait for the phase with parity `phase` of a barrier to complete; false if
-// the iteration limit ran out.
+// Wait for the phase with parity `phase` of a barrier to complete; false
+// once OZ_WAIT_NS of wall time (the global timer) or OZ_SPIN tries have passed.
 __device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t phase) {
+    unsigned long long t0;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t0));
     for (long long it = 0; it < OZ_SPIN; ++it) {
         uint32_t ok;
         asm volatile("{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
                      "selp.u32 %0, 1, 0, p;\n\t}"
                      : "=r"(ok) : "r"(smem_addr(bar)), "r"(phase) : "memory");
         if (ok) return true;
+        unsigned long long t1;
+        asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t1));
+        if (t1 - t0 > OZ_WAIT_NS) return false;
     }
     return false;
 }
@@ -444,7 +450,7 @@ __global__ void __launch_bounds__(OZ_THREADS, 1) oz_gemm_kernel(OzArgs z, const 
     tc_fence_before();
     __syncthreads();
     if (fail && tid == 0)   // bounded grace period for tensor-core work still in flight
-        for (int i = 0; i < 65536; ++i) __nanosleep(1000);
+        for (int i = 0; i < 1000; ++i) __nanosleep(1000);
     __syncthreads();
     if (warp == 0)
         asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" :: "r"(tbase), "r"(512) : "memory");

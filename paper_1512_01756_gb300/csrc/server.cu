@@ -67,7 +67,8 @@ bool same_problem(const Request& a, const Request& b) {
     const smpm_grid &x = a.grid, &y = b.grid;
     return x.mx == y.mx && x.mz == y.mz && x.order == y.order && x.lx == y.lx && x.lz == y.lz &&
            x.z_ratio == y.z_ratio && x.tau_scale == y.tau_scale && x.deflation_groups == y.deflation_groups &&
-           x.restart == y.restart && x.max_iter == y.max_iter && x.precision == y.precision && a.tol == b.tol;
+           x.restart == y.restart && x.max_iter == y.max_iter && x.precision == y.precision && x.krylov == y.krylov &&
+           a.tol == b.tol;
 }
 
 // Device bytes of a batch: operators per k^2 (slot inverses, G, block-Jacobi
@@ -326,6 +327,10 @@ int smpm_submit(smpm_server_t srv, const smpm_grid* grid, double k2, const doubl
         smpm::set_last_error("smpm_submit: bad argument");
         return SMPM_EINVAL;
     }
+    if (grid->krylov != 0) {   // a batch joins unrelated requests: each keeps its own Krylov space
+        smpm::set_last_error("smpm_submit: krylov must be 0 for served requests");
+        return SMPM_EINVAL;
+    }
     auto q = std::make_unique<Request>();
     q->id = s->next_id++;
     q->grid = *grid;
@@ -372,6 +377,15 @@ int smpm_poll(smpm_server_t srv, unsigned long long ticket, smpm_stats* st) {
     if (rc != SMPM_OK) smpm::set_last_error(it->second->err);
     s->all.erase(it);
     return rc;
+}
+
+int smpm_request_footprint(const smpm_grid* grid, int nop, int nrhs, long long* bytes) {
+    if (!grid || !bytes || nop < 1 || nrhs < 1) {
+        smpm::set_last_error("smpm_request_footprint: bad argument");
+        return SMPM_EINVAL;
+    }
+    *bytes = footprint(*grid, nop, nrhs);
+    return SMPM_OK;
 }
 
 int smpm_server_destroy(smpm_server_t srv) {

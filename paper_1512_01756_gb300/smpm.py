@@ -21,14 +21,16 @@ EXPORTS = ["smpm_setup", "smpm_solve", "smpm_solve_batch", "smpm_solve_guess", "
            "smpm_setup_3d", "smpm_solve_3d", "smpm_solve_3d_physical",
            "smpm_sizes", "smpm_node_coords", "smpm_grid_coords", "smpm_null_vectors", "smpm_set_stream", "smpm_device_bytes", "smpm_release", "smpm_probe_fp64",
            "smpm_profile", "smpm_profile_read", "smpm_profile_split", "smpm_kernel_launches", "smpm_apply", "smpm_last_residuals", "smpm_apply_deflation_noalloc",
-           "smpm_server_create", "smpm_submit", "smpm_poll", "smpm_server_destroy", "smpm_last_error"]
+           "smpm_server_create", "smpm_submit", "smpm_poll", "smpm_server_destroy", "smpm_request_footprint",
+           "smpm_last_error"]
 
 
 class Grid(ctypes.Structure):
     _fields_ = [("mx", ctypes.c_int), ("mz", ctypes.c_int), ("order", ctypes.c_int),
                 ("lx", ctypes.c_double), ("lz", ctypes.c_double), ("z_ratio", ctypes.c_double),
                 ("tau_scale", ctypes.c_double), ("deflation_groups", ctypes.c_int),
-                ("restart", ctypes.c_int), ("max_iter", ctypes.c_int), ("precision", ctypes.c_int)]
+                ("restart", ctypes.c_int), ("max_iter", ctypes.c_int), ("precision", ctypes.c_int),
+                ("krylov", ctypes.c_int)]
 
 
 class Stats(ctypes.Structure):
@@ -93,6 +95,8 @@ def load():
                                 ctypes.POINTER(ctypes.c_ulonglong)]
     lib.smpm_poll.argtypes = [H, ctypes.c_ulonglong, ctypes.POINTER(Stats)]
     lib.smpm_server_destroy.argtypes = [H]
+    lib.smpm_request_footprint.argtypes = [ctypes.POINTER(Grid), ctypes.c_int, ctypes.c_int,
+                                           ctypes.POINTER(ctypes.c_longlong)]
     lib.smpm_kernel_launches.argtypes = []
     lib.smpm_kernel_launches.restype = ctypes.c_longlong
     for name in EXPORTS:
@@ -137,8 +141,8 @@ def _stream_ptr(stream):
 
 
 def make_grid(mx, mz, order, lx, lz, z_ratio=1.0, tau_scale=-0.1, deflation_groups=0, restart=64,
-              max_iter=2000, precision=0):
-    return Grid(mx, mz, order, lx, lz, z_ratio, tau_scale, deflation_groups, restart, max_iter, precision)
+              max_iter=2000, precision=0, krylov=0):
+    return Grid(mx, mz, order, lx, lz, z_ratio, tau_scale, deflation_groups, restart, max_iter, precision, krylov)
 
 
 class Solver:
@@ -262,6 +266,14 @@ class Solver3D(Solver):
         st = Stats()
         _check(load().smpm_solve_3d_physical(self._h, _ptr(f3), _ptr(g3), float(tol), _ptr(u3), ctypes.byref(st)))
         return st
+
+
+def request_footprint(grid: Grid, nop=1, nrhs=1):
+    """Device bytes the serving runtime's admission charges for a batch of
+    nrhs requests with nop distinct k^2 on grid (host arithmetic)."""
+    b = ctypes.c_longlong()
+    _check(load().smpm_request_footprint(ctypes.byref(grid), int(nop), int(nrhs), ctypes.byref(b)))
+    return b.value
 
 
 def grid_coords(grid: Grid):

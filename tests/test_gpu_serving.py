@@ -91,9 +91,14 @@ def test_mix_equals_alone_and_oracle(smpm, device_buffers, precision):
 
 
 def test_budget_serialises_but_completes(smpm):
-    """A one-byte budget admits one batch at a time; everything still finishes."""
+    """A budget between the footprint of one request and that of a batch of
+    two admits one batch at a time (a larger batch runs alone); everything
+    still finishes."""
     shape = (8, 2, 6, 4.0, 1.0)
-    srv = smpm.Server(nworkers=2, device_budget_bytes=1, max_batch=2)
+    one = smpm.request_footprint(smpm.make_grid(*shape), 1, 1)
+    two = smpm.request_footprint(smpm.make_grid(*shape), 2, 2)
+    assert two > one
+    srv = smpm.Server(nworkers=2, device_budget_bytes=(one + two) // 2, max_batch=2)
     fs = [_rhs(shape, 100 + i) for i in range(5)]
     us = [np.zeros_like(f) for f in fs]
     k2s = [0.0, 1.0, 2.0, 0.0, 50.0]
