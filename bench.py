@@ -78,6 +78,8 @@ def parse():
     p.add_argument("--cpu-seconds", type=float, default=20.0, help="serve: oracle time budget of the cpu_baseline leg")
     p.add_argument("--profiled-requests", type=int, default=300,
                    help="serve: requests re-run with the dense-product profile on (roofline)")
+    p.add_argument("--kernel-trace", type=int, default=0,
+                   help="serve: requests re-run under a CUDA activity trace (device time per kernel; 0 = off)")
     p.add_argument("--mixed-rhs", type=int, default=16, help="mixed: right-hand sides per step")
     p.add_argument("--workers", type=int, default=4, help="serve: server worker threads (one stream each)")
     p.add_argument("--max-batch", type=int, default=16, help="serve: requests per batch at most")
@@ -166,11 +168,18 @@ class Clocks:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
+def dense_product_source_sha():
+    """sha256 (16 hex digits) of the dense-product kernels' source: the part of
+    kernels.cu from the class GEMM's header comment to the deflation section."""
+    text = open(os.path.join(ROOT, "paper_1512_01756_gb300", "csrc", "kernels.cu"), "rb").read()
+    i, j = text.find(b"// Class GEMM:"), text.find(b"// Deflation (Sec. 3.3)")
+    return hashlib.sha256(text[i:j] if 0 <= i < j else text).hexdigest()[:16]
+
+
 def traffic_per_launch():
     """DRAM bytes per dense-product launch from the committed ncu summary, if it was
-    taken on the current kernels.cu (else None)."""
+    taken on the current dense-product kernels (else None)."""
     path = os.path.join(ROOT, "profiles", "gemm_traffic.txt")
-    src = os.path.join(ROOT, "paper_1512_01756_gb300", "csrc", "kernels.cu")
     if not os.path.exists(path):
         return None
     kv = {}
@@ -178,8 +187,7 @@ def traffic_per_launch():
         if "=" in line and not line.startswith("#"):
             k, v = line.split("=", 1)
             kv[k.strip()] = v.strip()
-    sha = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
-    if kv.get("kernels_cu_sha256_16") != sha:
+    if kv.get("dense_product_source_sha256_16") != dense_product_source_sha():
         return None
     try:
         return float(kv["dram_bytes_per_launch_scaled"])
@@ -461,8 +469,13 @@ def run_other(args):
     else:
         shape = dict(mx=512, mz=16, order=16, lx=32.0, lz=1.0, z_ratio=1.2)
         R = args.mixed_rhs
-        for prec in (0, 1, 2):
+        # (precision, SMPM_OZAKI): FP64, the two mixed forms with FP32
+        # CUDA-core products, and the same with the FP32 products on the
+        # tensor cores (24-bit digit splits)
+        for prec, oz in ((0, 0), (1, 0), (2, 0), (1, 2), (2, 2)):
+            os.environ["SMPM_OZAKI"] = str(oz)
             s = smpm.Solver(smpm.make_grid(**shape, precision=prec), 0.0, stream)
+            os.environ.pop("SMPM_OZAKI")
             x, z = s.coords()
             F = np.stack([inputs.cos_modes(x, z, 32.0, 1.0, inputs.cos_modes_spec(inputs.seed_for(3) + i))[0]
                           for i in range(R)])
@@ -477,7 +490,8 @@ def run_other(args):
                                       "geometrically (ratio 1.2), cos-cos modes, %d right-hand sides per step" % R,
                           "precision": ["FP64", "mixed: FP64 FGMRES, FP32 block-Jacobi",
                                         "nested mixed: FP64 FGMRES, inner DBJ-GMRES with FP32 Schur "
-                                        "and block-Jacobi blocks"][prec],
+                                        "and block-Jacobi blocks"][prec]
+                                       + (" (FP32 products on the tcgen05 tensor cores, 24-bit digit splits)" if oz else ""),
                           "metric": "solves/s at 1e-10 rel. residual", "value": R * 1e3 / ms, "ms_per_step": ms,
                           "iters": st.iters, "worst_rel_resid": st.rel_resid_true, "setup_ms": st.setup_ms,
                           "device_bytes": s.device_bytes()})
@@ -778,6 +792,32 @@ def run_serve(args):
                                   "frac": ach32 / FP32_SIMT_TFLOPS if ach32 else None, "launches": fp32["launches"],
                                   "peak_source": "152 SMs x 128 FP32 lanes x 2 FLOP x 2.07 GHz"}}
 
+    # 6. optional: device time per kernel of the served mix from the CUDA
+    # activity trace (CUPTI through torch.profiler, every stream and thread),
+    # the first requests re-served once more
+    shares = None
+    if args.kernel_trace > 0:
+        from torch.profiler import profile, ProfilerActivity
+        Pk = min(N, args.kernel_trace)
+        srv = smpm.Server(**srv_args)
+        with profile(activities=[ProfilerActivity.CUDA]) as prof_k:
+            _served_pass(srv, reqs[:Pk], lambda i: view(Fd, i), lambda i: view(Ub, i))
+            torch.cuda.synchronize()
+        srv.close()
+        from torch.autograd import DeviceType
+        tot, cnt = {}, {}
+        for ev in prof_k.events():
+            if ev.device_type != DeviceType.CUDA:       # device activity only (kernels, copies, sets)
+                continue
+            dt = ev.time_range.elapsed_us()
+            name = ev.name.split("(")[0].replace("void ", "")
+            tot[name] = tot.get(name, 0.0) + dt * 1e-3
+            cnt[name] = cnt.get(name, 0) + 1
+        T = sum(tot.values())
+        top = sorted(tot.items(), key=lambda kv: -kv[1])[:25]
+        shares = {"requests": Pk, "total_device_ms": T, "source": "CUPTI kernel activity via torch.profiler",
+                  "kernels": [{"name": k, "launches": cnt[k], "ms": v, "share": v / T} for k, v in top]}
+
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         n_o, secs, cores, biggest = oracle_serve_sample(reqs, args.cpu_seconds)
@@ -816,6 +856,8 @@ def run_serve(args):
             "gpu_launches": launches, "roofline": roofline, "cpu_baseline": cpu, "clocks": clk,
             "latency": "completion - arrival, operator setup included",
             "timing": "CUDA events on the launching stream around each pass, device synchronised on both sides"}
+    if shares is not None:
+        line["kernel_shares"] = shares
     if rank == 0 and not args.no_secondary:
         line["secondary_poisson2d"] = poisson2d_summary(args, smpm, dev, stream)
     if rank == 0:

@@ -92,7 +92,10 @@ typedef struct {
                                and block-Jacobi applies use FP32 blocks with FP32
                                accumulation (its block-Jacobi inverses are
                                factorised in FP32 too; 10 inner steps or 1e-4 relative;
-                               SMPM_INNER_STEPS overrides the step count)      */
+                               SMPM_INNER_STEPS overrides the step count) and whose
+                               CGS2 projections and dot products use FP32
+                               arithmetic on FP64-stored vectors
+                               (SMPM_INNER_FP64_ARNOLDI=1 keeps them FP64)      */
     int krylov;             /* 0: every right-hand side (every Fourier mode's real
                                and imaginary part) keeps its own Krylov space and
                                meets tol itself; 1: the right-hand sides of one

@@ -181,6 +181,7 @@ struct Solver {
         int S = 0, beta = 0, N = 0, mt_n = 0, kcn = 0;
     };
     bool oz = false;
+    int oz_mask = 0;                      // 1: FP64 products, 2: FP32 products on the tensor cores
     std::map<const double*, OzMat> ozmats;
     int* d_ozerr = nullptr;
     unsigned int* d_pbar = nullptr;
@@ -1086,25 +1087,49 @@ static void setup_solver(Solver& S) {
             k_to_fp32(S.Gh32, S.Gh, (long long)nop * 2 * fz * fz, st);
         }
     }
-    // SMPM_OZAKI=1: the FP64 Schur and block-Jacobi products on the tensor
-    // cores; their class matrices are split into BF16 digit tensors here
-    if (const char* oe = std::getenv("SMPM_OZAKI")) S.oz = std::atoi(oe) != 0;
+    // SMPM_OZAKI (bit mask): 1 = the FP64 Schur and block-Jacobi products on
+    // the tensor cores at FP64 accuracy (56-bit digit splits); 2 = the FP32
+    // products (the FP32 block-Jacobi of precision 1, the inner Schur and
+    // block-Jacobi products of precision 2) on the tensor cores at the 24-bit
+    // accuracy of FP32 (4-5 digits).  Their class matrices are split into BF16
+    // digit tensors here, keyed by the matrix array the products name.
+    if (const char* oe = std::getenv("SMPM_OZAKI")) S.oz_mask = std::atoi(oe) & 3;
+    if (S.precision == 0) S.oz_mask &= 1;
+    S.oz = S.oz_mask != 0;
     if (S.oz) {
-        auto split = [&](const double* mats, long long stride, int nmat, int Mm) {
+        auto split = [&](const void* key, const double* mats, const float* mats_f, long long stride, int nmat, int Mm,
+                         int bits) {
             Solver::OzMat z;
-            if (!oz_choose(Mm, z.S, z.beta, z.N)) return;
+            if (!oz_choose(Mm, z.S, z.beta, z.N, bits)) return;
             z.mt_n = (Mm + 127) / 128;
             z.kcn = (Mm + 127) / 128;
             z.dig_stride = (long long)z.mt_n * z.kcn * z.S * 128 * 128;
             z.rexp_stride = (long long)z.mt_n * 128;
             z.dig = S.dalloc<unsigned short>((size_t)nmat * z.dig_stride, S.allocs);
             z.rexp = S.dalloc<int>((size_t)nmat * z.rexp_stride, S.allocs);
-            k_oz_split_rows(mats, stride, nmat, Mm, Mm, z.S, z.beta, z.mt_n, z.kcn, z.dig, z.dig_stride, z.rexp,
-                            z.rexp_stride, st);
-            S.ozmats[mats] = z;
+            if (mats)
+                k_oz_split_rows(mats, stride, nmat, Mm, Mm, z.S, z.beta, z.mt_n, z.kcn, z.dig, z.dig_stride, z.rexp,
+                                z.rexp_stride, st);
+            else
+                k_oz_split_rows_f(mats_f, stride, nmat, Mm, Mm, z.S, z.beta, z.mt_n, z.kcn, z.dig, z.dig_stride,
+                                  z.rexp, z.rexp_stride, st);
+            S.ozmats[reinterpret_cast<const double*>(key)] = z;
         };
-        split(S.G, S.sG, nop * 3, 2 * fz);
-        split(S.Minv, S.sM, nop * S.nmc, 4 * fz);
+        // precision 2 keeps its block-Jacobi inverses in FP32 only
+        const bool minv64 = S.precision != 2;
+        if (S.oz_mask & 1) {
+            split(S.G, S.G, nullptr, S.sG, nop * 3, 2 * fz, 56);
+            if (minv64) split(S.Minv, S.Minv, nullptr, S.sM, nop * S.nmc, 4 * fz, 56);
+        }
+        if (S.oz_mask & 2) {
+            // digits of the FP64 matrix where the handle keeps one (more
+            // accurate than its FP32 copy), of the FP32 copy otherwise
+            if (S.G32) split(S.G32, S.G, nullptr, S.sG, nop * 3, 2 * fz, 24);
+            if (S.Minv32) {
+                if (minv64) split(S.Minv32, S.Minv, nullptr, S.sM, nop * S.nmc, 4 * fz, 24);
+                else split(S.Minv32, nullptr, S.Minv32, S.sM, nop * S.nmc, 4 * fz, 24);
+            }
+        }
         S.d_ozerr = S.dalloc<int>(1, S.allocs);
         CK(cudaMemsetAsync(S.d_ozerr, 0, sizeof(int), st));
     }
@@ -1439,7 +1464,8 @@ static int tune_shape(Solver& S, GemmArgs& a, const TileSet& ts, int epi, bool& 
 }
 
 static void run_gemm(Solver& S, GemmArgs a, const TileSet& ts, int epi) {
-    if (S.oz && !S.capturing_prof_block() && !a.fp32 && a.mirror_nb == 0 && (epi == 0 || epi == 1)) {
+    if (S.oz && !S.capturing_prof_block() && (S.oz_mask & (a.fp32 ? 2 : 1)) && a.mirror_nb == 0 &&
+        (epi == 0 || epi == 1)) {
         auto it = S.ozmats.find(a.mats);
         if (it != S.ozmats.end()) {
             const Solver::OzMat& m = it->second;
@@ -1462,6 +1488,7 @@ static void run_gemm(Solver& S, GemmArgs a, const TileSet& ts, int epi) {
             if (ok) return;
             cudaGetLastError();
             S.oz = false;                        // SIMT products from now on
+            S.oz_mask = 0;
         }
     }
     bool launched = false;
@@ -1584,7 +1611,7 @@ static int schur_calls(Solver& S, const double* in, long long in_rs, long long i
     a.add = add;
     a.active = active;
     const double* h = fp32 ? reinterpret_cast<const double*>(S.Gh32) : S.Gh;
-    if (!S.useG || h == nullptr || (S.oz && !fp32)) {
+    if (!S.useG || h == nullptr || (S.oz_mask & (fp32 ? 2 : 1))) {
         c[0] = GemmCall{a, &S.wk.tG, 1};
         return 1;
     }
@@ -1616,7 +1643,7 @@ static int bj_calls(Solver& S, const double* in, long long in_rs, long long in_o
     a.out = out; a.out_rs = out_rs; a.out_us = f4; a.out_off0 = out_off + fz; a.out_off1 = 0; a.msplit = f4;
     a.active = active;
     const double* h = fp32 ? reinterpret_cast<const double*>(S.Mh32) : S.Mh;
-    if (!S.useM || h == nullptr || (S.oz && !fp32)) {
+    if (!S.useM || h == nullptr || (S.oz_mask & (fp32 ? 2 : 1))) {
         c[0] = GemmCall{a, &S.wk.tM, 0};
         return 1;
     }
@@ -1737,6 +1764,7 @@ static int solve_impl(Solver& S, const std::vector<int>& ops, const double* f, c
         ki.part1 = w.part1i; ki.part2 = w.part2i; ki.q = w.qi; ki.c = w.ci;
         ki.active = w.activei; ki.done = w.donei; ki.nit = w.niti; ki.target = w.targeti;
         ki.bnorm = w.bnormi; ki.rnorm = w.rnormi; ki.flags = w.flagsi;
+        ki.f32 = std::getenv("SMPM_INNER_FP64_ARNOLDI") ? 0 : 1;
         ka.K = nullptr;
     }
 

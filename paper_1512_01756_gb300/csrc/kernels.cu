@@ -33,6 +33,12 @@ __device__ __forceinline__ double warp_sum(double v) {
     return v;
 }
 
+__device__ __forceinline__ float warp_sum(float v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+
 // Sum over a block of NT threads; every thread gets the result.
 template <int NT = VB>
 __device__ __forceinline__ double block_sum(double v, double* sh) {
@@ -523,7 +529,9 @@ __device__ __forceinline__ double zc_at(const KArgs& a, int r, long long e) {
 // CGS2 Arnoldi step (Sec. 3.1 orthogonalisation; CGS applied twice)
 // ---------------------------------------------------------------------------
 // Chunk bx of right-hand side r; sm: ch + m + 2 + 32 doubles of shared memory.
-template <int NT>
+// T: the arithmetic of the projections and dot products (storage stays FP64);
+// float for the inner solve of the nested mixed-precision form (a.f32).
+template <int NT, typename T = double>
 __device__ __forceinline__ void cgs_body(const KArgs& a, int j, int mode, int bx, int r, double* sm) {
     if (!a.active[r]) return;
     double* wsh = sm;                 // [ch]
@@ -551,10 +559,10 @@ __device__ __forceinline__ void cgs_body(const KArgs& a, int j, int mode, int bx
         }
         __syncthreads();
         for (int e = threadIdx.x; e < len; e += NT) {
-            double x = w[e0 + e];
-            for (int i = 0; i < nv; ++i) x = fma(-Vr[(long long)i * a.ld + e0 + e], hsh[i], x);
-            wsh[e] = x;
-            w[e0 + e] = x;
+            T x = (T)w[e0 + e];
+            for (int i = 0; i < nv; ++i) x = fma(-(T)Vr[(long long)i * a.ld + e0 + e], (T)hsh[i], x);
+            wsh[e] = (double)x;
+            w[e0 + e] = (double)x;
         }
         if (bx == 0) {
             if (mode == 1)
@@ -570,22 +578,25 @@ __device__ __forceinline__ void cgs_body(const KArgs& a, int j, int mode, int bx
         const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
         for (int i = wid; i < nv; i += NT / 32) {
             const double* vi = Vr + (long long)i * a.ld + e0;
-            double s = 0.0;
-            for (int e = lane; e < len; e += 32) s = fma(vi[e], wsh[e], s);
+            T s = T(0);
+            for (int e = lane; e < len; e += 32) s = fma((T)vi[e], (T)wsh[e], s);
             s = warp_sum(s);
-            if (lane == 0) pout[i] = s;
+            if (lane == 0) pout[i] = (double)s;
         }
     } else {
-        double s = 0.0;
-        for (int e = threadIdx.x; e < len; e += NT) s = fma(wsh[e], wsh[e], s);
-        s = block_sum<NT>(s, red);
+        T st = T(0);
+        for (int e = threadIdx.x; e < len; e += NT) st = fma((T)wsh[e], (T)wsh[e], st);
+        double s = block_sum<NT>((double)st, red);
         if (threadIdx.x == 0) a.part1[(long long)r * pstride + (long long)bx * (a.m + 2)] = s;
     }
 }
 
 __global__ void __launch_bounds__(VB) cgs_kernel(KArgs a, int j, int mode) {
     extern __shared__ double sm[];
-    cgs_body<VB>(a, j, mode, blockIdx.x, blockIdx.y, sm);
+    if (a.f32)
+        cgs_body<VB, float>(a, j, mode, blockIdx.x, blockIdx.y, sm);
+    else
+        cgs_body<VB, double>(a, j, mode, blockIdx.x, blockIdx.y, sm);
 }
 
 // Concatenated Krylov spaces (a.grp > 1): the partial sums of chunk blockIdx.x,

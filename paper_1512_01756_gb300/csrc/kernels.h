@@ -52,6 +52,10 @@ struct KArgs {
     // columns [g grp, (g+1) grp) form one concatenated vector (Sec. 5: all
     // wavenumbers in one GMRES), every dot product and norm summed over them
     int grp;
+    // 1: the CGS2 projections and dot products in FP32 arithmetic on the FP64
+    // vectors (the inner solve of the nested mixed-precision form, which only
+    // has to reach 1e-4 and whose Arnoldi work is bound by the FP64 pipe)
+    int f32;
 };
 
 void k_deflate_sum(const KArgs& a, const double* v, const double* vsub, cudaStream_t s);
@@ -126,11 +130,14 @@ struct OzArgs {
     int* err;                      // set to 2 by a wait that ran out of iterations
 };
 // beta, S and the column-tile width N for inner dimension K (false: K too large)
-bool oz_choose(int K, int& S, int& beta, int& N);
+bool oz_choose(int K, int& S, int& beta, int& N, int bits = 56);
 int oz_smem_bytes(int S, int N);
 void k_oz_split_rows(const double* mats, long long mat_stride, int nmat, int M, int K, int S, int beta, int mt_n,
                      int kcn, unsigned short* dig, long long dig_stride, int* rexp, long long rexp_stride,
                      cudaStream_t s);
+void k_oz_split_rows_f(const float* mats, long long mat_stride, int nmat, int M, int K, int S, int beta, int mt_n,
+                       int kcn, unsigned short* dig, long long dig_stride, int* rexp, long long rexp_stride,
+                       cudaStream_t s);
 // false if the launch could not be configured (shared-memory limit)
 bool launch_oz_gemm(const OzArgs& z, const Tile* d_tiles, int ntiles, cudaStream_t s);
 

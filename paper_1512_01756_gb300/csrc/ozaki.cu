@@ -17,7 +17,8 @@
 // which stays an exact integer while S K (2^beta - 1)^2 < 2^24 (beta is
 // chosen per K so that it does).  Keeping the diagonals d <= S + 1 drops
 // terms below 2^-(S beta) of |a|_max,row |b|_max,col per product term (S beta
-// >= 56 bits: at or below FP64 rounding), and the sum
+// >= 56 bits: at or below FP64 rounding; S beta >= 24 bits in the variant
+// that replaces FP32 products), and the sum
 //     (A B)_ij = 2^(Ea_i + Eb_j - (S+1) beta) sum_d 2^((S+1-d) beta) D_d
 // is formed exactly in 64-bit integers and rounded once to FP64.
 //
@@ -185,17 +186,18 @@ __device__ __forceinline__ int exp_bound(double amax) {
 // tensor cores' K-major core-matrix order at
 //     dig + m * dig_stride + ((mt * kcn + kc) * S + s) * OZ_BLOCK;
 // rows >= M and columns >= K are zero digits.  One warp per row.
-__global__ void oz_split_rows_kernel(const double* __restrict__ mats, long long mat_stride, int nmat, int M, int K,
+template <typename T>
+__global__ void oz_split_rows_kernel(const T* __restrict__ mats, long long mat_stride, int nmat, int M, int K,
                                      int S, int beta, int mt_n, int kcn, unsigned short* __restrict__ dig,
                                      long long dig_stride, int* __restrict__ rexp, long long rexp_stride) {
     const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
     const int rows = mt_n * 128;
     if (warp >= nmat * rows) return;
     const int m = warp / rows, row = warp - m * rows;
-    const double* a = mats + (long long)m * mat_stride + (long long)row * K;
+    const T* a = mats + (long long)m * mat_stride + (long long)row * K;
     double amax = 0.0;
     if (row < M)
-        for (int k = lane; k < K; k += 32) amax = fmax(amax, fabs(a[k]));
+        for (int k = lane; k < K; k += 32) amax = fmax(amax, fabs((double)a[k]));
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) amax = fmax(amax, __shfl_xor_sync(0xffffffffu, amax, o));
     const int E = exp_bound(amax);
@@ -204,7 +206,7 @@ __global__ void oz_split_rows_kernel(const double* __restrict__ mats, long long 
     const unsigned mask = (1u << beta) - 1u;
     for (int k = lane; k < kcn * OZ_KC; k += 32) {
         bool neg = false;
-        const unsigned long long x = (row < M && k < K) ? fixed_of(a[k], E, sb, neg) : 0ULL;
+        const unsigned long long x = (row < M && k < K) ? fixed_of((double)a[k], E, sb, neg) : 0ULL;
         const int kc = k / OZ_KC, kk = k - kc * OZ_KC;
         unsigned short* base = dig + (long long)m * dig_stride + (long long)((mt * kcn + kc) * S) * OZ_BLOCK;
         for (int s = 0; s < S; ++s) {
@@ -462,8 +464,17 @@ void k_oz_split_rows(const double* mats, long long mat_stride, int nmat, int M, 
                      int kcn, unsigned short* dig, long long dig_stride, int* rexp, long long rexp_stride,
                      cudaStream_t s) {
     const long long warps = (long long)nmat * mt_n * 128;
-    oz_split_rows_kernel<<<(unsigned)((warps * 32 + 255) / 256), 256, 0, s>>>(mats, mat_stride, nmat, M, K, S, beta, mt_n,
-                                                                               kcn, dig, dig_stride, rexp, rexp_stride);
+    oz_split_rows_kernel<double><<<(unsigned)((warps * 32 + 255) / 256), 256, 0, s>>>(
+        mats, mat_stride, nmat, M, K, S, beta, mt_n, kcn, dig, dig_stride, rexp, rexp_stride);
+    count_launches(1);
+}
+
+void k_oz_split_rows_f(const float* mats, long long mat_stride, int nmat, int M, int K, int S, int beta, int mt_n,
+                       int kcn, unsigned short* dig, long long dig_stride, int* rexp, long long rexp_stride,
+                       cudaStream_t s) {
+    const long long warps = (long long)nmat * mt_n * 128;
+    oz_split_rows_kernel<float><<<(unsigned)((warps * 32 + 255) / 256), 256, 0, s>>>(
+        mats, mat_stride, nmat, M, K, S, beta, mt_n, kcn, dig, dig_stride, rexp, rexp_stride);
     count_launches(1);
 }
 
@@ -487,16 +498,21 @@ bool launch_oz_gemm(const OzArgs& z, const Tile* d_tiles, int ntiles, cudaStream
     if (z.S == 8 && z.beta == 7 && z.N == 64) return launch_oz_t<8, 7, 64>(z, d_tiles, ntiles, s);
     if (z.S == 10 && z.beta == 6 && z.N == 32) return launch_oz_t<10, 6, 32>(z, d_tiles, ntiles, s);
     if (z.S == 12 && z.beta == 5 && z.N == 32) return launch_oz_t<12, 5, 32>(z, d_tiles, ntiles, s);
+    if (z.S == 4 && z.beta == 7 && z.N == 64) return launch_oz_t<4, 7, 64>(z, d_tiles, ntiles, s);
+    if (z.S == 4 && z.beta == 6 && z.N == 64) return launch_oz_t<4, 6, 64>(z, d_tiles, ntiles, s);
+    if (z.S == 5 && z.beta == 5 && z.N == 64) return launch_oz_t<5, 5, 64>(z, d_tiles, ntiles, s);
     return false;
 }
 
-// Digit-size choice for K: the largest beta <= 7 with S = ceil(56 / beta)
+// Digit-size choice for K: the largest beta <= 7 with S = ceil(bits / beta)
 // digits such that S K (2^beta - 1)^2 < 2^24 (exact FP32 accumulation of a
 // whole anti-diagonal over all of K); N = 64 columns per tile for S <= 8,
-// 32 above (S N <= 512 tensor-memory columns).
-bool oz_choose(int K, int& S, int& beta, int& N) {
+// 32 above (S N <= 512 tensor-memory columns).  bits = 56 gives FP64
+// accuracy, bits = 24 the 24-bit significand of FP32 (the products that
+// replace FP32 CUDA-core products).
+bool oz_choose(int K, int& S, int& beta, int& N, int bits) {
     for (beta = 7; beta >= 5; --beta) {
-        S = (56 + beta - 1) / beta;
+        S = (bits + beta - 1) / beta;
         const double bound = (double)S * K * (double)((1 << beta) - 1) * (double)((1 << beta) - 1);
         if (bound < 16777216.0) {
             N = S <= 8 ? 64 : 32;

@@ -116,3 +116,71 @@ def test_tensor_core_solve_long_domain(smpm, monkeypatch):
     assert st.status == 0 and st.rel_resid_true <= 1e-10
     u_ref, _ = dbj.solve(g, f, method="dbj", tol=1e-13)
     assert _rel(u, u_ref) < 1e-9, _rel(u, u_ref)
+
+
+# --- FP32-accuracy variant (SMPM_OZAKI bit 2): the FP32 products of the mixed
+# forms (precision 1's block-Jacobi, precision 2's inner Schur and
+# block-Jacobi products) with 24-bit digit splits (4 digits of 7 or 6 bits,
+# 5 of 5 bits for K > 1056)
+
+def _handle_p(smpm, monkeypatch, oz, shape, precision, k2=0.0):
+    monkeypatch.setenv("SMPM_OZAKI", str(oz))
+    mx, mz, order, lx, lz, zr = shape
+    return smpm.Solver(smpm.make_grid(mx, mz, order, lx, lz, z_ratio=zr, precision=precision), k2)
+
+
+@pytest.mark.parametrize("shape", [(8, 2, 8, 4.0, 1.0, 1.0), (6, 8, 10, 1.5, 1.0, 1.0), (4, 16, 16, 0.5, 1.0, 1.2)])
+def test_fp32_tensor_core_block_jacobi(smpm, monkeypatch, shape):
+    """precision 2's block-Jacobi apply (FP32 inverses) through the 24-bit
+    tensor-core products against the FP32 CUDA-core products of the same
+    inverses (rounding-level agreement) and against the FP64 inverses (the
+    same distance as the CUDA-core products: both are set by the FP32
+    factorisation)."""
+    R = 24
+    so = _handle_p(smpm, monkeypatch, 2, shape, 2)
+    sf = _handle_p(smpm, monkeypatch, 0, shape, 2)
+    s64 = _handle_p(smpm, monkeypatch, 0, shape, 0)
+    X = np.random.default_rng(83).standard_normal((R, so.k))
+    X[2] *= 1e-6
+    out = {}
+    for name, s in (("oz", so), ("f32", sf), ("f64", s64)):
+        Y = np.zeros_like(X)
+        s.apply("Minv", X, Y)
+        out[name] = Y
+        s.close()
+    worst_of, worst_f = 0.0, 0.0
+    for i in range(R):
+        d_of = _rel(out["oz"][i], out["f32"][i])
+        e_o, e_f = _rel(out["oz"][i], out["f64"][i]), _rel(out["f32"][i], out["f64"][i])
+        worst_of = max(worst_of, d_of)
+        worst_f = max(worst_f, e_f)
+        assert d_of < 1e-4, (i, d_of)
+        assert e_o <= 1.5 * e_f + 1e-6, (i, e_o, e_f)
+    print(f"tensor-core vs CUDA-core FP32 products {worst_of:.2e}; FP32 inverses vs FP64 {worst_f:.2e}")
+
+
+@pytest.mark.parametrize("shape,k2,precision", [((8, 2, 8, 4.0, 1.0, 1.0), 0.0, 2), ((12, 4, 9, 3.0, 1.0, 1.2), 0.0, 2),
+                                                ((10, 3, 7, 2.5, 1.0, 1.0), 30.0, 2), ((32, 16, 16, 2.0, 1.0, 1.2), 0.0, 2),
+                                                ((12, 4, 9, 3.0, 1.0, 1.2), 0.0, 1)])
+def test_fp32_tensor_core_solve_matches_oracle(smpm, monkeypatch, shape, k2, precision):
+    """Mixed-precision solves with the FP32 products on the tensor cores
+    (SMPM_OZAKI=2) and with every product on them (SMPM_OZAKI=3): 1e-10
+    residual, the oracle's solution at 1e-9."""
+    g = Grid(*shape[:5], z_ratio=shape[5])
+    F = np.random.default_rng(84).uniform(0, 1, (2, g.r))
+    refs = [direct_solve(g, F[i], None, k2)[0] for i in range(2)] if g.r <= 20000 else None
+    if refs is None:
+        ref_s = _handle_p(smpm, monkeypatch, 0, shape, 0, k2)
+        U0 = np.zeros_like(F)
+        st0 = ref_s.solve(F, U0, tol=1e-11)
+        ref_s.close()
+        assert st0.rel_resid_true <= 1e-11
+        refs = list(U0)
+    for oz in (2, 3):
+        s = _handle_p(smpm, monkeypatch, oz, shape, precision, k2)
+        U = np.zeros_like(F)
+        st = s.solve(F, U, tol=1e-10)
+        s.close()
+        assert st.status == 0 and st.rel_resid_true <= 1e-10, (oz, st.as_dict())
+        for i in range(2):
+            assert _rel(U[i], refs[i]) < 1e-9, (oz, i, _rel(U[i], refs[i]))
