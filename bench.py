@@ -850,6 +850,7 @@ def run_serve(args):
                        "worst_rel_resid": max(worst_arr, worst_burst, worst_e2e),
                        "max_rel_diff_vs_plain": max(d_arr, d_burst), "max_abs_diff_vs_plain_rel_to_max": max(dmax_arr, dmax_burst)},
             "plain_fp64": {"solves_per_s": N / plain_span, "mean_service_ms": 1e3 * plain_span / N,
+                           "mean_setup_ms": float(np.mean([q["setup_ms"] for q in reqs])),
                            "worst_rel_resid": max(res_plain), "mean_iters": float(np.mean(it_plain))},
             "e2e": {"value": N * world / e2e_max, "unit": "solves/s", "h2d_bytes_per_step": bytes_f // K,
                     "d2h_bytes_per_step": bytes_f // K, "max_diff_vs_device_pass": d_e2e},

@@ -989,14 +989,32 @@ static void setup_solver(Solver& S) {
     CK(cudaMemcpyAsync(rho_h.data(), S.rho, sizeof(double) * rho_h.size(), cudaMemcpyDeviceToHost, st));
     CK(cudaStreamSynchronize(st));
     const int gs = fz / ng;
+    // One deflation vector per interface (ng = 1): C is tridiagonal (an
+    // interface couples to its two neighbours through the strips between
+    // them), and for k^2 > 0 it is nonsingular, so K = C^-1 comes from a
+    // pivoted tridiagonal LU on the host (O(d)) and one GPU thread per column
+    // (O(d^2) in all) instead of a dense d x d factorisation and d solves.
+    // SMPM_COARSE_DENSE=1 takes the dense path for every operator.
+    const bool tri_path = ng == 1 && std::getenv("SMPM_COARSE_DENSE") == nullptr;
+    bool any_dense = false;
+    for (int o = 0; o < nop; ++o) any_dense |= !(tri_path && S.k2[o] > 0.0);
     int lwork_d = 0;
-    CS(cusolverDnDgetrf_bufferSize(S.sol, d, d, S.K, d, &lwork_d));
-    double* dC = S.dalloc<double>((size_t)d * d, tmp);
-    double* dwork_d = S.dalloc<double>((size_t)std::max(lwork_d, 1), tmp);
-    int* dipiv_d = S.dalloc<int>((size_t)d, tmp);
-    double* duC = S.dalloc<double>((size_t)d, tmp);
-    double* dw = S.dalloc<double>((size_t)d, tmp);
-    std::vector<double> C((size_t)d * d), uC;
+    double *dC = nullptr, *dwork_d = nullptr, *duC = nullptr, *dw = nullptr;
+    int* dipiv_d = nullptr;
+    std::vector<double> C, uC;
+    if (any_dense) {
+        CS(cusolverDnDgetrf_bufferSize(S.sol, d, d, S.K, d, &lwork_d));
+        dC = S.dalloc<double>((size_t)d * d, tmp);
+        dwork_d = S.dalloc<double>((size_t)std::max(lwork_d, 1), tmp);
+        dipiv_d = S.dalloc<int>((size_t)d, tmp);
+        duC = S.dalloc<double>((size_t)d, tmp);
+        dw = S.dalloc<double>((size_t)d, tmp);
+        C.resize((size_t)d * d);
+    }
+    double* dfac = S.dalloc<double>((size_t)nop * 4 * std::max(d, 1), tmp);
+    int* dswap = S.dalloc<int>((size_t)nop * std::max(d, 1), tmp);
+    std::vector<std::vector<double>> tri_fac(nop);       // kept until the copies have run
+    std::vector<std::vector<int>> tri_swap(nop);
     for (int o = 0; o < nop; ++o) {
         const double k2 = S.k2[o];
         const double* rho_o = rho_h.data() + (size_t)o * S.sRho;
@@ -1008,6 +1026,31 @@ static void setup_solver(Solver& S) {
             for (int z = 0; z < gs; ++z) sm += v[z];
             return sm;
         };
+        if (tri_path && k2 > 0.0) {
+            // C(t, t), C(t+1, t), C(t-1, t) as in the dense assembly below
+            std::vector<double> dl((size_t)std::max(d - 1, 0)), dd((size_t)d), du((size_t)std::max(d - 1, 0)), du2;
+            for (int t = 0; t < nif; ++t) {
+                const int cl_r = S.strip_cls[t + 1], cl_l = S.strip_cls[t];
+                dd[t] = 2.0 * gs + gsum(cl_r, 0, 0, 0, 0) + gsum(cl_l, 1, 0, 1, 0);
+                if (t >= 1) du[t - 1] = gsum(cl_l, 1, 0, 0, 0);
+                if (t + 1 <= nif - 1) dl[t] = gsum(cl_r, 0, 0, 1, 0);
+            }
+            std::vector<int>& sw = tri_swap[o];
+            if (!tridiag_lu(d, dl, dd, du, du2, sw))
+                throw Err{SMPM_EBREAKDOWN, "singular coarse matrix (zero pivot of the tridiagonal LU)"};
+            std::vector<double>& fac = tri_fac[o];
+            fac.reserve((size_t)4 * d);
+            fac.insert(fac.end(), dl.begin(), dl.end());
+            fac.insert(fac.end(), dd.begin(), dd.end());
+            fac.insert(fac.end(), du.begin(), du.end());
+            fac.insert(fac.end(), du2.begin(), du2.end());
+            double* fo = dfac + (size_t)o * 4 * std::max(d, 1);
+            int* so = dswap + (size_t)o * std::max(d, 1);
+            CK(cudaMemcpyAsync(fo, fac.data(), sizeof(double) * fac.size(), cudaMemcpyHostToDevice, st));
+            if (!sw.empty()) CK(cudaMemcpyAsync(so, sw.data(), sizeof(int) * sw.size(), cudaMemcpyHostToDevice, st));
+            k_tridiag_inverse(S.K + (size_t)o * S.sK, fo, so, d, st);
+            continue;
+        }
         std::fill(C.begin(), C.end(), 0.0);
         for (int t = 0; t < nif; ++t)
             for (int gg = 0; gg < ng; ++gg) {
@@ -1667,8 +1710,24 @@ static int solve_impl(Solver& S, const std::vector<int>& ops, const double* f, c
     if (R <= 0) throw Err{SMPM_EINVAL, "nrhs must be positive"};
     if (!(tol > 0.0)) throw Err{SMPM_EINVAL, "tol must be positive"};
     if (!f || !u) throw Err{SMPM_EINVAL, "f and u must not be null"};
+    // SMPM_TRACE_PHASES=1: wall time of the solve's phases on stderr (the
+    // stream is synchronised at every phase boundary, so this slows the solve)
+    const bool tphase = std::getenv("SMPM_TRACE_PHASES") != nullptr;
+    auto tp_last = std::chrono::steady_clock::now();
+    std::string tp_msg;
+    auto phase = [&](const char* name) {
+        if (!tphase) return;
+        CK(cudaStreamSynchronize(S.stream));
+        const auto now = std::chrono::steady_clock::now();
+        char buf[96];
+        snprintf(buf, sizeof(buf), " %s=%.2f", name, std::chrono::duration<double, std::milli>(now - tp_last).count());
+        tp_msg += buf;
+        tp_last = now;
+    };
     ensure_workspace(S, R);
+    phase("workspace");
     prepare_ops(S, ops);
+    phase("tiles");
     const Geometry& g = S.g;
     auto& w = S.wk;
     cudaStream_t st_ = S.stream;
@@ -1740,6 +1799,7 @@ static int solve_impl(Solver& S, const std::vector<int>& ops, const double* f, c
         fprintf(stderr, "\n");
     }
 
+    phase("rhs");
     KArgs ka;
     std::memset(&ka, 0, sizeof(ka));
     ka.R = R; ka.m = m; ka.nch = nch; ka.ch = kChunk; ka.ld = ld; ka.kp = S.kp;
@@ -2146,6 +2206,7 @@ static int solve_impl(Solver& S, const std::vector<int>& ops, const double* f, c
         ++cycles;
         first = false;
     }
+    phase("cycles");
     // recovery: u = A^-1 (b - E x_S)  (Alg. seq step 9)
     if (S.fss) {
         fss_refined(S, fa, R, w.b, g.r, u_d, g.r, w.xS, ld, w.k2r, w.fs1, w.fs2, w.fs3, w.tS1, w.tS2);
@@ -2159,6 +2220,8 @@ static int solve_impl(Solver& S, const std::vector<int>& ops, const double* f, c
         run_gemm(S, a, w.tA, 0);
     }
     k_gauge(ga, R, u_d, g.r, w.gauge, w.rpart, rch, kChunk, st_);
+    phase("recovery");
+    if (tphase) fprintf(stderr, "smpm solve phases (ms, R=%d, %d cycles):%s\n", R, cycles, tp_msg.c_str());
     if (!u_dev) CK(cudaMemcpyAsync(u, u_d, sizeof(double) * g.r * R, cudaMemcpyDeviceToHost, st_));
     std::vector<double> h_r(R), h_b(R);
     CK(cudaMemcpyAsync(h_r.data(), w.rnorm, R * sizeof(double), cudaMemcpyDeviceToHost, st_));

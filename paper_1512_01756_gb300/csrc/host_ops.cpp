@@ -448,6 +448,42 @@ void coarse_matrix(std::vector<double>& C, int d, int fz_over_ng, const double* 
         for (int j = 0; j < d; ++j) C[(size_t)i * d + j] += a * uC[i];
 }
 
+// LU factorisation with partial pivoting of a tridiagonal matrix (the coarse
+// matrix with one deflation vector per interface couples each interface to its
+// two neighbours only).  On entry dl[i] = T(i+1, i), dd[i] = T(i, i),
+// du[i] = T(i, i+1); on exit dl holds the multipliers, dd the diagonal of U,
+// du and du2 its first and second superdiagonals, and swap[i] = 1 where rows
+// i and i+1 were interchanged at step i.  Row interchanges between neighbours
+// are the only fill-in, into du2.  Returns false if a pivot is zero.
+bool tridiag_lu(int d, std::vector<double>& dl, std::vector<double>& dd, std::vector<double>& du,
+                std::vector<double>& du2, std::vector<int>& swap) {
+    du2.assign((size_t)std::max(d - 2, 0), 0.0);
+    swap.assign((size_t)std::max(d - 1, 0), 0);
+    for (int i = 0; i + 1 < d; ++i) {
+        if (std::fabs(dd[i]) >= std::fabs(dl[i])) {
+            if (dd[i] == 0.0) return false;
+            const double l = dl[i] / dd[i];
+            dl[i] = l;
+            dd[i + 1] -= l * du[i];
+        } else {
+            // rows i and i+1 trade places: the new row i is the old row i+1
+            // (dl[i], dd[i+1], du[i+1]), the eliminated one the old row i
+            const double l = dd[i] / dl[i];
+            dd[i] = dl[i];
+            dl[i] = l;
+            const double u1 = du[i];
+            du[i] = dd[i + 1];
+            dd[i + 1] = u1 - l * dd[i + 1];
+            if (i + 2 < d) {
+                du2[i] = du[i + 1];
+                du[i + 1] = -l * du[i + 1];
+            }
+            swap[i] = 1;
+        }
+    }
+    return d == 0 || dd[d - 1] != 0.0;
+}
+
 // --- real block diagonalisation of a small nonsymmetric matrix ----------------
 //
 // Ax = Q B Q^-1 with B block diagonal: a 1 x 1 block per real eigenvalue and a

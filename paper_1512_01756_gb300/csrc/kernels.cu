@@ -1287,6 +1287,55 @@ __global__ void rank1_sub_kernel(double* __restrict__ A, const double* __restric
     A[idx] -= w[i] * u[j];
 }
 
+// K = T^-1 (row-major d x d) of a tridiagonal T from its pivoted LU factors
+// (tridiag_lu): thread j solves T x = e_j and writes x into column j of K,
+// which also holds the forward-substitution values in between.  The threads
+// of a warp take adjacent columns, so every row access is one coalesced line.
+// fac: [dl (d-1)][dd (d)][du (d-1)][du2 (d-2)], swap: [d-1].
+__global__ void tridiag_inverse_kernel(double* __restrict__ K, const double* __restrict__ fac,
+                                       const int* __restrict__ swap, int d) {
+    const int j = blockIdx.x * blockDim.x + threadIdx.x;
+    if (j >= d) return;
+    const double* dl = fac;
+    const double* dd = dl + (d - 1);
+    const double* du = dd + d;
+    const double* du2 = du + (d - 1);
+    // forward: L y = P e_j (rows above j - 1 stay zero: the interchanges
+    // before step j - 1 only mix zeros)
+    for (int i = 0; i < j - 1; ++i) K[(long long)i * d + j] = 0.0;
+    const int i0 = j > 0 ? j - 1 : 0;
+    double cur = (i0 == j) ? 1.0 : 0.0;            // y[i] at step i
+    for (int i = i0; i + 1 < d; ++i) {
+        const double nxt = (i + 1 == j) ? 1.0 : 0.0;   // untouched entry i+1 of e_j
+        double yi, yn;
+        if (swap[i]) {
+            yi = nxt;
+            yn = cur - dl[i] * nxt;
+        } else {
+            yi = cur;
+            yn = nxt - dl[i] * cur;
+        }
+        K[(long long)i * d + j] = yi;
+        cur = yn;
+    }
+    // backward: U x = y, U with two superdiagonals
+    double x1 = cur / dd[d - 1], x2 = 0.0;         // x[i+1], x[i+2]
+    K[(long long)(d - 1) * d + j] = x1;
+    for (int i = d - 2; i >= 0; --i) {
+        double v = K[(long long)i * d + j] - du[i] * x1;
+        if (i + 2 < d) v -= du2[i] * x2;
+        v /= dd[i];
+        K[(long long)i * d + j] = v;
+        x2 = x1;
+        x1 = v;
+    }
+}
+
+void k_tridiag_inverse(double* K, const double* fac, const int* swap, int d, cudaStream_t s) {
+    tridiag_inverse_kernel<<<(d + 127) / 128, 128, 0, s>>>(K, fac, swap, d);
+    count_launches(1);
+}
+
 void k_project_coarse(double* K, double* w, const double* u, int d, cudaStream_t s) {
     rowdot_kernel<<<(d + 7) / 8, 256, 0, s>>>(w, K, u, d);
     const long long tot = (long long)d * d;

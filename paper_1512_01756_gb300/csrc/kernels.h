@@ -191,6 +191,7 @@ void k_mirror_halves_nodes(double* H, const double* Mat, long long count, int fz
 void k_invert_flags(int* done, const int* active, int R, cudaStream_t s);
 // K <- K - (K u) u^T (row-major d x d, w: d scratch): the projected coarse division
 void k_project_coarse(double* K, double* w, const double* u, int d, cudaStream_t s);
+void k_tridiag_inverse(double* K, const double* fac, const int* swap, int d, cudaStream_t s);
 void k_build_W(double* W, const double* Ainv, const double* beta, int n, int fz, cudaStream_t s);
 void k_build_G(double* G, const double* W, int n, int fz, int cls, cudaStream_t s);
 // Pair block of block-Jacobi (Sec. 3.2) from the G of strips 2p, 2p+1, 2p+2

@@ -78,6 +78,8 @@ bool left_null_z(const Geometry& g, std::vector<double>& v, std::string& msg);
 // (I - uC uC^T) is the coarse division K (the zero-mean solution of the
 // consistent coarse system); else C unchanged (K = C^-1).
 void coarse_matrix(std::vector<double>& C, int d, int fz_over_ng, const double* uC);
+bool tridiag_lu(int d, std::vector<double>& dl, std::vector<double>& dd, std::vector<double>& du,
+                std::vector<double>& du2, std::vector<int>& swap);
 
 // Ax = Q B Q^-1 with B block diagonal in real form: slot t covers columns
 // [slot_start, slot_start + slot_size) of Q; size 1: eigenvalue alpha; size 2:
