@@ -509,8 +509,33 @@ static void setup_solver(Solver& S) {
             S.ns1 = std::max(S.ns1, c1);
             S.ns2 = std::max(S.ns2, c2);
         }
-        S.S1 = S.dalloc<double>((size_t)nop * 3 * std::max(S.ns1, 1) * fz * fz, S.allocs);
-        S.S2 = S.dalloc<double>((size_t)nop * 3 * std::max(S.ns2, 1) * 4 * fz * fz, S.allocs);
+        // With uniform h_z (and the same Neumann condition at the bottom and
+        // the top) L_z commutes with the reversal J of the z-nodes, and so does
+        // every slot matrix L_z + s I and its 2 x 2 block form.  In the basis
+        // of the node pairs (p, J p) a slot matrix is [[A, B], [B, A]], so its
+        // inverse is the mirror form with halves (A + B)^-1 / 2 and
+        // (A - B)^-1 / 2: two inversions of half the size (a quarter of the
+        // FLOPs) and slot products on half-size matrices.  The refinement step
+        // of every fast solve uses the exact operator, so rounding-level
+        // differences of the halves do not reach a result.
+        S.zmir = false;
+        if (fz % 2 == 0 && S.mirror_mode != 0) {
+            double diff = 0.0, amax = 0.0;
+            for (int i = 0; i < fz; ++i)
+                for (int j = 0; j < fz; ++j) {
+                    amax = std::max(amax, std::fabs(Lz[(size_t)i * fz + j]));
+                    diff = std::max(diff, std::fabs(Lz[(size_t)(fz - 1 - i) * fz + (fz - 1 - j)] - Lz[(size_t)i * fz + j]));
+                }
+            S.zmir = diff <= 1e-13 * amax;
+        }
+        if (S.zmir) {
+            const long long c1 = (long long)nop * 3 * std::max(S.ns1, 1), c2 = (long long)nop * 3 * std::max(S.ns2, 1);
+            S.S1h = S.dalloc<double>((size_t)c1 * fz * fz / 2, S.allocs);
+            S.S2h = S.dalloc<double>((size_t)c2 * 2 * fz * fz, S.allocs);
+        } else {
+            S.S1 = S.dalloc<double>((size_t)nop * 3 * std::max(S.ns1, 1) * fz * fz, S.allocs);
+            S.S2 = S.dalloc<double>((size_t)nop * 3 * std::max(S.ns2, 1) * 4 * fz * fz, S.allocs);
+        }
         std::vector<double> q3(3 * (size_t)n * n), qi3(3 * (size_t)n * n), b3(3 * 2 * (size_t)n);
         for (int c = 0; c < 3; ++c) {
             std::copy(Qh[c].begin(), Qh[c].end(), q3.begin() + (size_t)c * n * n);
@@ -688,7 +713,7 @@ static void setup_solver(Solver& S) {
         }
     }
     int n_inv = 0;
-    for (int c = 0; c < 3 && S.fss; ++c) n_inv += (int)S.sl_size[c].size();
+    for (int c = 0; c < 3 && S.fss; ++c) n_inv += (S.zmir ? 2 : 1) * (int)S.sl_size[c].size();
     n_inv = nop * (n_inv + S.nmc + 1);
     int* d_infos = S.dalloc<int>((size_t)2 * n_inv, tmp);
     CK(cudaMemsetAsync(d_infos, 0, sizeof(int) * 2 * n_inv, st));
@@ -716,6 +741,16 @@ static void setup_solver(Solver& S) {
         CS(cusolverDnDgetrs(lanes[l].h, CUBLAS_OP_N, m, m, src, m, lb[l].ipiv, dst, m, info + 1));
     };
 
+    // destination of slot t of class c, operator o: the full inverse, or its
+    // two mirror halves (first (A + B)^-1 / 2, then (A - B)^-1 / 2)
+    auto slot_dst = [&](int o, int c, size_t t) -> double* {
+        const int sz = S.sl_size[c][t], idx = S.sl_idx[c][t];
+        if (S.zmir)
+            return sz == 1 ? S.S1h + (((size_t)o * 3 + c) * std::max(S.ns1, 1) + idx) * fz * fz / 2
+                           : S.S2h + (((size_t)o * 3 + c) * std::max(S.ns2, 1) + idx) * 2 * fz * fz;
+        return sz == 1 ? S.S1 + (((size_t)o * 3 + c) * std::max(S.ns1, 1) + idx) * fz * fz
+                       : S.S2 + (((size_t)o * 3 + c) * std::max(S.ns2, 1) + idx) * 4 * fz * fz;
+    };
     // phase 1: slot inverses of B_c (+) L_z - k^2 for every operator (Sec. 5:
     // only the shift depends on k).  Slot matrices up to kBatchedMax rows go
     // through one batched LU and inversion per size (cuBLAS getrf/getriBatched,
@@ -729,7 +764,7 @@ static void setup_solver(Solver& S) {
         }
         cublasSetStream(t_lanes.blas, st);
         for (int sz = 1; sz <= 2; ++sz) {
-            const int m = sz * fz;
+            const int m = S.zmir ? sz * fz / 2 : sz * fz;      // size of one inversion
             if (m > kBatchedMax) continue;
             std::vector<double*> src_p, dst_p;
             std::vector<std::array<int, 3>> items;
@@ -739,16 +774,25 @@ static void setup_solver(Solver& S) {
                     for (size_t t = 0; t < S.sl_size[c].size(); ++t)
                         if (S.sl_size[c][t] == sz) items.push_back({o, c, (int)t});
                 }
-            const int nb = (int)items.size();
+            const int per = S.zmir ? 2 : 1;                   // inversions per slot
+            const int nb = (int)items.size() * per;
             if (nb == 0) continue;
             double* work = S.dalloc<double>((size_t)nb * m * m, tmp);
-            for (int i = 0; i < nb; ++i) {
-                const int o = items[i][0], c = items[i][1], t = items[i][2], idx = S.sl_idx[c][t];
-                double* a = work + (size_t)i * m * m;
-                k_build_slot(a, dLz, fz, sz, al[c][t] - S.k2[o], be[c][t], st);
-                src_p.push_back(a);
-                dst_p.push_back(sz == 1 ? S.S1 + (((size_t)o * 3 + c) * std::max(S.ns1, 1) + idx) * fz * fz
-                                        : S.S2 + (((size_t)o * 3 + c) * std::max(S.ns2, 1) + idx) * 4 * fz * fz);
+            for (size_t it = 0; it < items.size(); ++it) {
+                const int o = items[it][0], c = items[it][1], t = items[it][2];
+                double* a = work + (size_t)it * per * m * m;
+                double* dst = slot_dst(o, c, t);
+                if (S.zmir) {
+                    k_build_slot_halves(a, dLz, fz, sz, al[c][t] - S.k2[o], be[c][t], st);
+                    src_p.push_back(a);
+                    src_p.push_back(a + (size_t)m * m);
+                    dst_p.push_back(dst);
+                    dst_p.push_back(dst + (size_t)m * m);
+                } else {
+                    k_build_slot(a, dLz, fz, sz, al[c][t] - S.k2[o], be[c][t], st);
+                    src_p.push_back(a);
+                    dst_p.push_back(dst);
+                }
             }
             double** d_src = S.dalloc<double*>((size_t)nb, tmp);
             double** d_dst = S.dalloc<double*>((size_t)nb, tmp);
@@ -775,40 +819,24 @@ static void setup_solver(Solver& S) {
             for (int c = 0; c < 3; ++c) {
                 if (S.slot_cls[c] != c) continue;          // shares another class's slots
                 for (size_t t = 0; t < S.sl_size[c].size(); ++t) {
-                    const int sz = S.sl_size[c][t], m = sz * fz, idx = S.sl_idx[c][t];
+                    const int sz = S.sl_size[c][t];
+                    const int m = S.zmir ? sz * fz / 2 : sz * fz;
                     if (m <= kBatchedMax) continue;       // done by the batched inversion
-                    const int l = next_lane++ % L;
-                    k_build_slot(lb[l].a, dLz, fz, sz, al[c][t] - S.k2[o], be[c][t], lanes[l].s);
-                    double* dst = sz == 1 ? S.S1 + (((size_t)o * 3 + c) * std::max(S.ns1, 1) + idx) * fz * fz
-                                          : S.S2 + (((size_t)o * 3 + c) * std::max(S.ns2, 1) + idx) * 4 * fz * fz;
-                    invert_on(l, lb[l].a, dst, m);
+                    double* dst = slot_dst(o, c, t);
+                    if (S.zmir) {
+                        // the two halves on two lanes (lane buffer a holds 2 m^2 >= both)
+                        const int l = next_lane++ % L;
+                        k_build_slot_halves(lb[l].a, dLz, fz, sz, al[c][t] - S.k2[o], be[c][t], lanes[l].s);
+                        invert_on(l, lb[l].a, dst, m);
+                        invert_on(l, lb[l].a + (size_t)m * m, dst + (size_t)m * m, m);
+                    } else {
+                        const int l = next_lane++ % L;
+                        k_build_slot(lb[l].a, dLz, fz, sz, al[c][t] - S.k2[o], be[c][t], lanes[l].s);
+                        invert_on(l, lb[l].a, dst, m);
+                    }
                 }
             }
         join();
-        // With uniform h_z (and the same Neumann condition at the bottom and
-        // the top) L_z commutes with the reversal of the z-nodes, and so does
-        // every slot inverse (L_z + s I)^-1 and its 2 x 2 block form: the slot
-        // products run in the mirror form (half the FLOPs).  The halves are
-        // taken from the computed inverses; the refinement step of every fast
-        // solve uses the exact operator, so their rounding-level asymmetry
-        // does not reach a result.
-        S.zmir = false;
-        if (fz % 2 == 0 && S.mirror_mode != 0) {
-            double diff = 0.0, amax = 0.0;
-            for (int i = 0; i < fz; ++i)
-                for (int j = 0; j < fz; ++j) {
-                    amax = std::max(amax, std::fabs(Lz[(size_t)i * fz + j]));
-                    diff = std::max(diff, std::fabs(Lz[(size_t)(fz - 1 - i) * fz + (fz - 1 - j)] - Lz[(size_t)i * fz + j]));
-                }
-            S.zmir = diff <= 1e-13 * amax;
-        }
-        if (S.zmir) {
-            const long long c1 = (long long)nop * 3 * std::max(S.ns1, 1), c2 = (long long)nop * 3 * std::max(S.ns2, 1);
-            S.S1h = S.dalloc<double>((size_t)c1 * fz * fz / 2, S.allocs);
-            S.S2h = S.dalloc<double>((size_t)c2 * 2 * fz * fz, S.allocs);
-            k_mirror_halves_nodes(S.S1h, S.S1, c1, fz, 1, st);
-            k_mirror_halves_nodes(S.S2h, S.S2, c2, fz, 2, st);
-        }
         phase("slot_inverses");
     }
 

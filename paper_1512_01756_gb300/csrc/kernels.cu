@@ -1635,6 +1635,39 @@ void k_build_slot(double* M, const double* Lz, int fz, int size, double shift, d
     count_launches(1);
 }
 
+// The two half-size matrices of a reversal-symmetric slot matrix M (uniform
+// h_z): with p the first half of the z-nodes of each f_z block and q = J p
+// their mirror images, M = [[A, B], [B, A]] in (p, q) order and
+// M^-1 = the mirror form with halves (A + B)^-1 / 2 and (A - B)^-1 / 2.
+// Writes 2 (A + B) at H and 2 (A - B) at H + h^2 (h = size fz / 2, row-major),
+// whose inverses are those halves.
+__global__ void build_slot_halves_kernel(double* __restrict__ H, const double* __restrict__ Lz, int fz, int size,
+                                         double shift, double beta) {
+    const int hb = fz / 2, h = size * hb;
+    const long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx >= (long long)h * h) return;
+    const int i = (int)(idx / h), j = (int)(idx - (long long)i * h);
+    const int bi = i / hb, zi = i - bi * hb;              // row p(i): block bi, node zi
+    const int bj = j / hb, zp = j - bj * hb, zq = fz - 1 - zp;   // columns p(j), q(j) in block bj
+    double vp = 0.0, vq = 0.0;
+    if (bi == bj) {
+        vp = Lz[(long long)zi * fz + zp] + (zi == zp ? shift : 0.0);
+        vq = Lz[(long long)zi * fz + zq] + (zi == zq ? shift : 0.0);
+    } else {
+        const double b = bi == 0 ? beta : -beta;
+        vp = zi == zp ? b : 0.0;
+        vq = zi == zq ? b : 0.0;
+    }
+    H[idx] = 2.0 * (vp + vq);
+    H[(long long)h * h + idx] = 2.0 * (vp - vq);
+}
+
+void k_build_slot_halves(double* H, const double* Lz, int fz, int size, double shift, double beta, cudaStream_t s) {
+    const long long h = (long long)size * fz / 2, tot = h * h;
+    build_slot_halves_kernel<<<(unsigned)((tot + 255) / 256), 256, 0, s>>>(H, Lz, fz, size, shift, beta);
+    count_launches(1);
+}
+
 // Unit right-hand sides for the Schur blocks: column j < fz is the west-face
 // node (a = 0, Z = j) of one strip, column j >= fz the east-face node (a = N).
 __global__ void unit_faces_kernel(double* __restrict__ U, int n, int fz) {
@@ -1894,30 +1927,6 @@ __global__ void mirror_halves_kernel(T* __restrict__ H, const T* __restrict__ Ma
 void k_mirror_halves(double* H, const double* Mat, int fz, int nb, cudaStream_t s) {
     const long long h = (long long)nb * fz / 2;
     mirror_halves_kernel<double><<<(unsigned)((h * h + 255) / 256), 256, 0, s>>>(H, Mat, fz, nb);
-    count_launches(1);
-}
-
-// count matrices of size m = nblk * fz (fz even) at stride m^2, z-reversal
-// inside each block: H[c] = [Hp; Hm] of size 2 (m/2)^2
-__global__ void mirror_halves_nodes_kernel(double* __restrict__ H, const double* __restrict__ Mat, long long count,
-                                           int fz, int nblk) {
-    const long long m = (long long)nblk * fz, h = m / 2, hb = fz / 2;
-    const long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    if (idx >= count * h * h) return;
-    const long long c = idx / (h * h), e = idx - c * h * h;
-    const long long i = e / h, j = e - i * h;
-    const long long pi = (i / hb) * fz + i % hb;
-    const long long pj = (j / hb) * fz + j % hb, qj = (j / hb) * fz + fz - 1 - j % hb;
-    const double* A = Mat + c * m * m;
-    const double x = A[pi * m + pj], y = A[pi * m + qj];
-    H[c * 2 * h * h + e] = 0.5 * (x + y);
-    H[c * 2 * h * h + h * h + e] = 0.5 * (x - y);
-}
-
-void k_mirror_halves_nodes(double* H, const double* Mat, long long count, int fz, int nblk, cudaStream_t s) {
-    const long long h = (long long)nblk * fz / 2, tot = count * h * h;
-    if (tot <= 0) return;
-    mirror_halves_nodes_kernel<<<(unsigned)((tot + 255) / 256), 256, 0, s>>>(H, Mat, count, fz, nblk);
     count_launches(1);
 }
 

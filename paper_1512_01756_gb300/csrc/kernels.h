@@ -186,7 +186,6 @@ void k_mirror_halves(double* H, const double* Mat, int fz, int nb, cudaStream_t 
 void k_mirror_halves_f(float* H, const float* Mat, int fz, int nb, cudaStream_t s);
 // Halves of count slot matrices (nblk blocks of fz values, fz even, stride
 // (nblk fz)^2) under the z-reversal inside each block: H[c] = [Hp; Hm].
-void k_mirror_halves_nodes(double* H, const double* Mat, long long count, int fz, int nblk, cudaStream_t s);
 // done[r] = active[r] ? 0 : 1 for r < R
 void k_invert_flags(int* done, const int* active, int R, cudaStream_t s);
 // K <- K - (K u) u^T (row-major d x d, w: d scratch): the projected coarse division
@@ -223,6 +222,7 @@ void k_strip_residual(const FssArgs& f, int R, const double* Ax3, const double* 
 void k_face_flux(const FssArgs& f, int R, const double* beta, const double* y, long long y_ld, double* bS,
                  long long b_ld, long long kp, cudaStream_t s);
 void k_build_slot(double* M, const double* Lz, int fz, int size, double shift, double beta, cudaStream_t s);
+void k_build_slot_halves(double* H, const double* Lz, int fz, int size, double shift, double beta, cudaStream_t s);
 void k_unit_faces(double* U, int n, int fz, cudaStream_t s);
 void k_g_from_solves(double* G, const double* Y, const double* beta, int n, int fz, int cls, cudaStream_t s);
 
