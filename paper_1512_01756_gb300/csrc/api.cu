@@ -310,28 +310,32 @@ static void fss_refined(Solver& S, const FssArgs& fa, int R, const double* in, l
     fss_run(S, fa, R, t3, ld, out, out_ld, nullptr, 0, t1, t2, tS1, tS2, true);
 }
 
-// Slot tiles of one class on a single strip for R right-hand sides of operator o.
-static std::vector<Tile> single_strip_slot_tiles(const Solver& S, int o, int c, int R, int sz, int bn) {
+// Slot tiles of one class on a single strip: operators o0 .. o0 + no - 1,
+// Rper right-hand sides each (operator o0 + q owns columns [q Rper, (q+1) Rper)).
+static std::vector<Tile> single_strip_slot_tiles(const Solver& S, int o0, int no, int c, int Rper, int sz, int bn) {
     std::vector<Tile> out;
     const int ns = std::max(sz == 1 ? S.ns1 : S.ns2, 1);
-    for (size_t t = 0; t < S.sl_size[c].size(); ++t) {
-        if (S.sl_size[c][t] != sz) continue;
-        for (int rr = 0; rr < R; rr += bn)
-            out.push_back(Tile{(o * 3 + S.slot_cls[c]) * ns + S.sl_idx[c][t], 0, 1, rr, std::min(bn, R - rr),
-                               (long long)S.sl_start[c][t] * S.g.fz});
-    }
+    for (int q = 0; q < no; ++q)
+        for (size_t t = 0; t < S.sl_size[c].size(); ++t) {
+            if (S.sl_size[c][t] != sz) continue;
+            for (int rr = 0; rr < Rper; rr += bn)
+                out.push_back(Tile{((o0 + q) * 3 + S.slot_cls[c]) * ns + S.sl_idx[c][t], 0, 1, q * Rper + rr,
+                                   std::min(bn, Rper - rr), (long long)S.sl_start[c][t] * S.g.fz});
+        }
     return out;
 }
 
-// A_c(k)^-1 of R strip vectors (one strip of class c, operator o), for setup.
-static void fss_single(Solver& S, int o, int c, int R, const double* in, double* out, double* t1, double* t2,
-                       std::vector<void*>& tmp) {
+// A_c(k)^-1 of strip vectors of class c for setup: Rper right-hand sides for
+// each of the operators o0 .. o0 + no - 1, all in one refined fast solve.
+static void fss_setup(Solver& S, int o0, int no, int c, int Rper, const double* in, double* out, double* t1,
+                      double* t2, std::vector<void*>& tmp) {
     FssArgs fa{S.g.n, S.g.fz, 1, S.d_cls3 + c};
+    const int R = no * Rper;
     TileSet ts[2];
     std::vector<Tile> tv[2][2];
     for (int sz = 1; sz <= 2; ++sz)
         for (int sh = 0; sh < 2; ++sh) {
-            tv[sz - 1][sh] = single_strip_slot_tiles(S, o, c, R, sz, gemm_tile_columns(sh));
+            tv[sz - 1][sh] = single_strip_slot_tiles(S, o0, no, c, Rper, sz, gemm_tile_columns(sh));
             const auto& v = tv[sz - 1][sh];
             ts[sz - 1].t[sh] = S.dalloc<Tile>(std::max<size_t>(v.size(), 1), tmp);
             ts[sz - 1].n[sh] = (int)v.size();
@@ -339,8 +343,10 @@ static void fss_single(Solver& S, int o, int c, int R, const double* in, double*
                 CK(cudaMemcpyAsync(ts[sz - 1].t[sh], v.data(), v.size() * sizeof(Tile), cudaMemcpyHostToDevice, S.stream));
         }
     const long long nfz = (long long)S.g.n * S.g.fz;
+    std::vector<double> k2h((size_t)R);
+    for (int r = 0; r < R; ++r) k2h[r] = S.k2[o0 + r / Rper];
     double* k2r = S.dalloc<double>((size_t)R, tmp);
-    k_fill(k2r, R, S.k2[o], S.stream);
+    upload(k2r, k2h, S.stream);
     double* t3 = S.dalloc<double>((size_t)R * nfz, tmp);
     fss_refined(S, fa, R, in, nfz, out, nfz, nullptr, 0, k2r, t1, t2, t3, ts[0], ts[1]);
     CK(cudaStreamSynchronize(S.stream));
@@ -713,7 +719,7 @@ static void setup_solver(Solver& S) {
         }
     }
     int n_inv = 0;
-    for (int c = 0; c < 3 && S.fss; ++c) n_inv += (S.zmir ? 2 : 1) * (int)S.sl_size[c].size();
+    for (int c = 0; c < 3 && S.fss; ++c) n_inv += (int)S.sl_size[c].size();
     n_inv = nop * (n_inv + S.nmc + 1);
     int* d_infos = S.dalloc<int>((size_t)2 * n_inv, tmp);
     CK(cudaMemsetAsync(d_infos, 0, sizeof(int) * 2 * n_inv, st));
@@ -764,8 +770,8 @@ static void setup_solver(Solver& S) {
         }
         cublasSetStream(t_lanes.blas, st);
         for (int sz = 1; sz <= 2; ++sz) {
-            const int m = S.zmir ? sz * fz / 2 : sz * fz;      // size of one inversion
-            if (m > kBatchedMax) continue;
+            const int m = sz * fz;
+            if (m > kBatchedMax || S.zmir) continue;
             std::vector<double*> src_p, dst_p;
             std::vector<std::array<int, 3>> items;
             for (int o = 0; o < nop; ++o)
@@ -774,25 +780,15 @@ static void setup_solver(Solver& S) {
                     for (size_t t = 0; t < S.sl_size[c].size(); ++t)
                         if (S.sl_size[c][t] == sz) items.push_back({o, c, (int)t});
                 }
-            const int per = S.zmir ? 2 : 1;                   // inversions per slot
-            const int nb = (int)items.size() * per;
+            const int nb = (int)items.size();
             if (nb == 0) continue;
             double* work = S.dalloc<double>((size_t)nb * m * m, tmp);
-            for (size_t it = 0; it < items.size(); ++it) {
-                const int o = items[it][0], c = items[it][1], t = items[it][2];
-                double* a = work + (size_t)it * per * m * m;
-                double* dst = slot_dst(o, c, t);
-                if (S.zmir) {
-                    k_build_slot_halves(a, dLz, fz, sz, al[c][t] - S.k2[o], be[c][t], st);
-                    src_p.push_back(a);
-                    src_p.push_back(a + (size_t)m * m);
-                    dst_p.push_back(dst);
-                    dst_p.push_back(dst + (size_t)m * m);
-                } else {
-                    k_build_slot(a, dLz, fz, sz, al[c][t] - S.k2[o], be[c][t], st);
-                    src_p.push_back(a);
-                    dst_p.push_back(dst);
-                }
+            for (int i = 0; i < nb; ++i) {
+                const int o = items[i][0], c = items[i][1], t = items[i][2];
+                double* a = work + (size_t)i * m * m;
+                k_build_slot(a, dLz, fz, sz, al[c][t] - S.k2[o], be[c][t], st);
+                src_p.push_back(a);
+                dst_p.push_back(slot_dst(o, c, t));
             }
             double** d_src = S.dalloc<double*>((size_t)nb, tmp);
             double** d_dst = S.dalloc<double*>((size_t)nb, tmp);
@@ -813,63 +809,104 @@ static void setup_solver(Solver& S) {
                 if (v != 0) throw Err{SMPM_EBREAKDOWN, "singular slot matrix (batched getrf info " + std::to_string(v) + ")"};
         }
     }
-    if (S.fss) {
+    if (S.fss && !S.zmir) {
         fork();
         for (int o = 0; o < nop; ++o)
             for (int c = 0; c < 3; ++c) {
                 if (S.slot_cls[c] != c) continue;          // shares another class's slots
                 for (size_t t = 0; t < S.sl_size[c].size(); ++t) {
-                    const int sz = S.sl_size[c][t];
-                    const int m = S.zmir ? sz * fz / 2 : sz * fz;
+                    const int sz = S.sl_size[c][t], m = sz * fz;
                     if (m <= kBatchedMax) continue;       // done by the batched inversion
-                    double* dst = slot_dst(o, c, t);
-                    if (S.zmir) {
-                        // the two halves on two lanes (lane buffer a holds 2 m^2 >= both)
-                        const int l = next_lane++ % L;
-                        k_build_slot_halves(lb[l].a, dLz, fz, sz, al[c][t] - S.k2[o], be[c][t], lanes[l].s);
-                        invert_on(l, lb[l].a, dst, m);
-                        invert_on(l, lb[l].a + (size_t)m * m, dst + (size_t)m * m, m);
-                    } else {
-                        const int l = next_lane++ % L;
-                        k_build_slot(lb[l].a, dLz, fz, sz, al[c][t] - S.k2[o], be[c][t], lanes[l].s);
-                        invert_on(l, lb[l].a, dst, m);
-                    }
+                    const int l = next_lane++ % L;
+                    k_build_slot(lb[l].a, dLz, fz, sz, al[c][t] - S.k2[o], be[c][t], lanes[l].s);
+                    invert_on(l, lb[l].a, slot_dst(o, c, t), m);
                 }
             }
         join();
-        phase("slot_inverses");
     }
+    if (S.fss && S.zmir) {
+        // mirror halves: every half of every slot and operator of one size
+        // inverted by one Gauss-Jordan launch (one CTA per matrix): the
+        // per-matrix cuSOLVER calls spent ~3 ms each in launch latency on
+        // matrices of 136-272 rows, two orders of magnitude above their FLOPs
+        for (int sz = 1; sz <= 2; ++sz) {
+            const int h = sz * fz / 2;
+            std::vector<const double*> src_p;
+            std::vector<double*> dst_p;
+            std::vector<std::array<int, 3>> items;
+            for (int o = 0; o < nop; ++o)
+                for (int c = 0; c < 3; ++c) {
+                    if (S.slot_cls[c] != c) continue;
+                    for (size_t t = 0; t < S.sl_size[c].size(); ++t)
+                        if (S.sl_size[c][t] == sz) items.push_back({o, c, (int)t});
+                }
+            const int nb = 2 * (int)items.size();
+            if (nb == 0) continue;
+            double* work = S.dalloc<double>((size_t)nb * h * h, tmp);
+            for (size_t it = 0; it < items.size(); ++it) {
+                const int o = items[it][0], c = items[it][1], t = items[it][2];
+                double* a = work + (size_t)2 * it * h * h;
+                double* d = slot_dst(o, c, t);
+                k_build_slot_halves(a, dLz, fz, sz, al[c][t] - S.k2[o], be[c][t], st);
+                src_p.push_back(a);
+                src_p.push_back(a + (size_t)h * h);
+                dst_p.push_back(d);
+                dst_p.push_back(d + (size_t)h * h);
+            }
+            const double** d_src = S.dalloc<const double*>((size_t)nb, tmp);
+            double** d_dst = S.dalloc<double*>((size_t)nb, tmp);
+            int* inf = S.dalloc<int>((size_t)nb, tmp);
+            CK(cudaMemcpyAsync(d_src, src_p.data(), nb * sizeof(double*), cudaMemcpyHostToDevice, st));
+            CK(cudaMemcpyAsync(d_dst, dst_p.data(), nb * sizeof(double*), cudaMemcpyHostToDevice, st));
+            k_gj_inverse(d_src, d_dst, h, nb, inf, st);
+            CK(cudaGetLastError());
+            std::vector<int> h_inf((size_t)nb);
+            CK(cudaMemcpyAsync(h_inf.data(), inf, h_inf.size() * sizeof(int), cudaMemcpyDeviceToHost, st));
+            CK(cudaStreamSynchronize(st));
+            for (int v : h_inf)
+                if (v != 0) throw Err{SMPM_EBREAKDOWN, "singular slot matrix half (Gauss-Jordan pivot " + std::to_string(v) + ")"};
+        }
+    }
+    if (S.fss) phase("slot_inverses");
 
     // phase 2: G_c = B A_c^-1 E_c and the coarse row sums, per operator
     double *U = nullptr, *Y = nullptr, *T1 = nullptr, *T2 = nullptr;
+    // fast solves of the 2 fz unit face vectors of one strip, for up to
+    // kGOps operators in one refined solve per class
+    constexpr int kGOps = 8;
+    const int gops = std::min(nop, kGOps);
     if (S.fss) {
-        U = S.dalloc<double>((size_t)f2 * nfz, tmp);
-        Y = S.dalloc<double>((size_t)f2 * nfz, tmp);
-        T1 = S.dalloc<double>((size_t)f2 * nfz, tmp);
-        T2 = S.dalloc<double>((size_t)f2 * nfz, tmp);
-    }
-    for (int o = 0; o < nop; ++o) {
-        const double k2 = S.k2[o];
-        double* G = S.G + (size_t)o * 3 * S.sG;
-        if (S.fss) {
-            // from fast solves of the 2 fz unit face vectors of one strip; the
-            // east boundary class of a mirror-symmetric grid is the west one
-            // with its two faces swapped
+        U = S.dalloc<double>((size_t)gops * f2 * nfz, tmp);
+        Y = S.dalloc<double>((size_t)gops * f2 * nfz, tmp);
+        T1 = S.dalloc<double>((size_t)gops * f2 * nfz, tmp);
+        T2 = S.dalloc<double>((size_t)gops * f2 * nfz, tmp);
+        for (int q = 0; q < gops; ++q) k_unit_faces(U + (size_t)q * f2 * nfz, n, fz, st);
+        for (int o0 = 0; o0 < nop; o0 += gops) {
+            const int no = std::min(gops, nop - o0);
+            // the east boundary class of a mirror-symmetric grid is the west
+            // one with its two faces swapped (after both are built)
             for (int c = 0; c < 3; ++c) {
                 if (c == 1 && mx < 3) {
-                    k_fill(G + c * S.sG, S.sG, 0.0, st);
+                    for (int o = o0; o < o0 + no; ++o) k_fill(S.G + ((size_t)o * 3 + c) * S.sG, S.sG, 0.0, st);
                     continue;
                 }
-                if (S.slot_cls[c] != c) {
-                    k_mirror_blocks(G + c * S.sG, G + S.slot_cls[c] * S.sG, fz, 2, st);
-                    continue;
-                }
-                k_unit_faces(U, n, fz, st);
-                fss_single(S, o, c, f2, U, Y, T1, T2, tmp);
-                k_g_from_solves(G + c * S.sG, Y, S.d_beta + (size_t)c * 2 * n, n, fz, c, st);
+                if (S.slot_cls[c] != c) continue;
+                fss_setup(S, o0, no, c, f2, U, Y, T1, T2, tmp);
+                for (int q = 0; q < no; ++q)
+                    k_g_from_solves(S.G + ((size_t)(o0 + q) * 3 + c) * S.sG, Y + (size_t)q * f2 * nfz,
+                                    S.d_beta + (size_t)c * 2 * n, n, fz, c, st);
             }
-            continue;
+            for (int o = o0; o < o0 + no; ++o)
+                for (int c = 0; c < 3; ++c)
+                    if (S.slot_cls[c] != c && !(c == 1 && mx < 3)) {
+                        double* G = S.G + (size_t)o * 3 * S.sG;
+                        k_mirror_blocks(G + c * S.sG, G + S.slot_cls[c] * S.sG, fz, 2, st);
+                    }
         }
+    }
+    for (int o = 0; o < nop && !S.fss; ++o) {
+        const double k2 = S.k2[o];
+        double* G = S.G + (size_t)o * 3 * S.sG;
         for (int c = 0; c < 3; ++c) {
             double* Ainv = S.Ainv + (size_t)o * 3 * S.sA;
             double* W = S.W + (size_t)o * 3 * S.sW;
@@ -1208,7 +1245,8 @@ static void setup_solver(Solver& S) {
     S.free_list(tmp);
     S.setup_ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
     if (trace)
-        fprintf(stderr, "smpm setup %dx%d p%d nop=%d fss=%d total=%.2f:%s\n", g.mx, g.mz, g.N, S.nop, (int)S.fss,
+        fprintf(stderr, "smpm setup %dx%d p%d nop=%d fss=%d zmir=%d slots(1x1, 2x2 per class)=%d,%d total=%.2f:%s\n",
+                g.mx, g.mz, g.N, S.nop, (int)S.fss, (int)S.zmir, S.ns1, S.ns2,
                 S.setup_ms, trace_line.c_str());
 }
 

@@ -10,6 +10,7 @@
 // FP64 arithmetic is bound by the DFMA pipe on this part, so the dense applies
 // are register-tiled SIMT GEMMs over tiles that share one class matrix; the
 // vector kernels are chunked streams over the face vectors.
+#include <mutex>
 #include <algorithm>
 #include <atomic>
 #include <cmath>
@@ -1632,6 +1633,123 @@ __global__ void build_slot_kernel(double* __restrict__ M, const double* __restri
 void k_build_slot(double* M, const double* Lz, int fz, int size, double shift, double beta, cudaStream_t s) {
     const long long tot = (long long)size * fz * size * fz;
     build_slot_kernel<<<(unsigned)((tot + 255) / 256), 256, 0, s>>>(M, Lz, fz, size, shift, beta);
+    count_launches(1);
+}
+
+// Batched inversion by Gauss-Jordan elimination with partial pivoting, one
+// CTA per matrix (row-major n x n): the pivot row is scaled in place with its
+// pivot entry replaced by 1 (so that column k of the other rows becomes the
+// inverse's column), every other row is eliminated, and the column order is
+// restored at the end by undoing the row interchanges in reverse.  SM: the
+// working matrix in shared memory (n <= kGjSmemMax), else in dst (global
+// memory, L2-resident while the CTA works on it).  info[b] = k + 1 if the
+// pivot of step k is zero or not finite (dst then holds no inverse).
+constexpr int GJ_THREADS = 256;
+
+template <bool SM>
+__global__ void __launch_bounds__(GJ_THREADS) gj_inverse_kernel(const double* const* __restrict__ src,
+                                                               double* const* __restrict__ dst, int n,
+                                                               int* __restrict__ info) {
+    extern __shared__ double gj_sh[];
+    __shared__ double red_v[GJ_THREADS / 32];
+    __shared__ int red_i[GJ_THREADS / 32];
+    __shared__ int s_p, s_fail;
+    const int b = blockIdx.x, tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    constexpr int NW = GJ_THREADS / 32;
+    double* W = SM ? gj_sh : dst[b];
+    double* col = SM ? gj_sh + (size_t)n * n : gj_sh;
+    int* piv = reinterpret_cast<int*>(col + n);
+    const double* S = src[b];
+    for (long long idx = tid; idx < (long long)n * n; idx += GJ_THREADS) W[idx] = S[idx];
+    if (tid == 0) s_fail = 0;
+    __syncthreads();
+    for (int k = 0; k < n; ++k) {
+        // pivot: the largest |W[i][k]|, i >= k (smallest i among equals)
+        double best = -1.0;
+        int bi = n;
+        for (int i = k + tid; i < n; i += GJ_THREADS) {
+            const double v = fabs(W[(long long)i * n + k]);
+            if (v > best) { best = v; bi = i; }
+        }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            const double ov = __shfl_xor_sync(0xffffffffu, best, o);
+            const int oi = __shfl_xor_sync(0xffffffffu, bi, o);
+            if (ov > best || (ov == best && oi < bi)) { best = ov; bi = oi; }
+        }
+        if (lane == 0) { red_v[warp] = best; red_i[warp] = bi; }
+        __syncthreads();
+        if (tid == 0) {
+            double bv = red_v[0];
+            int bx = red_i[0];
+            for (int w = 1; w < NW; ++w)
+                if (red_v[w] > bv || (red_v[w] == bv && red_i[w] < bx)) { bv = red_v[w]; bx = red_i[w]; }
+            s_p = bx;
+            if (!(bv > 0.0) || !isfinite(bv) || bx >= n) s_fail = k + 1;
+        }
+        __syncthreads();
+        if (s_fail) break;
+        const int p = s_p;
+        if (tid == 0) piv[k] = p;
+        if (p != k)
+            for (int j = tid; j < n; j += GJ_THREADS) {
+                const double t = W[(long long)k * n + j];
+                W[(long long)k * n + j] = W[(long long)p * n + j];
+                W[(long long)p * n + j] = t;
+            }
+        __syncthreads();
+        const double pinv = 1.0 / W[(long long)k * n + k];
+        for (int i = tid; i < n; i += GJ_THREADS) col[i] = W[(long long)i * n + k];
+        __syncthreads();
+        for (int j = tid; j < n; j += GJ_THREADS)
+            W[(long long)k * n + j] = (j == k ? 1.0 : W[(long long)k * n + j]) * pinv;
+        __syncthreads();
+        for (int i = warp; i < n; i += NW) {
+            if (i == k) continue;
+            const double f = col[i];
+            double* Wi = W + (long long)i * n;
+            const double* Wk = W + (long long)k * n;
+            for (int j = lane; j < n; j += 32) Wi[j] = (j == k) ? -Wk[k] * f : fma(-Wk[j], f, Wi[j]);
+        }
+        __syncthreads();
+    }
+    if (!s_fail) {
+        for (int k = n - 1; k >= 0; --k) {
+            const int p = piv[k];
+            if (p != k)
+                for (int i = tid; i < n; i += GJ_THREADS) {
+                    const double t = W[(long long)i * n + k];
+                    W[(long long)i * n + k] = W[(long long)i * n + p];
+                    W[(long long)i * n + p] = t;
+                }
+            __syncthreads();
+        }
+        if (SM) {
+            double* D = dst[b];
+            for (long long idx = tid; idx < (long long)n * n; idx += GJ_THREADS) D[idx] = W[idx];
+        }
+    }
+    if (tid == 0) info[b] = s_fail;
+}
+
+int gj_smem_max() { return 158; }
+
+void k_gj_inverse(const double* const* src, double* const* dst, int n, int count, int* info, cudaStream_t s) {
+    if (count <= 0) return;
+    const auto smem_of = [](int m) {
+        return (size_t)m * m * sizeof(double) + (size_t)m * sizeof(double) + (size_t)m * sizeof(int);
+    };
+    if (n <= gj_smem_max()) {
+        static std::once_flag once;   // setups on several host threads
+        std::call_once(once, [&] {
+            cudaFuncSetAttribute(gj_inverse_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)smem_of(gj_smem_max()));
+        });
+        gj_inverse_kernel<true><<<count, GJ_THREADS, smem_of(n), s>>>(src, dst, n, info);
+    } else {
+        const size_t sh = (size_t)n * sizeof(double) + (size_t)n * sizeof(int);
+        gj_inverse_kernel<false><<<count, GJ_THREADS, sh, s>>>(src, dst, n, info);
+    }
     count_launches(1);
 }
 

@@ -223,6 +223,11 @@ void k_face_flux(const FssArgs& f, int R, const double* beta, const double* y, l
                  long long b_ld, long long kp, cudaStream_t s);
 void k_build_slot(double* M, const double* Lz, int fz, int size, double shift, double beta, cudaStream_t s);
 void k_build_slot_halves(double* H, const double* Lz, int fz, int size, double shift, double beta, cudaStream_t s);
+// Batched Gauss-Jordan inversion with partial pivoting, one CTA per matrix
+// (row-major n x n, src and dst device arrays of count pointers; info[b] != 0:
+// zero or non-finite pivot).  Shared memory up to n = gj_smem_max().
+void k_gj_inverse(const double* const* src, double* const* dst, int n, int count, int* info, cudaStream_t s);
+int gj_smem_max();
 void k_unit_faces(double* U, int n, int fz, cudaStream_t s);
 void k_g_from_solves(double* G, const double* Y, const double* beta, int n, int fz, int cls, cudaStream_t s);
 
