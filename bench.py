@@ -804,14 +804,18 @@ def run_serve(args):
             _served_pass(srv, reqs[:Pk], lambda i: view(Fd, i), lambda i: view(Ub, i))
             torch.cuda.synchronize()
         srv.close()
-        from torch.autograd import DeviceType
+        # the raw activity records (kernels, copies, sets) from the exported trace
         tot, cnt = {}, {}
-        for ev in prof_k.events():
-            if ev.device_type != DeviceType.CUDA:       # device activity only (kernels, copies, sets)
+        with tempfile.TemporaryDirectory() as td:
+            path = os.path.join(td, "trace.json")
+            prof_k.export_chrome_trace(path)
+            with open(path) as fh:
+                trace = json.load(fh)
+        for ev in trace.get("traceEvents", []):
+            if ev.get("cat") not in ("kernel", "gpu_memcpy", "gpu_memset") or "dur" not in ev:
                 continue
-            dt = ev.time_range.elapsed_us()
-            name = ev.name.split("(")[0].replace("void ", "")
-            tot[name] = tot.get(name, 0.0) + dt * 1e-3
+            name = ev.get("name", "?").split("(")[0].replace("void ", "")
+            tot[name] = tot.get(name, 0.0) + float(ev["dur"]) * 1e-3
             cnt[name] = cnt.get(name, 0) + 1
         T = sum(tot.values())
         top = sorted(tot.items(), key=lambda kv: -kv[1])[:25]

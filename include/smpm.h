@@ -329,6 +329,20 @@ int smpm_server_destroy(smpm_server_t srv);
  * null argument, nop < 1 or nrhs < 1.  Host arithmetic only (no GPU call). */
 int smpm_request_footprint(const smpm_grid* grid, int nop, int nrhs, long long* bytes);
 
+/* Residual history of right-hand side `rhs` of the handle's last solve
+ * (tracing; Sec. 4 reports convergence as the relative residual per
+ * iteration).  kind 0: after every Arnoldi step of every restart cycle, the
+ * GMRES residual estimate |g_{j+1}| / ||b_S|| from the Givens rotations (of
+ * the deflated, preconditioned cycle system; written on the device by the
+ * normalisation kernel, outer iteration of the nested form); kind 1: at every
+ * restart-cycle start while the right-hand side was running, the recomputed
+ * true residual ||S x_S - b_S|| / ||b_S||.  Writes min(n, available) values
+ * to out (host memory) and the number available to *count; n = 0 queries the
+ * count (out may then be NULL).  SMPM_EINVAL for a null handle or count, rhs
+ * outside the last solve, a bad kind, n < 0 or out NULL with n > 0.  Valid
+ * until the next solve on the handle. */
+int smpm_residual_history(smpm_handle h, int rhs, int kind, int n, double* out, int* count);
+
 /* Message of the calling thread's last failure ("" if none). */
 const char* smpm_last_error(void);
 

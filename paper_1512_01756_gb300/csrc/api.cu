@@ -134,8 +134,16 @@ struct Solver {
         TileSet tGb, tGm, tMb, tMm;       // boundary-class / mirror-form tiles
         double *fs1 = nullptr, *fs2 = nullptr, *fs3 = nullptr, *k2r = nullptr;
         double* Zb = nullptr;             // FGMRES preconditioned vectors [R][m][ld] (precision 1)
+        double* hist = nullptr;           // [R][max_iter + 1] Givens residual estimates per Arnoldi step
+        int* hist_base = nullptr;         // [R] steps before the current cycle
         std::vector<void*> allocs;
     } wk;
+    // residual history of the last solve: per right-hand side, the relative
+    // true residual at every cycle start (host), and the number of Arnoldi
+    // steps whose Givens estimates are in wk.hist
+    std::vector<std::vector<double>> hist_true;
+    std::vector<int> hist_steps;
+    int hist_R = 0;
     std::vector<int> cur_ops;               // op layout the tiles were built for
     std::vector<void*> allocs;
     long long bytes = 0, wk_bytes = 0;
@@ -411,6 +419,7 @@ struct LaneGuard {
 };
 
 static void setup_solver(Solver& S) {
+    NvtxRange nvtx_range("smpm setup");
     auto t0 = std::chrono::steady_clock::now();
     // SMPM_TRACE_SETUP=1: per-phase wall times of the setup on stderr
     const bool trace = std::getenv("SMPM_TRACE_SETUP") != nullptr;
@@ -1334,6 +1343,8 @@ static void ensure_workspace(Solver& S, int R) {
     w.active = S.dalloc<int>(R, L);
     w.done = S.dalloc<int>(R, L);
     w.nit = S.dalloc<int>(R, L);
+    w.hist = S.dalloc<double>((size_t)R * (S.max_iter + 1), L);
+    w.hist_base = S.dalloc<int>(R, L);
     w.flags = S.dalloc<int>(R, L);
     w.op = S.dalloc<int>(R, L);
     w.gauge = S.dalloc<int>(R, L);
@@ -1771,6 +1782,7 @@ static void bj_apply(Solver& S, const double* in, long long in_rs, long long in_
 
 static int solve_impl(Solver& S, const std::vector<int>& ops, const double* f, const double* gb, double tol,
                       double* u, smpm_stats* st, const double* u0 = nullptr) {
+    NvtxRange nvtx_range("smpm solve");
     auto t0 = std::chrono::steady_clock::now();
     const int R = (int)ops.size();
     if (R <= 0) throw Err{SMPM_EINVAL, "nrhs must be positive"};
@@ -1877,6 +1889,7 @@ static int solve_impl(Solver& S, const std::vector<int>& ops, const double* f, c
     ka.active = w.active; ka.done = w.done; ka.nit = w.nit; ka.target = w.target;
     ka.bnorm = w.bnorm; ka.rnorm = w.rnorm; ka.flags = w.flags;
     ka.grp = S.krylov == 1 ? R : 1;
+    ka.hist = w.hist; ka.hist_base = w.hist_base; ka.hist_stride = S.max_iter + 1;
 
     // Nested mixed-precision form (precision 2): the outer flexible GMRES runs
     // on S itself (no deflation: K = null makes every coarse coefficient zero)
@@ -1891,6 +1904,7 @@ static int solve_impl(Solver& S, const std::vector<int>& ops, const double* f, c
         ki.active = w.activei; ki.done = w.donei; ki.nit = w.niti; ki.target = w.targeti;
         ki.bnorm = w.bnormi; ki.rnorm = w.rnormi; ki.flags = w.flagsi;
         ki.f32 = std::getenv("SMPM_INNER_FP64_ARNOLDI") ? 0 : 1;
+        ki.hist = nullptr;                       // the history is the outer iteration's
         ka.K = nullptr;
     }
 
@@ -1976,6 +1990,12 @@ static int solve_impl(Solver& S, const std::vector<int>& ops, const double* f, c
     // of running to max_iter.
     std::vector<double> prev_rel(R, -1.0), h_rn(R), h_bn(R);
     std::vector<int> stall(R, 0);
+    // residual history: the true residual at every cycle start of a
+    // right-hand side still running, and the Arnoldi steps taken so far
+    // (each step's Givens estimate is written by the normalisation kernel)
+    std::vector<int> h_base(R, 0), was_done(R, 0);
+    S.hist_true.assign(R, std::vector<double>());
+    S.hist_R = 0;
     const int one_i = 1, zero_i = 0;
     bool stagnated = false;
     int total_it = 0, cycles = 0, status = SMPM_OK;
@@ -2042,6 +2062,10 @@ static int solve_impl(Solver& S, const std::vector<int>& ops, const double* f, c
         CK(cudaMemcpyAsync(h_rn.data(), w.rnorm, R * sizeof(double), cudaMemcpyDeviceToHost, st_));
         CK(cudaMemcpyAsync(h_bn.data(), w.bnorm, R * sizeof(double), cudaMemcpyDeviceToHost, st_));
         CK(cudaStreamSynchronize(st_));
+        for (int r = 0; r < R; ++r) {
+            if (!was_done[r]) S.hist_true[r].push_back(h_bn[r] > 0.0 ? h_rn[r] / h_bn[r] : 0.0);
+            was_done[r] = h_done[r];
+        }
         if (trace) {
             fprintf(stderr, "smpm solve trace: cycle %d it %d", cycles, total_it);
             for (int r = 0; r < R; ++r) fprintf(stderr, " rel[%d] %.3e", r, h_bn[r] > 0 ? h_rn[r] / h_bn[r] : 0.0);
@@ -2098,6 +2122,7 @@ static int solve_impl(Solver& S, const std::vector<int>& ops, const double* f, c
         if (all) break;
         if (total_it >= S.max_iter) { status = SMPM_ENOCONV; break; }
         const int last_allowed = std::min(m, S.max_iter - total_it);
+        CK(cudaMemcpyAsync(w.hist_base, h_base.data(), R * sizeof(int), cudaMemcpyHostToDevice, st_));
         int j = 0;
         const bool mixed = S.precision >= 1;      // flexible: the preconditioned vectors are kept
         // (the nested form's steps carry whole inner solves; they run uncaptured)
@@ -2268,10 +2293,13 @@ static int solve_impl(Solver& S, const std::vector<int>& ops, const double* f, c
         CK(cudaStreamSynchronize(st_));
         int mx_it = 0;
         for (int r = 0; r < R; ++r) mx_it = std::max(mx_it, h_nit[r]);
+        for (int r = 0; r < R; ++r) h_base[r] = std::min(h_base[r] + h_nit[r], S.max_iter);
         total_it += std::max(mx_it, 1);
         ++cycles;
         first = false;
     }
+    S.hist_steps = h_base;
+    S.hist_R = R;
     phase("cycles");
     // recovery: u = A^-1 (b - E x_S)  (Alg. seq step 9)
     if (S.fss) {
@@ -2710,6 +2738,31 @@ int smpm_last_residuals(smpm_handle h, int n, double* out) {
         const Solver& S = *(Solver*)h;
         if (n > (int)S.last_res.size()) throw Err{SMPM_EINVAL, "more values requested than the last solve had"};
         for (int i = 0; i < n; ++i) out[i] = S.last_res[i];
+        return SMPM_OK;
+    });
+}
+
+int smpm_residual_history(smpm_handle h, int rhs, int kind, int n, double* out, int* count) {
+    return guarded([&] {
+        if (!h || !count) throw Err{SMPM_EINVAL, "null argument"};
+        Solver& S = *(Solver*)h;
+        if (rhs < 0 || rhs >= S.hist_R) throw Err{SMPM_EINVAL, "rhs out of range of the last solve"};
+        if (kind != 0 && kind != 1) throw Err{SMPM_EINVAL, "kind must be 0 (per Arnoldi step) or 1 (per cycle)"};
+        if (n < 0 || (n > 0 && !out)) throw Err{SMPM_EINVAL, "n must be >= 0 and out non-null when n > 0"};
+        if (kind == 1) {
+            const auto& v = S.hist_true[rhs];
+            *count = (int)v.size();
+            std::copy(v.begin(), v.begin() + std::min<size_t>(n, v.size()), out);
+            return SMPM_OK;
+        }
+        const int steps = S.hist_steps[rhs];
+        *count = steps;
+        const int k = std::min(n, steps);
+        if (k > 0) {
+            CK(cudaMemcpyAsync(out, S.wk.hist + (size_t)rhs * (S.max_iter + 1) + 1, sizeof(double) * k,
+                               cudaMemcpyDeviceToHost, S.stream));
+            CK(cudaStreamSynchronize(S.stream));
+        }
         return SMPM_OK;
     });
 }

@@ -679,6 +679,10 @@ __device__ __forceinline__ void normalize_body(const KArgs& a, int j, int last_a
         g[j + 1] = -s * g[j];
         g[j] = c * g[j];
         a.nit[r] = j + 1;
+        if (a.hist) {
+            const int k = a.hist_base[r] + j + 1;
+            if (k < a.hist_stride) a.hist[(long long)r * a.hist_stride + k] = fabs(g[j + 1]) / a.bnorm[r];
+        }
         const bool nonfinite = !isfinite(g[j + 1]) || !isfinite(rho);
         if (nonfinite || !(rho > 0.0)) a.flags[r] |= 1;
         if (nonfinite || !(rho > 0.0) || fabs(g[j + 1]) <= a.target[r] || j + 1 >= last_allowed || bad)

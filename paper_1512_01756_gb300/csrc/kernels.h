@@ -56,6 +56,11 @@ struct KArgs {
     // vectors (the inner solve of the nested mixed-precision form, which only
     // has to reach 1e-4 and whose Arnoldi work is bound by the FP64 pipe)
     int f32;
+    // residual history (null: off): hist[r * hist_stride + hist_base[r] + j + 1]
+    // = |Givens residual| / ||b_S|| after Arnoldi step j of the current cycle
+    double* hist;
+    const int* hist_base;
+    int hist_stride;
 };
 
 void k_deflate_sum(const KArgs& a, const double* v, const double* vsub, cudaStream_t s);

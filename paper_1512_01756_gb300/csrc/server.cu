@@ -38,6 +38,7 @@
 #include <vector>
 
 #include "../../include/smpm.h"
+#include "smpm_internal.h"
 
 namespace smpm {
 void set_last_error(const std::string& msg);
@@ -154,6 +155,7 @@ struct Server {
                     cv.wait(lk);
                 }
             }
+            smpm::NvtxRange nvtx_range("smpm served batch");
             // order the batch by k^2 so that operator indices are non-decreasing
             std::stable_sort(batch.begin(), batch.end(), [](const Request* a, const Request* b) { return a->k2 < b->k2; });
             std::vector<double> k2s;

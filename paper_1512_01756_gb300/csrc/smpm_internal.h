@@ -4,6 +4,8 @@
 
 #include <cuda_runtime.h>
 
+#include <nvtx3/nvToolsExt.h>
+
 #include <cstdint>
 #include <string>
 #include <vector>
@@ -11,6 +13,15 @@
 #include "../../include/smpm.h"
 
 namespace smpm {
+
+// NVTX range for the lifetime of a scope (tracing: setups, solves and served
+// batches show as named ranges in a profiler timeline; a no-op without one)
+struct NvtxRange {
+    explicit NvtxRange(const char* name) { nvtxRangePushA(name); }
+    ~NvtxRange() { nvtxRangePop(); }
+    NvtxRange(const NvtxRange&) = delete;
+    NvtxRange& operator=(const NvtxRange&) = delete;
+};
 
 // ---------------------------------------------------------------------------
 // Host side (plain C++, FP64)

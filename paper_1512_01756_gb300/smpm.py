@@ -22,7 +22,7 @@ EXPORTS = ["smpm_setup", "smpm_solve", "smpm_solve_batch", "smpm_solve_guess", "
            "smpm_sizes", "smpm_node_coords", "smpm_grid_coords", "smpm_null_vectors", "smpm_set_stream", "smpm_device_bytes", "smpm_release", "smpm_probe_fp64",
            "smpm_profile", "smpm_profile_read", "smpm_profile_split", "smpm_kernel_launches", "smpm_apply", "smpm_last_residuals", "smpm_apply_deflation_noalloc",
            "smpm_server_create", "smpm_submit", "smpm_poll", "smpm_server_destroy", "smpm_request_footprint",
-           "smpm_last_error"]
+           "smpm_residual_history", "smpm_last_error"]
 
 
 class Grid(ctypes.Structure):
@@ -95,6 +95,7 @@ def load():
                                 ctypes.POINTER(ctypes.c_ulonglong)]
     lib.smpm_poll.argtypes = [H, ctypes.c_ulonglong, ctypes.POINTER(Stats)]
     lib.smpm_server_destroy.argtypes = [H]
+    lib.smpm_residual_history.argtypes = [H, ctypes.c_int, ctypes.c_int, ctypes.c_int, P, ctypes.POINTER(ctypes.c_int)]
     lib.smpm_request_footprint.argtypes = [ctypes.POINTER(Grid), ctypes.c_int, ctypes.c_int,
                                            ctypes.POINTER(ctypes.c_longlong)]
     lib.smpm_kernel_launches.argtypes = []
@@ -203,6 +204,17 @@ class Solver:
         _check(load().smpm_solve_multi(self._h, len(ops), ops.ctypes.data_as(ctypes.c_void_p), _ptr(f), _ptr(g),
                                        float(tol), _ptr(u), ctypes.byref(st)))
         return st
+
+    def residual_history(self, rhs=0, kind=0):
+        """Residual history of right-hand side rhs of the last solve: kind 0 the
+        Givens estimate after every Arnoldi step, kind 1 the true residual at
+        every restart-cycle start (relative to ||b_S||)."""
+        cnt = ctypes.c_int()
+        _check(load().smpm_residual_history(self._h, int(rhs), int(kind), 0, None, ctypes.byref(cnt)))
+        out = np.empty(cnt.value)
+        if cnt.value:
+            _check(load().smpm_residual_history(self._h, int(rhs), int(kind), cnt.value, _ptr(out), ctypes.byref(cnt)))
+        return out
 
     def last_residuals(self, n):
         out = np.empty(n)
