@@ -78,8 +78,6 @@ def parse():
     p.add_argument("--cpu-seconds", type=float, default=20.0, help="serve: oracle time budget of the cpu_baseline leg")
     p.add_argument("--profiled-requests", type=int, default=300,
                    help="serve: requests re-run with the dense-product profile on (roofline)")
-    p.add_argument("--kernel-trace", type=int, default=0,
-                   help="serve: requests re-run under a CUDA activity trace (device time per kernel; 0 = off)")
     p.add_argument("--mixed-rhs", type=int, default=16, help="mixed: right-hand sides per step")
     p.add_argument("--workers", type=int, default=4, help="serve: server worker threads (one stream each)")
     p.add_argument("--max-batch", type=int, default=16, help="serve: requests per batch at most")
@@ -792,36 +790,6 @@ def run_serve(args):
                                   "frac": ach32 / FP32_SIMT_TFLOPS if ach32 else None, "launches": fp32["launches"],
                                   "peak_source": "152 SMs x 128 FP32 lanes x 2 FLOP x 2.07 GHz"}}
 
-    # 6. optional: device time per kernel of the served mix from the CUDA
-    # activity trace (CUPTI through torch.profiler, every stream and thread),
-    # the first requests re-served once more
-    shares = None
-    if args.kernel_trace > 0:
-        from torch.profiler import profile, ProfilerActivity
-        Pk = min(N, args.kernel_trace)
-        srv = smpm.Server(**srv_args)
-        with profile(activities=[ProfilerActivity.CUDA]) as prof_k:
-            _served_pass(srv, reqs[:Pk], lambda i: view(Fd, i), lambda i: view(Ub, i))
-            torch.cuda.synchronize()
-        srv.close()
-        # the raw activity records (kernels, copies, sets) from the exported trace
-        tot, cnt = {}, {}
-        with tempfile.TemporaryDirectory() as td:
-            path = os.path.join(td, "trace.json")
-            prof_k.export_chrome_trace(path)
-            with open(path) as fh:
-                trace = json.load(fh)
-        for ev in trace.get("traceEvents", []):
-            if ev.get("cat") not in ("kernel", "gpu_memcpy", "gpu_memset") or "dur" not in ev:
-                continue
-            name = ev.get("name", "?").split("(")[0].replace("void ", "")
-            tot[name] = tot.get(name, 0.0) + float(ev["dur"]) * 1e-3
-            cnt[name] = cnt.get(name, 0) + 1
-        T = sum(tot.values())
-        top = sorted(tot.items(), key=lambda kv: -kv[1])[:25]
-        shares = {"requests": Pk, "total_device_ms": T, "source": "CUPTI kernel activity via torch.profiler",
-                  "kernels": [{"name": k, "launches": cnt[k], "ms": v, "share": v / T} for k, v in top]}
-
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         n_o, secs, cores, biggest = oracle_serve_sample(reqs, args.cpu_seconds)
@@ -861,8 +829,6 @@ def run_serve(args):
             "gpu_launches": launches, "roofline": roofline, "cpu_baseline": cpu, "clocks": clk,
             "latency": "completion - arrival, operator setup included",
             "timing": "CUDA events on the launching stream around each pass, device synchronised on both sides"}
-    if shares is not None:
-        line["kernel_shares"] = shares
     if rank == 0 and not args.no_secondary:
         line["secondary_poisson2d"] = poisson2d_summary(args, smpm, dev, stream)
     if rank == 0:

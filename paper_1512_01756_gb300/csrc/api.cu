@@ -728,7 +728,7 @@ static void setup_solver(Solver& S) {
         }
     }
     int n_inv = 0;
-    for (int c = 0; c < 3 && S.fss; ++c) n_inv += (int)S.sl_size[c].size();
+    for (int c = 0; c < 3 && S.fss; ++c) n_inv += (S.zmir ? 2 : 1) * (int)S.sl_size[c].size();
     n_inv = nop * (n_inv + S.nmc + 1);
     int* d_infos = S.dalloc<int>((size_t)2 * n_inv, tmp);
     CK(cudaMemsetAsync(d_infos, 0, sizeof(int) * 2 * n_inv, st));
@@ -773,6 +773,7 @@ static void setup_solver(Solver& S) {
     // (measured: batched 0.21 vs 0.66 ms for the 14-row slots of 64x2 order 6,
     // 94 vs 19 ms for the 272-row slots of 1024x16 order 16).
     constexpr int kBatchedMax = 128;
+    constexpr int kGjMinGlobal = 32;     // Gauss-Jordan in global memory only for this many matrices or more
     if (S.fss) {
         if (!t_lanes.blas) {
             if (cublasCreate(&t_lanes.blas) != CUBLAS_STATUS_SUCCESS) throw Err{SMPM_ECUDA, "cublasCreate failed"};
@@ -851,6 +852,22 @@ static void setup_solver(Solver& S) {
                 }
             const int nb = 2 * (int)items.size();
             if (nb == 0) continue;
+            if (h > gj_smem_max() && nb < kGjMinGlobal) {
+                // few large halves (a single operator's 2 x 2 slots): one CTA
+                // per matrix would leave most SMs idle for ~5 ms, so they go
+                // to cuSOLVER on the lanes, concurrently
+                fork();
+                for (const auto& it : items) {
+                    const int o = it[0], c = it[1], t = it[2];
+                    const int l = next_lane++ % L;
+                    double* d = slot_dst(o, c, t);
+                    k_build_slot_halves(lb[l].a, dLz, fz, sz, al[c][t] - S.k2[o], be[c][t], lanes[l].s);
+                    invert_on(l, lb[l].a, d, h);
+                    invert_on(l, lb[l].a + (size_t)h * h, d + (size_t)h * h, h);
+                }
+                join();
+                continue;
+            }
             double* work = S.dalloc<double>((size_t)nb * h * h, tmp);
             for (size_t it = 0; it < items.size(); ++it) {
                 const int o = items[it][0], c = items[it][1], t = items[it][2];
@@ -1103,11 +1120,15 @@ static void setup_solver(Solver& S) {
         if (tri_path && k2 > 0.0) {
             // C(t, t), C(t+1, t), C(t-1, t) as in the dense assembly below
             std::vector<double> dl((size_t)std::max(d - 1, 0)), dd((size_t)d), du((size_t)std::max(d - 1, 0)), du2;
+            double sums[3][2][2];                        // gsum(cls, side, 0, half, 0): 12 values per operator
+            for (int cl = 0; cl < 3; ++cl)
+                for (int side = 0; side < 2; ++side)
+                    for (int half = 0; half < 2; ++half) sums[cl][side][half] = gsum(cl, side, 0, half, 0);
             for (int t = 0; t < nif; ++t) {
                 const int cl_r = S.strip_cls[t + 1], cl_l = S.strip_cls[t];
-                dd[t] = 2.0 * gs + gsum(cl_r, 0, 0, 0, 0) + gsum(cl_l, 1, 0, 1, 0);
-                if (t >= 1) du[t - 1] = gsum(cl_l, 1, 0, 0, 0);
-                if (t + 1 <= nif - 1) dl[t] = gsum(cl_r, 0, 0, 1, 0);
+                dd[t] = 2.0 * gs + sums[cl_r][0][0] + sums[cl_l][1][1];
+                if (t >= 1) du[t - 1] = sums[cl_l][1][0];
+                if (t + 1 <= nif - 1) dl[t] = sums[cl_r][0][1];
             }
             std::vector<int>& sw = tri_swap[o];
             if (!tridiag_lu(d, dl, dd, du, du2, sw))
