@@ -374,8 +374,9 @@ def run_poisson2d(args):
 
 
 def run_other(args):
-    """Separate measurements of the 3-D mode batch and of the mixed-precision
-    solve (one JSON line each; the default bench line is poisson2d)."""
+    """Separate measurements: the 8x2 latency case, the 3-D mode batch and the
+    mixed-precision solves (one JSON line each; the default line is the
+    serving workload)."""
     import numpy as np
     import torch
     import __graft_entry__
@@ -507,6 +508,13 @@ SERVE_GRIDS = [(64, 2), (128, 4), (256, 8), (512, 16), (1024, 16)]
 SERVE_ORDERS = [6, 8, 12, 16]
 
 
+def serve_seed(rank):
+    """First seed of a rank's request stream: every rank serves its own stream
+    (weak scaling), seeds 100,000 apart so streams never overlap."""
+    from paper_1512_01756_gb300 import inputs
+    return inputs.seed_for(5) + 100_000 * rank
+
+
 def serve_stream(n, seed):
     """The request stream: grid uniform from SERVE_GRIDS on [0, mx/mz] x [0, 1],
     order uniform from SERVE_ORDERS, k^2 = 0 with probability 0.1 else
@@ -633,7 +641,7 @@ def run_serve(args):
     stream = torch.cuda.current_stream()
     K, W, per = args.steps, args.warmup, args.requests_per_step
     N = K * per
-    seed = inputs.seed_for(5) + 100_000 * rank          # every rank its own stream
+    seed = serve_seed(rank)                             # every rank its own stream
     reqs = serve_requests(N, seed, smpm, args.served_precision)
     offs = np.concatenate([[0], np.cumsum([q["r"] for q in reqs])])
     total = int(offs[-1])

@@ -32,8 +32,15 @@
  * Gauge: for k^2 = 0 the solution is returned with zero GLL-quadrature mean
  *   (the Neumann problem fixes u only up to a constant, Sec. 2.4).
  * Environment switches (none changes a result beyond rounding):
- *   SMPM_TRACE_SETUP / SMPM_TRACE_SOLVE print setup phases and per-cycle
- *   residuals on stderr; SMPM_NO_GRAPHS disables CUDA-graph replay of the
+ *   SMPM_TRACE_SETUP / SMPM_TRACE_SOLVE / SMPM_TRACE_PHASES print setup
+ *   phases, per-cycle residuals and a solve's phase times on stderr (the last
+ *   synchronises the stream at every phase); SMPM_OZAKI (bit mask, read at
+ *   setup): 1 runs the FP64 Schur and block-Jacobi products on the tensor
+ *   cores at FP64 accuracy, 2 the FP32 products of precisions 1 and 2 at FP32
+ *   accuracy; SMPM_COARSE_DENSE=1 (setup) takes the dense factorisation of
+ *   the coarse matrix instead of the tridiagonal one; SMPM_INNER_FP64_ARNOLDI=1
+ *   keeps the inner Arnoldi arithmetic of precision 2 in FP64;
+ *   SMPM_NO_GRAPHS disables CUDA-graph replay of the
  *   Arnoldi steps; SMPM_TILE_SHAPE=0|1 forces a GEMM tile shape instead of
  *   the autotuned one; SMPM_REFINE_EXTENDED forces extra-precise refinement;
  *   SMPM_INNER_STEPS sets the inner steps of precision 2; SMPM_MIRROR=0|1

@@ -311,7 +311,7 @@ int smpm_server_create(int nworkers, long long device_budget_bytes, int max_batc
     }
     s->budget = device_budget_bytes;
     // keep freed operator and Krylov memory in the device pool between batches
-    // (up to the budget) instead of returning it to the driver at every sync
+    // (up to the budget) instead of releasing it to the system at every sync
     cudaMemPool_t pool;
     if (cudaDeviceGetDefaultMemPool(&pool, s->device) == cudaSuccess) {
         unsigned long long keep = (unsigned long long)device_budget_bytes;
