@@ -121,3 +121,26 @@ def test_two_and_three_strips(mx):
     for method in ("dbj", "bj", "2las"):
         u, info = dbj.solve(g, f, method=method, tol=1e-13)
         assert np.linalg.norm(u - u_d) < 1e-10 * np.linalg.norm(u_d), method
+
+
+@pytest.mark.parametrize("shape,k2", [((8, 2, 6, 4.0, 1.0, 1.0), 0.0), ((9, 3, 5, 3.0, 1.0, 1.3), 2.5),
+                                      ((6, 4, 7, 1.5, 1.0, 1.0), 400.0)])
+def test_coarse_matrix_is_tridiagonal_with_one_vector_per_interface(shape, k2):
+    """C = Z^T S Z (Sec. 3.3) couples an interface only to its two neighbours
+    when each interface has one deflation vector: the strips between them are
+    the only coupling of S.  (The library's coarse division for k^2 > 0 relies
+    on this structure.)  With one vector per interface and element row the
+    couplings of one interface pair form full m_z x m_z blocks instead."""
+    mx, mz, order, lx, lz, zr = shape
+    g = Grid(mx, mz, order, lx, lz, z_ratio=zr)
+    sch = StripSchur(g, k2)
+    uS = sch.null_vectors()[1] if k2 == 0.0 else None
+    C = dbj.Deflation(g, sch.S, uS, groups="interface").C
+    assert C.shape == (mx - 1, mx - 1)
+    scale = np.abs(C).max()
+    assert np.abs(np.triu(C, 2)).max() <= 1e-14 * scale
+    assert np.abs(np.tril(C, -2)).max() <= 1e-14 * scale
+    assert np.abs(np.diag(C, 1)).min() > 1e-8 * scale     # the neighbours do couple
+    Ce = dbj.Deflation(g, sch.S, uS, groups="element_row").C
+    d = mz
+    assert np.abs(np.triu(Ce, 2 * d)).max() <= 1e-14 * scale   # block tridiagonal in m_z blocks
