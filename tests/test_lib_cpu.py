@@ -81,3 +81,20 @@ def test_grid_coords_match_oracle(lib):
     assert np.abs(x - X).max() < 1e-14 and np.abs(z - Z).max() < 1e-14
     with pytest.raises(smpm.SmpmError):
         smpm.grid_coords(smpm.make_grid(1, 1, 6, 2.5, 1.0))
+
+
+def test_request_footprint_is_host_arithmetic(lib):
+    """smpm_request_footprint needs no GPU: it grows with the operators and
+    the right-hand sides of a batch and with the grid, and rejects bad
+    arguments with SMPM_EINVAL."""
+    from paper_1512_01756_gb300 import smpm
+    small = smpm.make_grid(64, 2, 6, 32.0, 1.0)
+    big = smpm.make_grid(1024, 16, 16, 64.0, 1.0)
+    f11 = smpm.request_footprint(small, 1, 1)
+    assert f11 > 0
+    assert smpm.request_footprint(small, 4, 1) > f11
+    assert smpm.request_footprint(small, 1, 4) > f11
+    assert smpm.request_footprint(big, 1, 1) > 100 * (f11 - (64 << 20))
+    with pytest.raises(smpm.SmpmError) as e:
+        smpm.request_footprint(small, 0, 1)
+    assert e.value.code == smpm.SMPM_EINVAL
