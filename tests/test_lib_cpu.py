@@ -98,3 +98,12 @@ def test_request_footprint_is_host_arithmetic(lib):
     with pytest.raises(smpm.SmpmError) as e:
         smpm.request_footprint(small, 0, 1)
     assert e.value.code == smpm.SMPM_EINVAL
+
+
+def test_residual_history_rejects_a_null_handle(lib):
+    import ctypes
+    from paper_1512_01756_gb300 import smpm
+    cnt = ctypes.c_int(-1)
+    rc = lib.smpm_residual_history(None, 0, 0, 0, None, ctypes.byref(cnt))
+    assert rc == smpm.SMPM_EINVAL
+    assert b"null" in lib.smpm_last_error()
